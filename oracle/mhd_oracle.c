@@ -1,0 +1,594 @@
+/*
+ * mhd_oracle.c -- plain FP64 CPU oracle for the 3D pseudo-spectral isothermal compressible MHD
+ * right-hand side and the explicit Adams-Bashforth step that consumes it.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the GPU library links, includes or calls this file; only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark load it (through ctypes).
+ * It is deliberately slow and unfused: every stage of one time step is a separate full-grid pass
+ * over full complex N^3 spectra, in the order the paper's method prescribes, so that a reader can
+ * check it against the paper by eye.
+ *
+ * What is computed (paper, "Three dimensional numerical tests", Eqs. density, velocity, Bfield):
+ *   d(rho)/dt  = -div(rho u)
+ *   d(rho u)/dt = -div[ rho u(x)u + (P + |B|^2/2) I - B(x)B ] + mu lap(u),   P = Cs^2 rho
+ *   dB/dt      = -div( u(x)B - B(x)u ) + eta lap(B)
+ * in the component form the paper writes out for the momentum and induction equations
+ * (section "Governing equations"), with no forcing and no energy equation (isothermal closure).
+ *
+ * Spatial discretisation (paper, section "Code G-MHD3D"; Table I): pseudo-spectral.  Derivatives
+ * are products with i k in Fourier space, nonlinear products are formed in real space.  Products
+ * are dealiased with the 2/3 rule: a mode survives iff 3|k_x| < N, 3|k_y| < N and 3|k_z| < N.
+ * The derivative multiplier of the Nyquist index N/2 is zero (that mode is masked anyway).
+ *
+ * Conventions (the readings this oracle takes where the paper is silent):
+ *   grid          x_i = 2 pi i / N on the periodic box [0, 2 pi)^3, real index (z*N + y)*N + x
+ *   forward FFT   fhat(k) = N^-3 sum_x f(x) exp(-i k.x)     (so fhat(0) is the mean)
+ *   inverse FFT   f(x) = sum_k fhat(k) exp(+i k.x)          (unscaled)
+ *   wavenumber    FFT index m -> m for m < N/2, m - N for m > N/2, and 0 (derivative) at N/2
+ *   viscosity     +nu lap(u) with u = m / rho, as in Eq. velocity (mu there is nu here)
+ *   magnetic      Heaviside-Lorentz units: B^2/2 and B(x)B, as in Eq. velocity
+ *   pressure      -grad P = -i k Cs^2 rho_hat, taken from the (already dealiased) density spectrum
+ *   integrator    Adams-Bashforth of order 2 with variable step (forward Euler on the first step):
+ *                 y^{n+1} = y^n + dt_n [ (1 + r/2) f^n - (r/2) f^{n-1} ],  r = dt_n / dt_{n-1}
+ *   CFL           dt = min( C_a dx / max_x(|u| + c_f),  C_v / (max(nu, eta) k_max^2) ),
+ *                 dx = 2 pi / N, c_f = sqrt(Cs^2 + |B|^2 / rho), k_max = floor((N-1)/3);
+ *                 a fixed dt is used instead when one is given.
+ *
+ * Everything is IEEE double precision; no -ffast-math.  Results do not depend on the number of
+ * OpenMP threads: every parallel loop writes disjoint outputs and every sum is taken in a fixed
+ * serial order over per-plane partials.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------------------------------ */
+/* Radix-2 FFT                                                                                */
+/* ------------------------------------------------------------------------------------------ */
+
+static int is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+/* exp(sign * 2 pi i * j / n), each value computed directly from cos/sin of its own angle. */
+static cplx twiddle(int j, int n, int sign) {
+  const double ang = 2.0 * M_PI * (double)j / (double)n;
+  return cos(ang) + (double)sign * sin(ang) * I;
+}
+
+/*
+ * In-place iterative radix-2 decimation-in-time FFT of length n (a power of two):
+ *   a[k] <- sum_j a[j] exp(sign * 2 pi i j k / n),   unscaled.
+ * Step 1 permutes the input into bit-reversed order; step 2 merges sub-transforms of length
+ * len/2 into transforms of length len with the butterfly (u, w v) -> (u + w v, u - w v).
+ * `w` holds exp(sign 2 pi i j / n) for j < n/2.
+ */
+void or_fft1d_tw(cplx *a, int n, const cplx *w) {
+  for (int i = 1, j = 0; i < n; ++i) {
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      cplx t = a[i];
+      a[i] = a[j];
+      a[j] = t;
+    }
+  }
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1;
+    const int step = n / len; /* w_len^j = w_n^(j * n / len) */
+    for (int s = 0; s < n; s += len) {
+      for (int j = 0; j < half; ++j) {
+        const cplx u = a[s + j];
+        const cplx v = a[s + j + half] * w[j * step];
+        a[s + j] = u + v;
+        a[s + j + half] = u - v;
+      }
+    }
+  }
+}
+
+static cplx *make_twiddles(int n, int sign) {
+  cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)(n / 2 > 0 ? n / 2 : 1));
+  for (int j = 0; j < n / 2; ++j) w[j] = twiddle(j, n, sign);
+  return w;
+}
+
+/* 1D transform of a contiguous array; returns 0 on success, -1 if n is not a power of two. */
+int or_fft1d(cplx *a, int n, int sign) {
+  if (!is_pow2(n)) return -1;
+  cplx *w = make_twiddles(n, sign);
+  or_fft1d_tw(a, n, w);
+  free(w);
+  return 0;
+}
+
+/*
+ * 3D transform of an N^3 complex array with index (z*N + y)*N + x, unscaled, applied as three
+ * passes of 1D transforms: along x (contiguous rows), then y, then z.  Each strided pencil is
+ * gathered into a contiguous buffer, transformed and scattered back.
+ */
+int or_fft3d(cplx *a, int n, int sign) {
+  if (!is_pow2(n)) return -1;
+  cplx *w = make_twiddles(n, sign);
+  const size_t N = (size_t)n;
+#pragma omp parallel
+  {
+    cplx *buf = (cplx *)malloc(sizeof(cplx) * N);
+    /* x pass */
+#pragma omp for schedule(static)
+    for (long r = 0; r < (long)(N * N); ++r) or_fft1d_tw(a + (size_t)r * N, n, w);
+    /* y pass */
+#pragma omp for schedule(static)
+    for (long p = 0; p < (long)(N * N); ++p) {
+      const size_t z = (size_t)p / N, x = (size_t)p % N;
+      for (size_t y = 0; y < N; ++y) buf[y] = a[(z * N + y) * N + x];
+      or_fft1d_tw(buf, n, w);
+      for (size_t y = 0; y < N; ++y) a[(z * N + y) * N + x] = buf[y];
+    }
+    /* z pass */
+#pragma omp for schedule(static)
+    for (long p = 0; p < (long)(N * N); ++p) {
+      const size_t y = (size_t)p / N, x = (size_t)p % N;
+      for (size_t z = 0; z < N; ++z) buf[z] = a[(z * N + y) * N + x];
+      or_fft1d_tw(buf, n, w);
+      for (size_t z = 0; z < N; ++z) a[(z * N + y) * N + x] = buf[z];
+    }
+    free(buf);
+  }
+  free(w);
+  return 0;
+}
+
+/* fhat = N^-3 FFT(f) for a real field f. */
+int or_forward(const double *f, cplx *fhat, int n) {
+  const size_t n3 = (size_t)n * n * n;
+  for (size_t i = 0; i < n3; ++i) fhat[i] = f[i];
+  if (or_fft3d(fhat, n, -1)) return -1;
+  const double s = 1.0 / (double)n3;
+  for (size_t i = 0; i < n3; ++i) fhat[i] *= s;
+  return 0;
+}
+
+/* f = Re IFFT(fhat), unscaled.  `tmp` is N^3 complex scratch (may alias nothing else). */
+static int or_inverse_tmp(const cplx *fhat, double *f, int n, cplx *tmp) {
+  const size_t n3 = (size_t)n * n * n;
+  memcpy(tmp, fhat, sizeof(cplx) * n3);
+  if (or_fft3d(tmp, n, +1)) return -1;
+  for (size_t i = 0; i < n3; ++i) f[i] = creal(tmp[i]);
+  return 0;
+}
+
+int or_inverse(const cplx *fhat, double *f, int n) {
+  const size_t n3 = (size_t)n * n * n;
+  cplx *tmp = (cplx *)malloc(sizeof(cplx) * n3);
+  if (!tmp) return -2;
+  int rc = or_inverse_tmp(fhat, f, n, tmp);
+  free(tmp);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Wavenumbers and the 2/3 dealiasing mask                                                     */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Signed wavenumber of FFT index m used in derivatives; the Nyquist index gets 0. */
+static double wavenumber(int m, int n) {
+  if (2 * m < n) return (double)m;
+  if (2 * m == n) return 0.0;
+  return (double)(m - n);
+}
+
+/* Magnitude of the signed index of FFT index m (the Nyquist index counts as n/2). */
+static int absindex(int m, int n) { return (2 * m <= n) ? m : n - m; }
+
+/* D(k) of the 2/3 rule: 1 iff 3|k_x| < N, 3|k_y| < N and 3|k_z| < N. */
+static int mask23(int mx, int my, int mz, int n) {
+  return 3 * absindex(mx, n) < n && 3 * absindex(my, n) < n && 3 * absindex(mz, n) < n;
+}
+
+int or_kmax(int n) { return (n - 1) / 3; }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Solver state                                                                               */
+/* ------------------------------------------------------------------------------------------ */
+
+enum { F_RHO = 0, F_MX, F_MY, F_MZ, F_BX, F_BY, F_BZ, NSTATE };
+/* flux fields, in this order: T_xx T_yy T_zz T_xy T_xz T_yz, E_x E_y E_z, u_x u_y u_z */
+enum { T_XX = 0, T_YY, T_ZZ, T_XY, T_XZ, T_YZ, E_X, E_Y, E_Z, U_X, U_Y, U_Z, NFLUX };
+
+typedef struct {
+  int n;
+  double nu, eta, cs;   /* viscosity (mu), resistivity, isothermal sound speed */
+  double dt_fixed;      /* > 0: fixed step; <= 0: CFL step */
+  double cfl_adv, cfl_visc;
+} or_params;
+
+typedef struct {
+  or_params p;
+  size_t n3;
+  cplx *state[NSTATE]; /* masked spectra of rho, m, B */
+  cplx *hist[NSTATE];  /* f^{n-1}: the RHS of the previous step */
+  cplx *rhs[NSTATE];
+  cplx *flux[NFLUX];
+  double *real[NSTATE];
+  double *rflux[NFLUX];
+  cplx *tmp;
+  double t, dt_prev, dt_last;
+  int64_t step;
+} or_ctx;
+
+static void ctx_free(or_ctx *c) {
+  if (!c) return;
+  for (int f = 0; f < NSTATE; ++f) {
+    free(c->state[f]);
+    free(c->hist[f]);
+    free(c->rhs[f]);
+    free(c->real[f]);
+  }
+  for (int f = 0; f < NFLUX; ++f) {
+    free(c->flux[f]);
+    free(c->rflux[f]);
+  }
+  free(c->tmp);
+  free(c);
+}
+
+or_ctx *or_create(const or_params *p) {
+  if (!p || !is_pow2(p->n) || p->n < 4) return NULL;
+  or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
+  if (!c) return NULL;
+  c->p = *p;
+  c->n3 = (size_t)p->n * p->n * p->n;
+  int ok = 1;
+  for (int f = 0; f < NSTATE; ++f) {
+    ok &= (c->state[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->hist[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->rhs[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->real[f] = (double *)calloc(c->n3, sizeof(double))) != NULL;
+  }
+  for (int f = 0; f < NFLUX; ++f) {
+    ok &= (c->flux[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->rflux[f] = (double *)calloc(c->n3, sizeof(double))) != NULL;
+  }
+  ok &= (c->tmp = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+  if (!ok) {
+    ctx_free(c);
+    return NULL;
+  }
+  return c;
+}
+
+void or_destroy(or_ctx *c) { ctx_free(c); }
+
+static void apply_mask(cplx *a, int n) {
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x)
+        if (!mask23(x, y, z, n)) a[((size_t)z * n + y) * n + x] = 0.0;
+}
+
+/*
+ * Initial state from real-space rho, u = (u_x, u_y, u_z), B = (B_x, B_y, B_z) (each N^3, the
+ * components of u and B stacked).  The evolved variable is the momentum density m = rho u; every
+ * field is transformed and projected onto the dealiased modes.  Resets time, step and history.
+ */
+int or_set_state(or_ctx *c, const double *rho, const double *u, const double *b) {
+  const size_t n3 = c->n3;
+  const int n = c->p.n;
+  double *m = (double *)malloc(sizeof(double) * n3);
+  if (!m) return -2;
+  if (or_forward(rho, c->state[F_RHO], n)) return -1;
+  for (int d = 0; d < 3; ++d) {
+    for (size_t i = 0; i < n3; ++i) m[i] = rho[i] * u[d * n3 + i];
+    or_forward(m, c->state[F_MX + d], n);
+    or_forward(b + d * n3, c->state[F_BX + d], n);
+  }
+  free(m);
+  for (int f = 0; f < NSTATE; ++f) {
+    apply_mask(c->state[f], n);
+    memset(c->hist[f], 0, sizeof(cplx) * n3);
+  }
+  c->t = 0.0;
+  c->dt_prev = 0.0;
+  c->dt_last = 0.0;
+  c->step = 0;
+  return 0;
+}
+
+/* Real-space rho, m, B of the current state (each N^3; m and B components stacked). */
+int or_get_state(or_ctx *c, double *rho, double *m, double *b) {
+  const size_t n3 = c->n3;
+  const int n = c->p.n;
+  or_inverse_tmp(c->state[F_RHO], rho, n, c->tmp);
+  for (int d = 0; d < 3; ++d) {
+    or_inverse_tmp(c->state[F_MX + d], m + d * n3, n, c->tmp);
+    or_inverse_tmp(c->state[F_BX + d], b + d * n3, n, c->tmp);
+  }
+  return 0;
+}
+
+/* Copy of one state spectrum (full N^3 complex layout, zeros outside the mask). */
+int or_get_spectrum(or_ctx *c, int field, cplx *out) {
+  if (field < 0 || field >= NSTATE) return -1;
+  memcpy(out, c->state[field], sizeof(cplx) * c->n3);
+  return 0;
+}
+
+/* Replace one state spectrum (the caller's spectrum is masked on the way in). */
+int or_set_spectrum(or_ctx *c, int field, const cplx *in) {
+  if (field < 0 || field >= NSTATE) return -1;
+  memcpy(c->state[field], in, sizeof(cplx) * c->n3);
+  apply_mask(c->state[field], c->p.n);
+  return 0;
+}
+
+/*
+ * The right-hand side f(y) of the 3D system, in the order of the pseudo-spectral method:
+ *   1. inverse transforms of rho_hat, m_hat, B_hat to the grid;
+ *   2. u = m / rho, |B|^2, and the products on the grid:
+ *        T_ij = m_i u_j + delta_ij |B|^2 / 2 - B_i B_j       (momentum flux without P)
+ *        E    = u x B                                       (so that -div(uB - Bu) = curl E)
+ *        u                                                  (for the viscous term)
+ *   3. forward transforms of the 12 products;
+ *   4. in Fourier space:
+ *        rho_t   = -i k . m_hat
+ *        m_t,i   = -i sum_j k_j T_ij_hat - i k_i Cs^2 rho_hat - nu |k|^2 u_i_hat
+ *        B_t     =  i k x E_hat - eta |k|^2 B_hat
+ *   5. multiplication of every RHS spectrum by the 2/3 mask D(k).
+ * Also returns max_x(|u| + c_f) over the grid (for the CFL step) in *smax.
+ */
+static int compute_rhs(or_ctx *c, double *smax) {
+  const int n = c->p.n;
+  const size_t n3 = c->n3;
+  const double cs2 = c->p.cs * c->p.cs;
+
+  /* 1. */
+  for (int f = 0; f < NSTATE; ++f) or_inverse_tmp(c->state[f], c->real[f], n, c->tmp);
+
+  /* 2. */
+  double *plane_max = (double *)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < n; ++z) {
+    double pm = 0.0;
+    for (size_t i = (size_t)z * n * n; i < (size_t)(z + 1) * n * n; ++i) {
+      const double rho = c->real[F_RHO][i];
+      const double m[3] = {c->real[F_MX][i], c->real[F_MY][i], c->real[F_MZ][i]};
+      const double B[3] = {c->real[F_BX][i], c->real[F_BY][i], c->real[F_BZ][i]};
+      const double u[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+      const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+      c->rflux[T_XX][i] = m[0] * u[0] + 0.5 * b2 - B[0] * B[0];
+      c->rflux[T_YY][i] = m[1] * u[1] + 0.5 * b2 - B[1] * B[1];
+      c->rflux[T_ZZ][i] = m[2] * u[2] + 0.5 * b2 - B[2] * B[2];
+      c->rflux[T_XY][i] = m[0] * u[1] - B[0] * B[1];
+      c->rflux[T_XZ][i] = m[0] * u[2] - B[0] * B[2];
+      c->rflux[T_YZ][i] = m[1] * u[2] - B[1] * B[2];
+      c->rflux[E_X][i] = u[1] * B[2] - u[2] * B[1];
+      c->rflux[E_Y][i] = u[2] * B[0] - u[0] * B[2];
+      c->rflux[E_Z][i] = u[0] * B[1] - u[1] * B[0];
+      c->rflux[U_X][i] = u[0];
+      c->rflux[U_Y][i] = u[1];
+      c->rflux[U_Z][i] = u[2];
+      const double speed = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      const double cf = sqrt(cs2 + b2 / rho);
+      const double s = speed + cf;
+      if (!(s <= pm)) pm = s; /* propagates NaN */
+    }
+    plane_max[z] = pm;
+  }
+  double sm = 0.0;
+  for (int z = 0; z < n; ++z)
+    if (!(plane_max[z] <= sm)) sm = plane_max[z];
+  free(plane_max);
+  if (smax) *smax = sm;
+
+  /* 3. */
+  for (int f = 0; f < NFLUX; ++f) or_forward(c->rflux[f], c->flux[f], n);
+
+  /* 4. and 5. */
+  const double nu = c->p.nu, eta = c->p.eta;
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < n; ++z) {
+    for (int y = 0; y < n; ++y) {
+      for (int x = 0; x < n; ++x) {
+        const size_t i = ((size_t)z * n + y) * n + x;
+        if (!mask23(x, y, z, n)) {
+          for (int f = 0; f < NSTATE; ++f) c->rhs[f][i] = 0.0;
+          continue;
+        }
+        const double k[3] = {wavenumber(x, n), wavenumber(y, n), wavenumber(z, n)};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        const cplx rho = c->state[F_RHO][i];
+        const cplx mh[3] = {c->state[F_MX][i], c->state[F_MY][i], c->state[F_MZ][i]};
+        const cplx Bh[3] = {c->state[F_BX][i], c->state[F_BY][i], c->state[F_BZ][i]};
+        /* symmetric momentum-flux tensor T_ij_hat */
+        const cplx Txx = c->flux[T_XX][i], Tyy = c->flux[T_YY][i], Tzz = c->flux[T_ZZ][i];
+        const cplx Txy = c->flux[T_XY][i], Txz = c->flux[T_XZ][i], Tyz = c->flux[T_YZ][i];
+        const cplx T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+        const cplx Eh[3] = {c->flux[E_X][i], c->flux[E_Y][i], c->flux[E_Z][i]};
+        const cplx uh[3] = {c->flux[U_X][i], c->flux[U_Y][i], c->flux[U_Z][i]};
+
+        /* continuity */
+        c->rhs[F_RHO][i] = -I * (k[0] * mh[0] + k[1] * mh[1] + k[2] * mh[2]);
+        /* momentum */
+        for (int a = 0; a < 3; ++a) {
+          cplx divT = k[0] * T[a][0] + k[1] * T[a][1] + k[2] * T[a][2];
+          c->rhs[F_MX + a][i] = -I * divT - I * k[a] * cs2 * rho - nu * k2 * uh[a];
+        }
+        /* induction: curl E with E = u x B */
+        const cplx curlE[3] = {I * (k[1] * Eh[2] - k[2] * Eh[1]), I * (k[2] * Eh[0] - k[0] * Eh[2]),
+                               I * (k[0] * Eh[1] - k[1] * Eh[0])};
+        for (int a = 0; a < 3; ++a) c->rhs[F_BX + a][i] = curlE[a] - eta * k2 * Bh[a];
+      }
+    }
+  }
+  return 0;
+}
+
+/* Real-space RHS of the current state: drho (N^3), dm (3 N^3), dB (3 N^3).  State unchanged. */
+int or_rhs(or_ctx *c, double *drho, double *dm, double *db) {
+  compute_rhs(c, NULL);
+  const size_t n3 = c->n3;
+  or_inverse_tmp(c->rhs[F_RHO], drho, c->p.n, c->tmp);
+  for (int d = 0; d < 3; ++d) {
+    or_inverse_tmp(c->rhs[F_MX + d], dm + d * n3, c->p.n, c->tmp);
+    or_inverse_tmp(c->rhs[F_BX + d], db + d * n3, c->p.n, c->tmp);
+  }
+  return 0;
+}
+
+/* RHS spectrum of one field (full N^3 complex layout) for the current state. */
+int or_rhs_spectrum(or_ctx *c, int field, cplx *out) {
+  if (field < 0 || field >= NSTATE) return -1;
+  compute_rhs(c, NULL);
+  memcpy(out, c->rhs[field], sizeof(cplx) * c->n3);
+  return 0;
+}
+
+/* The CFL step of the current state given max_x(|u| + c_f). */
+static double cfl_dt(const or_ctx *c, double smax) {
+  const int n = c->p.n;
+  const double dx = 2.0 * M_PI / (double)n;
+  double dt = c->p.cfl_adv * dx / smax;
+  const double diff = c->p.nu > c->p.eta ? c->p.nu : c->p.eta;
+  const int km = or_kmax(n);
+  if (diff > 0.0 && km > 0) {
+    const double dtv = c->p.cfl_visc / (diff * (double)km * (double)km);
+    if (dtv < dt) dt = dtv;
+  }
+  return dt;
+}
+
+/*
+ * Advance `nsteps` Adams-Bashforth steps (order 2, variable dt; forward Euler when there is no
+ * previous RHS).  Returns 0, or 1 if a non-finite value appeared in max(|u| + c_f) or dt (the
+ * state is then left at the last finite step).
+ */
+int or_step(or_ctx *c, int nsteps) {
+  const size_t n3 = c->n3;
+  for (int s = 0; s < nsteps; ++s) {
+    double smax = 0.0;
+    compute_rhs(c, &smax);
+    const double dt = c->p.dt_fixed > 0.0 ? c->p.dt_fixed : cfl_dt(c, smax);
+    if (!isfinite(smax) || !isfinite(dt) || dt <= 0.0) return 1;
+    double a1 = 1.0, a0 = 0.0; /* coefficients of f^n and f^{n-1} */
+    if (c->step > 0) {
+      const double r = dt / c->dt_prev;
+      a1 = 1.0 + 0.5 * r;
+      a0 = -0.5 * r;
+    }
+    for (int f = 0; f < NSTATE; ++f) {
+      cplx *y = c->state[f], *fn = c->rhs[f], *fo = c->hist[f];
+#pragma omp parallel for schedule(static)
+      for (long i = 0; i < (long)n3; ++i) {
+        y[i] = y[i] + dt * (a1 * fn[i] + a0 * fo[i]);
+        fo[i] = fn[i];
+      }
+    }
+    c->dt_prev = dt;
+    c->dt_last = dt;
+    c->t += dt;
+    c->step += 1;
+  }
+  return 0;
+}
+
+/* History (f^{n-1}) access for checkpoint tests. */
+int or_get_history(or_ctx *c, int field, cplx *out, double *dt_prev, double *t, int64_t *step) {
+  if (field < 0 || field >= NSTATE) return -1;
+  memcpy(out, c->hist[field], sizeof(cplx) * c->n3);
+  if (dt_prev) *dt_prev = c->dt_prev;
+  if (t) *t = c->t;
+  if (step) *step = c->step;
+  return 0;
+}
+
+/*
+ * Scalar diagnostics of the current state (volume averages <.> over the grid):
+ *   out[0]  ke        <|m|^2 / (2 rho)>
+ *   out[1]  me        <|B|^2 / 2>
+ *   out[2]  eint      <Cs^2 rho ln rho>  (isothermal internal energy, conserved with ke + me
+ *                                         in the ideal limit)
+ *   out[3]  cross_hel <u . B>
+ *   out[4]  mean_speed <|u|>
+ *   out[5]  mean_bmag  <|B|>
+ *   out[6]  smax       max(|u| + c_f)
+ *   out[7]  mean_rho   rho_hat(0)
+ *   out[8..10]  mean_m   m_hat(0)
+ *   out[11..13] mean_b   B_hat(0)
+ *   out[14] divb_rms  sqrt(<(div B)^2>), from Parseval over the spectrum
+ *   out[15] t, out[16] dt of the last step, out[17] step
+ * Sums are taken per z-plane, then over planes in order.
+ */
+int or_diagnostics(or_ctx *c, double *out) {
+  const int n = c->p.n;
+  const size_t n3 = c->n3;
+  const double cs2 = c->p.cs * c->p.cs;
+  for (int f = 0; f < NSTATE; ++f) or_inverse_tmp(c->state[f], c->real[f], n, c->tmp);
+  double *acc = (double *)calloc((size_t)n * 7, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < n; ++z) {
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (size_t i = (size_t)z * n * n; i < (size_t)(z + 1) * n * n; ++i) {
+      const double rho = c->real[F_RHO][i];
+      const double m[3] = {c->real[F_MX][i], c->real[F_MY][i], c->real[F_MZ][i]};
+      const double B[3] = {c->real[F_BX][i], c->real[F_BY][i], c->real[F_BZ][i]};
+      const double u[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+      const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+      const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+      s[0] += 0.5 * rho * u2;
+      s[1] += 0.5 * b2;
+      s[2] += cs2 * rho * log(rho);
+      s[3] += u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+      s[4] += sqrt(u2);
+      s[5] += sqrt(b2);
+      const double v = sqrt(u2) + sqrt(cs2 + b2 / rho);
+      if (!(v <= s[6])) s[6] = v;
+    }
+    for (int q = 0; q < 7; ++q) acc[(size_t)z * 7 + q] = s[q];
+  }
+  double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int z = 0; z < n; ++z) {
+    for (int q = 0; q < 6; ++q) tot[q] += acc[(size_t)z * 7 + q];
+    if (!(acc[(size_t)z * 7 + 6] <= tot[6])) tot[6] = acc[(size_t)z * 7 + 6];
+  }
+  free(acc);
+  for (int q = 0; q < 6; ++q) out[q] = tot[q] / (double)n3;
+  out[6] = tot[6];
+  out[7] = creal(c->state[F_RHO][0]);
+  for (int d = 0; d < 3; ++d) {
+    out[8 + d] = creal(c->state[F_MX + d][0]);
+    out[11 + d] = creal(c->state[F_BX + d][0]);
+  }
+  /* Parseval: <g^2> = sum_k |ghat(k)|^2 for g = div B, ghat = i k . B_hat */
+  double dsum = 0.0;
+  for (int z = 0; z < n; ++z) {
+    for (int y = 0; y < n; ++y) {
+      for (int x = 0; x < n; ++x) {
+        const size_t i = ((size_t)z * n + y) * n + x;
+        const cplx g = I * (wavenumber(x, n) * c->state[F_BX][i] + wavenumber(y, n) * c->state[F_BY][i] +
+                            wavenumber(z, n) * c->state[F_BZ][i]);
+        dsum += creal(g) * creal(g) + cimag(g) * cimag(g);
+      }
+    }
+  }
+  out[14] = sqrt(dsum);
+  out[15] = c->t;
+  out[16] = c->dt_last;
+  out[17] = (double)c->step;
+  return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
