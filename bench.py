@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the MHD time step on GB300.
+
+Workload (default): N = 256^3 FP64 dynamo run -- ABC flow (A = B = C = 1, k_f = 1), Mach 0.1
+(Cs = 10), seed magnetic field of random |k| <= 4 modes at energy <|B|^2>/2 = 1e-5 from seed 1,
+nu = eta = 2e-3, rho0 = 1, CFL-limited dt.  One bench step is one Adams-Bashforth step of the whole
+hot path (inverse transforms, fluxes, forward transforms, spectral assembly, CFL dt, update).
+The per-step working set (about 2.4 GB) is far larger than the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent replica (the
+instances share nothing), the timed region is bracketed by barriers and the slowest rank's time
+is used.  `--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MHD grid-point-steps/s & HBM GB/s vs peak; served p50/p99 at rel err ≤1e-5"
+UNIT = "grid-point-steps/s"
+# Paper, Table III: 256^3 on a Tesla V100 at 0.22 s per step (FP64, OpenACC + cuFFT, unified
+# memory) -> 256^3 / 0.22 grid-point-steps/s.  Another machine: context for the ratio only.
+PAPER_256_V100 = 256 ** 3 / 0.22
+FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(n: int):
+    from paper_1810_12707_gb300 import inputs
+    return inputs.abc_dynamo(n, seed=1, b_energy=1e-5, mach=0.1, nu=2e-3, eta=2e-3)
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithmic work per launch of each kernel (FP64: 16-byte complex).  Bytes are the compulsory
+# HBM reads + writes of the pass; flops count 5 N log2 N per complex FFT of length N plus the
+# pointwise arithmetic.
+# ---------------------------------------------------------------------------------------------
+def kernel_model(n: int, batch: int = 1):
+    k = (n - 1) // 3
+    nx, nk = k + 1, 2 * k + 1
+    spec = nk * nk * nx
+    c = 16.0
+    fft = 5.0 * n * math.log2(n)
+    m = {
+        "inverse_z": (7 * (spec + n * nk * nx) * c, 7 * nk * nx * fft),
+        "inverse_y": (7 * (n * nk * nx + n * n * nx) * c, 7 * n * nx * fft),
+        "flux_x": ((7 + 12) * n * n * nx * c, (7 + 12) * (n * n / 2) * fft + 49.0 * n ** 3),
+        "step_dt": (8.0 * n * n / 2, 0.0),
+        "forward_y": (12 * (n * n * nx + n * nk * nx) * c, 12 * n * nx * fft),
+        "forward_z": (12 * (n * nk * nx + spec) * c, 12 * nk * nx * fft),
+        "assemble_ab2": ((12 + 7 + 7 + 7 + 7) * spec * c, 110.0 * spec),
+    }
+    return {key: (b * batch, f * batch) for key, (b, f) in m.items()}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_oracle(n: int, steps: int, budget_s: float = 30.0):
+    """Time the CPU oracle on the same workload: `steps` AB2 steps after one untimed set_state."""
+    from oracle import oracle
+    ic = workload(n)
+    o = oracle.Oracle(n, ic.nu, ic.eta, ic.cs, dt=0.0)
+    o.set_state(ic.rho, ic.u, ic.b)
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n ** 3 * done / el, done, el, oracle.num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.n
+    # each bench step is one oracle step of the same workload; the run is capped at about three
+    # minutes of CPU work in total
+    _, _, t_one, _ = time_oracle(n, 1)
+    budget = 180.0
+    k = max(1, min(args.steps, int(budget / max(t_one, 1e-9))))
+    value, done, el, cores = time_oracle(n, k, budget_s=budget)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": done, "warmup": 1, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_256_V100 if n == 256 else None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"abc_dynamo_{n}^3_fp64", "n": n, "batch": 1, "precision": "fp64",
+                   "ic": "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", "mach": 0.1, "nu": 2e-3,
+                   "eta": 2e-3, "dt": "cfl"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} AB2 steps of the {n}^3 workload after set_state (one untimed warm-up step)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1810_12707_gb300 import build_lib
+    if rank == 0:
+        build_lib.build()
+    if dist:
+        dist.barrier()
+    from paper_1810_12707_gb300 import mhd
+
+    n, K, W = args.n, args.steps, args.warmup
+    ic = workload(n)
+    ctx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0)
+    mhd.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+    stream = torch.cuda.current_stream()
+
+    mhd.mhd_step(ctx, W)
+    if mhd.mhd_synchronize(ctx) != mhd.MHD_OK:
+        raise RuntimeError("non-finite state during warm-up")
+
+    sampler = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    mhd.mhd_profile(ctx, True)
+    e0.record(stream)
+    for _ in range(K):
+        mhd.mhd_step(ctx, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = mhd.mhd_profile_read(ctx)
+    mhd.mhd_profile(ctx, False)
+    st = mhd.mhd_synchronize(ctx)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n ** 3 * K / (ms / 1e3)
+    diag = mhd.mhd_diagnostics(ctx, 0)
+
+    # end to end through the C ABI with pinned host buffers: per step, H2D of the state
+    # (rho, u, B), one step, D2H of the state (rho, m, B)
+    E = max(1, min(K, args.e2e_steps))
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    h_rho, h_u, h_b = pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))
+    h_rho[...] = ic.rho
+    h_u[...] = ic.u
+    h_b[...] = ic.b
+    lib = mhd.load_library()
+    o_rho, o_m, o_b = pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))
+    ectx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0)
+    mhd.mhd_set_state(ectx, 0, h_rho, h_u, h_b)
+    mhd.mhd_step(ectx, 2)
+    lib.mhd_get_state(ectx.handle, 0, o_rho.ctypes.data, o_m.ctypes.data, o_b.ctypes.data, 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        assert lib.mhd_set_state(ectx.handle, 0, h_rho.ctypes.data, h_u.ctypes.data, h_b.ctypes.data, 0) == 0
+        assert lib.mhd_step(ectx.handle, 1) == 0
+        assert lib.mhd_get_state(ectx.handle, 0, o_rho.ctypes.data, o_m.ctypes.data, o_b.ctypes.data, 0) == 0
+    te = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": world * n ** 3 * E / te, "unit": UNIT, "h2d_bytes_per_step": 7 * n ** 3 * 8,
+           "d2h_bytes_per_step": 7 * n ** 3 * 8, "steps": E}
+    mhd.mhd_destroy(ectx)
+
+    # roofline of the dominant kernel (largest share of device time)
+    hbm, hbm_src = peaks()
+    model = kernel_model(n)
+    per = {}
+    for name, (tot, cnt) in prof.items():
+        if cnt:
+            b, f = model[name]
+            avg = tot / cnt
+            per[name] = {"avg_ms": avg, "share": tot / max(sum(v[0] for v in prof.values()), 1e-30),
+                         "gbs": b / (avg * 1e-3) / 1e9, "tflops": f / (avg * 1e-3) / 1e12}
+    top = max(per, key=lambda k: per[k]["share"])
+    tb, tf = model[top]
+    t_mem = tb / (hbm * 1e9)
+    t_alu = tf / (FP64_PEAK_TFLOPS * 1e12)
+    if t_alu >= t_mem:
+        roof = {"bound": "alu", "achieved": per[top]["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": per[top]["tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)"}
+    else:
+        roof = {"bound": "hbm", "achieved": per[top]["gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": per[top]["gbs"] / hbm, "traffic": None, "peak_source": f"{hbm_src} copy"}
+    roof.update({"kernel": top, "algorithmic_bytes": tb, "algorithmic_flops": tf,
+                 "achieved_gbs": per[top]["gbs"], "frac_hbm_of_measured": per[top]["gbs"] / hbm})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, done, el, cores = time_oracle(n, 2, budget_s=30.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{done} AB2 steps of the {n}^3 workload after an untimed set_state ({el:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / (world * PAPER_256_V100) if n == 256 else None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"abc_dynamo_{n}^3_fp64", "n": n, "batch": 1, "precision": "fp64",
+                       "ic": "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", "mach": 0.1, "nu": 2e-3,
+                       "eta": 2e-3, "dt": "cfl", "l2": "per-step working set > L2 (no flush)",
+                       "parallelism": f"replicas x{world}",
+                       "baseline": "paper Table III 256^3 V100 0.22 s/step (other hardware, context)"},
+            "roofline": roof,
+            "kernels": per,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 7 * K,
+            "clocks": clocks,
+            "status": mhd.STATUS_NAMES.get(st, st),
+            "final": {"t": diag["t"], "dt": diag["dt"], "step": diag["step"], "ke": diag["ke"], "me": diag["me"]},
+        }
+        print(json.dumps(line), flush=True)
+    mhd.mhd_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

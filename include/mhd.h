@@ -1,0 +1,185 @@
+/*
+ * mhd.h -- C ABI of the GB300 (sm_103a) pseudo-spectral compressible MHD library.
+ *
+ * The library evolves the isothermal compressible MHD system of the paper's 3D tests (section
+ * "Three dimensional numerical tests", Eqs. density, velocity, Bfield):
+ *     d(rho)/dt   = -div(rho u)
+ *     d(rho u)/dt = -div[ rho u(x)u + (Cs^2 rho + |B|^2/2) I - B(x)B ] + nu lap(u)
+ *     dB/dt       = -div( u(x)B - B(x)u ) + eta lap(B)
+ * on the periodic box [0, 2 pi)^3 with N^3 points, pseudo-spectrally (section "Code G-MHD3D":
+ * derivatives as i k products in Fourier space, products on the grid), with the 2/3-rule
+ * truncation (a mode is kept iff 3|k_x| < N, 3|k_y| < N and 3|k_z| < N) applied to every product
+ * and to the initial state, and the explicit Adams-Bashforth time step the paper reports its
+ * results with, taken here as second order with variable step (forward Euler on the first step)
+ * and a CFL-limited dt:
+ *     dt = min( cfl_adv * (2 pi / N) / max_x(|u| + sqrt(Cs^2 + |B|^2 / rho)),
+ *               cfl_visc / (max(nu, eta) * k_max^2) ),    k_max = floor((N - 1) / 3)
+ * unless a fixed dt is given.
+ *
+ * Conventions shared by every entry point:
+ *   - real fields are float64, x fastest: value (x_i, y_j, z_k) at index (k*N + j)*N + i, with
+ *     x_i = 2 pi i / N; a vector field is three such arrays stacked (x, y, z components);
+ *   - spectra are forward-normalised: fhat(k) = N^-3 sum_x f(x) exp(-i k.x);
+ *   - a pointer flagged `on_device` = 1 is a CUDA device pointer of the current device, else a
+ *     host pointer (pageable or pinned); input arrays are only read during the call and never
+ *     retained; output arrays are written before the call returns;
+ *   - every entry point returns an mhd_status; nothing throws across the ABI.  After an error
+ *     other than MHD_ENONFINITE the context may only be destroyed; mhd_last_error() explains;
+ *   - work is issued on the stream given at init; entry points that return host data
+ *     synchronise that stream, mhd_step does not.
+ */
+#ifndef MHD_H_
+#define MHD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MHD_API __attribute__((visibility("default")))
+#else
+#define MHD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MHD_OK = 0,
+  MHD_EINVAL = 1,     /* bad argument (size, index, null pointer, parameter out of range) */
+  MHD_ENOMEM = 2,     /* device allocation failed */
+  MHD_ECUDA = 3,      /* a CUDA call failed; see mhd_last_error */
+  MHD_ESTATE = 4,     /* call not valid in the current state (e.g. step before set_state) */
+  MHD_ENONFINITE = 5, /* an instance produced a non-finite speed or step: it stopped advancing */
+  MHD_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  MHD_EBUSY = 7       /* no free slot */
+} mhd_status;
+
+typedef enum {
+  MHD_FP64 = 0 /* IEEE double everywhere */
+} mhd_precision;
+
+typedef struct mhd_ctx mhd_ctx;
+
+typedef struct {
+  int32_t n;          /* grid points per axis: a power of two, 16 <= n <= 1024 */
+  int32_t batch;      /* independent instances sharing n, >= 1 */
+  int32_t precision;  /* mhd_precision */
+  int32_t reserved0;  /* must be 0 */
+  double dt;          /* > 0: fixed step; <= 0: CFL step */
+  double cfl_adv;     /* advective Courant number (default 0.2 when <= 0) */
+  double cfl_visc;    /* diffusive number (default 0.5 when <= 0) */
+  void *stream;       /* cudaStream_t the library issues all work on; NULL = legacy default */
+  /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/Free.
+   * dev_alloc returns NULL on failure; blocks must be at least 256-byte aligned. */
+  void *(*dev_alloc)(size_t bytes, void *user);
+  void (*dev_free)(void *ptr, void *user);
+  void *alloc_user;
+} mhd_params;
+
+/* Physical parameters of one instance (paper, section "Normalisation of the MHD equations":
+ * Cs = u0 / M_s with u0 = 1; Re = 1 / nu and R_m = 1 / eta for unit density and length). */
+typedef struct {
+  double nu;  /* kinematic viscosity (mu of Eq. velocity), >= 0 */
+  double eta; /* magnetic diffusivity, >= 0 */
+  double cs;  /* isothermal sound speed, > 0 */
+} mhd_phys;
+
+/* Scalar diagnostics of one instance; <.> is the average over the N^3 grid points
+ * (paper, section "Governing equations": mean speed, Mach numbers, Alfven speed; energies of
+ * section "for magnetohydrodynamic flow"). */
+typedef struct {
+  double t;          /* simulated time */
+  double dt;         /* step size of the last step (0 before the first) */
+  double ke;         /* <rho |u|^2 / 2> */
+  double me;         /* <|B|^2 / 2> */
+  double eint;       /* <Cs^2 rho ln rho>: ke + me + eint is conserved in the ideal limit */
+  double cross_hel;  /* <u . B> */
+  double mean_speed; /* <|u|> */
+  double mean_bmag;  /* <|B|> */
+  double smax;       /* max over the grid of |u| + sqrt(Cs^2 + |B|^2 / rho) */
+  double mean_rho;   /* <rho>, the k = 0 density mode */
+  double mean_m[3];  /* <rho u> */
+  double mean_b[3];  /* <B> */
+  double divb_rms;   /* sqrt(<(div B)^2>), spectral */
+  double mach_s;     /* <|u|> / Cs */
+  double v_a;        /* Alfven speed <|B|> / sqrt(<rho>) (Heaviside-Lorentz units) */
+  double mach_a;     /* <|u|> / v_a (0 when v_a = 0) */
+  int64_t step;      /* steps taken since set_state */
+  int32_t status;    /* MHD_OK, or MHD_ENONFINITE once the instance stopped advancing */
+  int32_t reserved;
+} mhd_diag;
+
+/* Bytes of device memory a context of this size holds (state, history, two scratch buffers). */
+MHD_API size_t mhd_footprint_bytes(int32_t n, int32_t precision, int32_t batch);
+
+/* Create a context for `p->batch` instances of size `p->n`; `phys` points to p->batch entries.
+ * Allocates all device memory up front.  MHD_EINVAL on bad sizes or parameters, MHD_ENOMEM when
+ * the allocation fails (nothing is leaked), MHD_ECUDA on other CUDA failures. */
+MHD_API mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out);
+
+/* Release everything the context holds (NULL is a no-op). */
+MHD_API void mhd_destroy(mhd_ctx *ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next call on it. */
+MHD_API const char *mhd_last_error(const mhd_ctx *ctx);
+
+/* Set instance `inst` from real-space rho (N^3), u (3 N^3) and B (3 N^3).  The evolved momentum
+ * is m = rho u; every field is transformed and projected onto the 2/3-rule modes.  Resets the
+ * instance's time, step count, history and status.  Synchronises the stream. */
+MHD_API mhd_status mhd_set_state(mhd_ctx *ctx, int32_t inst, const double *rho, const double *u,
+                         const double *b, int32_t on_device);
+
+/* Real-space rho (N^3), m = rho u (3 N^3) and B (3 N^3) of instance `inst`.  Synchronises. */
+MHD_API mhd_status mhd_get_state(mhd_ctx *ctx, int32_t inst, double *rho, double *m, double *b,
+                         int32_t on_device);
+
+/* Real-space right-hand side of instance `inst` at its current state (the inverse transform of
+ * the dealiased RHS spectra): d rho/dt (N^3), d m/dt (3 N^3), d B/dt (3 N^3).  The state, the
+ * history and the time are unchanged.  Synchronises. */
+MHD_API mhd_status mhd_rhs(mhd_ctx *ctx, int32_t inst, double *drho, double *dm, double *db,
+                   int32_t on_device);
+
+/* Spectrum of state field `field` (0 rho, 1-3 m, 4-6 B) of instance `inst` in the full
+ * half-complex layout: complex (re, im) pairs at [kz][ky][kx] for kz, ky in FFT index order
+ * 0..N-1 and kx = 0..N/2, i.e. N * N * (N/2 + 1) pairs; modes outside the 2/3 rule are 0.
+ * Synchronises. */
+MHD_API mhd_status mhd_get_spectrum(mhd_ctx *ctx, int32_t inst, int32_t field, double *out, int32_t on_device);
+
+/* Advance every instance `nsteps` steps.  Asynchronous: returns once the work is queued.  An
+ * instance whose CFL speed or step becomes non-finite stops advancing and reports
+ * MHD_ENONFINITE in its diagnostics and from mhd_synchronize. */
+MHD_API mhd_status mhd_step(mhd_ctx *ctx, int32_t nsteps);
+
+/* Wait for queued work; MHD_ENONFINITE if any instance stopped advancing. */
+MHD_API mhd_status mhd_synchronize(mhd_ctx *ctx);
+
+/* Diagnostics of instance `inst` at its current state.  Synchronises. */
+MHD_API mhd_status mhd_diagnostics(mhd_ctx *ctx, int32_t inst, mhd_diag *out);
+
+/* Checkpoint support.  The restartable state of an instance is its state spectra, its history
+ * (the previous step's RHS spectra), and (t, dt_prev, step).  Both calls move
+ * mhd_checkpoint_doubles(ctx) doubles through `buf` (host or device), in a layout private to the
+ * library that mhd_restore accepts for the same n and precision.  Both synchronise. */
+MHD_API size_t mhd_checkpoint_doubles(const mhd_ctx *ctx);
+MHD_API mhd_status mhd_checkpoint(mhd_ctx *ctx, int32_t inst, double *buf, int32_t on_device);
+MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, int32_t on_device);
+
+/* Per-kernel device time of mhd_step, for measurement.  While profiling is on, every kernel that
+ * mhd_step launches is bracketed by CUDA events on the context's stream.  mhd_profile(ctx, 1)
+ * clears the totals and starts recording, mhd_profile(ctx, 0) stops.  mhd_profile_read
+ * synchronises and fills up to `max` entries (name, summed milliseconds, launch count), one per
+ * kernel kind, and stores how many it wrote in *count. */
+typedef struct {
+  const char *name; /* static string owned by the library */
+  double total_ms;
+  int64_t launches;
+} mhd_kernel_time;
+MHD_API mhd_status mhd_profile(mhd_ctx *ctx, int32_t enable);
+MHD_API mhd_status mhd_profile_read(mhd_ctx *ctx, mhd_kernel_time *out, int32_t max, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHD_H_ */

@@ -1,0 +1,184 @@
+// fft_device.cuh -- device building blocks: complex arithmetic, small DFTs in registers, and the
+// Stockham pencil FFT executed by a group of N/8 threads on a pencil held in shared memory.
+//
+// Transform convention (both directions unscaled):  X[k] = sum_j x[j] exp(DIR * 2 pi i j k / N)
+// with DIR = -1 for the forward and +1 for the inverse transform.
+#pragma once
+
+#include "mhd_internal.h"
+
+namespace mhd {
+
+__device__ __forceinline__ cplx64 c_add(cplx64 a, cplx64 b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx64 c_sub(cplx64 a, cplx64 b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx64 c_scale(cplx64 a, double s) { return {a.re * s, a.im * s}; }
+// a * w
+__device__ __forceinline__ cplx64 c_mul(cplx64 a, cplx64 w) {
+  return {a.re * w.re - a.im * w.im, a.re * w.im + a.im * w.re};
+}
+// a * conj(w)
+__device__ __forceinline__ cplx64 c_mulc(cplx64 a, cplx64 w) {
+  return {a.re * w.re + a.im * w.im, a.im * w.re - a.re * w.im};
+}
+// a * (DIR i)
+template <int DIR>
+__device__ __forceinline__ cplx64 c_mul_i(cplx64 a) {
+  return DIR > 0 ? cplx64{-a.im, a.re} : cplx64{a.im, -a.re};
+}
+
+// NaN-propagating maximum (a non-finite CFL speed must reach the step-size kernel).
+__device__ __forceinline__ double nan_max(double a, double b) {
+  if (a != a) return a;
+  if (b != b) return b;
+  return a > b ? a : b;
+}
+
+// ---- DFTs of length 2, 4, 8 on registers, natural order in and out ----
+
+template <int DIR>
+__device__ __forceinline__ void dft2(cplx64 *v) {
+  const cplx64 a = v[0], b = v[1];
+  v[0] = c_add(a, b);
+  v[1] = c_sub(a, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(cplx64 *v) {
+  const cplx64 s0 = c_add(v[0], v[2]), d0 = c_sub(v[0], v[2]);
+  const cplx64 s1 = c_add(v[1], v[3]), d1 = c_mul_i<DIR>(c_sub(v[1], v[3]));
+  v[0] = c_add(s0, s1);
+  v[2] = c_sub(s0, s1);
+  v[1] = c_add(d0, d1);
+  v[3] = c_sub(d0, d1);
+}
+
+// Length 8 by one decimation-in-frequency split: b_j = a_j + a_{j+4} feeds the even outputs,
+// c_j = (a_j - a_{j+4}) W8^j the odd ones, each through a length-4 DFT.
+template <int DIR>
+__device__ __forceinline__ void dft8(cplx64 *v) {
+  constexpr double h = 0.70710678118654752440;  // sqrt(2) / 2
+  cplx64 b[4], c[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    b[j] = c_add(v[j], v[j + 4]);
+    c[j] = c_sub(v[j], v[j + 4]);
+  }
+  // W8^1 = h (1 + DIR i), W8^2 = DIR i, W8^3 = h (-1 + DIR i)
+  c[1] = cplx64{h * (c[1].re - DIR * c[1].im), h * (c[1].im + DIR * c[1].re)};
+  c[2] = c_mul_i<DIR>(c[2]);
+  c[3] = cplx64{h * (-c[3].re - DIR * c[3].im), h * (-c[3].im + DIR * c[3].re)};
+  dft4<DIR>(b);
+  dft4<DIR>(c);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[2 * m] = b[m];
+    v[2 * m + 1] = c[m];
+  }
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft_small(cplx64 *v) {
+  if constexpr (R == 8) dft8<DIR>(v);
+  else if constexpr (R == 4) dft4<DIR>(v);
+  else dft2<DIR>(v);
+}
+
+// ---- Stockham pencil FFT ----
+//
+// The transform of length N = product of radices (8 while at least 8 points remain, then 4 or
+// 2) runs as a sequence of stages.  Before a stage, sub-transforms of length NS are complete;
+// butterfly j (0 <= j < N/R) gathers x[j + r N/R] (r < R), multiplies element r by the twiddle
+// W_{NS R}^{r (j mod NS)}, applies a length-R DFT and scatters the results to
+// (j div NS) NS R + (j mod NS) + r NS.  After the last stage the pencil holds X in natural order
+// (the auto-sorting formulation of Cooley-Tukey by Stockham).  Each of the N/8 threads of a
+// group owns 8 / R butterflies per stage, so it always holds 8 values.  `tw[m]` = W_N^m =
+// exp(-2 pi i m / N); the inverse uses its conjugate.
+//
+// Every thread of the block must call this (it contains __syncthreads); threads with
+// `active == false` only take part in the barriers.
+template <int N, int DIR, int NS>
+__device__ __forceinline__ void stockham_stages(cplx64 *buf, int t, bool active,
+                                                const cplx64 *__restrict__ tw) {
+  if constexpr (NS < N) {
+    constexpr int R = (N / NS >= 8) ? 8 : N / NS;
+    constexpr int NB = 8 / R;
+    constexpr int TPP = N / 8;
+    constexpr int TWSTEP = N / (NS * R);
+    cplx64 v[8];
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int j = t + b * TPP;
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          cplx64 x = buf[j + r * (N / R)];
+          if (NS > 1 && r > 0) {
+            const cplx64 w = tw[r * k * TWSTEP];
+            x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
+          }
+          v[b * R + r] = x;
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        dft_small<R, DIR>(v + b * R);
+        const int j = t + b * TPP;
+        const int k = j % NS;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[base + r * NS] = v[b * R + r];
+      }
+    }
+    __syncthreads();
+    stockham_stages<N, DIR, NS * R>(buf, t, active, tw);
+  }
+}
+
+template <int N, int DIR>
+__device__ __forceinline__ void pencil_fft(cplx64 *buf, int t, bool active, const cplx64 *__restrict__ tw) {
+  stockham_stages<N, DIR, 1>(buf, t, active, tw);
+}
+
+// FFT index of kept index j (0..2K) along a truncated axis: j for j <= K, else j - (2K+1) + N.
+__device__ __forceinline__ int kept_to_fft(int j, int K, int n) { return j <= K ? j : j - (2 * K + 1) + n; }
+// Signed wavenumber of kept index j.
+__device__ __forceinline__ int kept_wave(int j, int K) { return j <= K ? j : j - (2 * K + 1); }
+
+// Block-wide reductions with a fixed combination order (deterministic for a fixed block size).
+// `red` must hold blockDim.x / 32 doubles; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+  }
+  return s;
+}
+
+__device__ __forceinline__ double block_nan_max(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = red[0];
+    for (int i = 1; i < nw; ++i) s = nan_max(s, red[i]);
+  }
+  return s;
+}
+
+}  // namespace mhd

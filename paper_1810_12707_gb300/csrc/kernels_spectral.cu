@@ -1,0 +1,265 @@
+// kernels_spectral.cu -- pointwise work in Fourier space: RHS assembly and the Adams-Bashforth
+// update, the step size, and the spectral side of the diagnostics.
+//
+// RHS of the 3D system (paper, section "Three dimensional numerical tests", Eqs. density,
+// velocity, Bfield) at a kept wavevector k, with T_ij, E = u x B and u the forward-transformed
+// products (scaled here by N^-3) and rho, m, B the state:
+//   rho_t = -i k . m
+//   m_t,i = -i sum_j k_j T_ij - i k_i Cs^2 rho - nu |k|^2 u_i
+//   B_t   =  i k x E - eta |k|^2 B
+// Every stored mode lies inside the 2/3-rule set, so the dealiasing mask is 1 on all of them.
+#include <math.h>
+
+#include "fft_device.cuh"
+
+namespace mhd {
+
+__global__ void assemble_kernel(const cplx64 *__restrict__ flux, cplx64 *__restrict__ state,
+                                cplx64 *__restrict__ hist, cplx64 *__restrict__ rhs_out,
+                                const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
+                                int mode, int K, int batch, double inv_n3) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const size_t total = spec * batch;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(idx / spec);
+    const size_t m = idx - (size_t)inst * spec;
+    if (mode == 1 && coef[inst].skip) continue;
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    const int jy = (int)(t % NK), jz = (int)(t / NK);
+    const double kx = kxi, ky = kept_wave(jy, K), kz = kept_wave(jz, K);
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
+
+    const cplx64 *S = state + (size_t)inst * 7 * spec + m;
+    const cplx64 *F = flux + (size_t)inst * 12 * spec + m;
+    cplx64 y[7], f[12];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
+    const cplx64 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+    const cplx64 Ex = f[6], Ey = f[7], Ez = f[8];
+
+    cplx64 r[7];
+    // continuity: -i k . m
+    {
+      const cplx64 s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+      r[0] = cplx64{s.im, -s.re};
+    }
+    // momentum
+    {
+      const double kk[3] = {kx, ky, kz};
+      const cplx64 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cplx64 divT = {kx * T[a][0].re + ky * T[a][1].re + kz * T[a][2].re,
+                             kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im};
+        const cplx64 g = {divT.re + kk[a] * cs2 * y[0].re, divT.im + kk[a] * cs2 * y[0].im};
+        const cplx64 u = f[9 + a];
+        r[1 + a] = cplx64{g.im - nu * k2 * u.re, -g.re - nu * k2 * u.im};
+      }
+    }
+    // induction: i k x E - eta k^2 B
+    {
+      const cplx64 c[3] = {{ky * Ez.re - kz * Ey.re, ky * Ez.im - kz * Ey.im},
+                           {kz * Ex.re - kx * Ez.re, kz * Ex.im - kx * Ez.im},
+                           {kx * Ey.re - ky * Ex.re, kx * Ey.im - ky * Ex.im}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        r[4 + a] = cplx64{-c[a].im - eta * k2 * y[4 + a].re, c[a].re - eta * k2 * y[4 + a].im};
+    }
+
+    if (mode == 0) {
+      cplx64 *R = rhs_out + (size_t)inst * 7 * spec + m;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) R[q * spec] = r[q];
+    } else {
+      const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
+      cplx64 *Sw = state + (size_t)inst * 7 * spec + m;
+      cplx64 *H = hist + (size_t)inst * 7 * spec + m;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        cplx64 inc = {a1 * r[q].re, a1 * r[q].im};
+        if (a0 != 0.0) {
+          const cplx64 h = H[q * spec];
+          inc.re += a0 * h.re;
+          inc.im += a0 * h.im;
+        }
+        Sw[q * spec] = cplx64{y[q].re + dt * inc.re, y[q].im + dt * inc.im};
+        H[q * spec] = r[q];
+      }
+    }
+  }
+}
+
+// One block per instance: maximum of the CFL partials, the step size, the Adams-Bashforth
+// coefficients of this step, and the advance of the time state.
+__global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
+                               const PhysDev *__restrict__ phys, TimeState *__restrict__ ts,
+                               StepCoef *__restrict__ coef, int n, int K, double dt_fixed,
+                               double cfl_adv, double cfl_visc) {
+  __shared__ double red[32];
+  const int inst = blockIdx.x;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) m = nan_max(m, part[(size_t)inst * nparts + i]);
+  m = block_nan_max(m, red);
+  if (threadIdx.x != 0) return;
+  TimeState s = ts[inst];
+  StepCoef c = {0.0, 0.0, 0.0, 1, 0};
+  if (s.status == 0) {
+    double dt;
+    if (dt_fixed > 0.0) {
+      dt = dt_fixed;
+    } else {
+      const double dx = 2.0 * M_PI / (double)n;
+      dt = cfl_adv * dx / m;
+      const double diff = phys[inst].nu > phys[inst].eta ? phys[inst].nu : phys[inst].eta;
+      if (diff > 0.0 && K > 0) {
+        const double dtv = cfl_visc / (diff * (double)K * (double)K);
+        if (dtv < dt) dt = dtv;
+      }
+    }
+    if (!isfinite(m) || !isfinite(dt) || dt <= 0.0) {
+      s.status = 5;  // MHD_ENONFINITE
+    } else {
+      c.dt = dt;
+      c.skip = 0;
+      if (s.step > 0) {
+        const double r = dt / s.dt_prev;
+        c.a1 = 1.0 + 0.5 * r;
+        c.a0 = -0.5 * r;
+      } else {
+        c.a1 = 1.0;
+        c.a0 = 0.0;
+      }
+      s.t += dt;
+      s.dt_prev = dt;
+      s.dt_last = dt;
+      s.step += 1;
+    }
+  }
+  ts[inst] = s;
+  coef[inst] = c;
+}
+
+// One block: reduce the diagnostic partials of one instance in a fixed order and add the
+// spectral terms.  out: [0] ke [1] me [2] eint [3] cross_hel [4] mean_speed [5] mean_bmag
+// [6] smax [7] mean_rho [8..10] mean_m [11..13] mean_b [14] divb_rms [15] t [16] dt_last
+// [17] step [18] status.
+__global__ void diag_finish_kernel(const double *__restrict__ part, int nparts,
+                                   const cplx64 *__restrict__ state, const PhysDev *__restrict__ phys,
+                                   const TimeState *__restrict__ ts, double *__restrict__ out, int n,
+                                   int K) {
+  __shared__ double red[32];
+  const double inv_n3 = 1.0 / ((double)n * n * n);
+  for (int q = 0; q < 7; ++q) {
+    double v = 0.0;
+    if (q < 6) {
+      for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(size_t)i * 8 + q];
+      v = block_sum(v, red);
+    } else {
+      for (int i = threadIdx.x; i < nparts; i += blockDim.x) v = nan_max(v, part[(size_t)i * 8 + q]);
+      v = block_nan_max(v, red);
+    }
+    if (threadIdx.x == 0) out[q] = q < 6 ? v * inv_n3 : v;
+  }
+  // sum over the full spectrum of |k . B|^2 (kx > 0 counted twice for the mirrored half)
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  double d = 0.0;
+  for (size_t m = threadIdx.x; m < spec; m += blockDim.x) {
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    const double kx = kxi, ky = kept_wave((int)(t % NK), K), kz = kept_wave((int)(t / NK), K);
+    const cplx64 bx = state[4 * spec + m], by = state[5 * spec + m], bz = state[6 * spec + m];
+    const double re = kx * bx.re + ky * by.re + kz * bz.re;
+    const double im = kx * bx.im + ky * by.im + kz * bz.im;
+    d += (kxi > 0 ? 2.0 : 1.0) * (re * re + im * im);
+  }
+  d = block_sum(d, red);
+  if (threadIdx.x == 0) {
+    out[7] = state[0].re;
+    for (int a = 0; a < 3; ++a) {
+      out[8 + a] = state[(1 + a) * spec].re;
+      out[11 + a] = state[(4 + a) * spec].re;
+    }
+    out[14] = sqrt(d);
+    out[15] = ts->t;
+    out[16] = ts->dt_last;
+    out[17] = (double)ts->step;
+    out[18] = (double)ts->status;
+  }
+}
+
+// Truncated spectrum -> full half-complex layout [N][N][N/2+1], zeros outside the kept set.
+__global__ void expand_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict__ out, int n, int K) {
+  const int H = n / 2 + 1, NX = K + 1;
+  const size_t total = (size_t)n * n * H;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % H);
+    const size_t t = i / H;
+    const int fy = (int)(t % n), fz = (int)(t / n);
+    // FFT index -> kept index (or -1)
+    const int jy = fy <= K ? fy : (fy >= n - K ? fy - n + 2 * K + 1 : -1);
+    const int jz = fz <= K ? fz : (fz >= n - K ? fz - n + 2 * K + 1 : -1);
+    cplx64 v = {0.0, 0.0};
+    if (kx <= K && jy >= 0 && jz >= 0) v = in[((size_t)jz * (2 * K + 1) + jy) * NX + kx];
+    out[i] = v;
+  }
+}
+
+__global__ void status_any_kernel(const TimeState *__restrict__ ts, int batch, int32_t *flag) {
+  int any = 0;
+  for (int i = threadIdx.x; i < batch; i += blockDim.x) any |= ts[i].status != 0;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) *flag = any;
+}
+
+// ------------------------------------------------------------------------------------------
+
+static unsigned grid_for(size_t total, int threads) {
+  size_t b = (total + threads - 1) / threads;
+  const size_t cap = 152 * 16;  // enough blocks to fill every SM several times; grid-stride beyond
+  if (b > cap) b = cap;
+  return (unsigned)(b == 0 ? 1 : b);
+}
+
+cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                            cudaStream_t s) {
+  const size_t total = d.spec * d.batch;
+  const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
+  assemble_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, state, hist, rhs_out, phys, coef, mode, d.k,
+                                                       d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys, TimeState *ts,
+                           StepCoef *coef, const Dims &d, double dt_fixed, double cfl_adv,
+                           double cfl_visc, cudaStream_t s) {
+  step_dt_kernel<<<d.batch, 256, 0, s>>>(smax_part, nparts, phys, ts, coef, d.n, d.k, dt_fixed, cfl_adv,
+                                         cfl_visc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state, const PhysDev *phys,
+                               const TimeState *ts, double *out, const Dims &d, cudaStream_t s) {
+  diag_finish_kernel<<<1, 1024, 0, s>>>(part, nparts, state, phys, ts, out, d.n, d.k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_spectrum(const cplx64 *in, cplx64 *out, const Dims &d, cudaStream_t s) {
+  const size_t total = (size_t)d.n * d.n * (d.n / 2 + 1);
+  expand_kernel<<<grid_for(total, 256), 256, 0, s>>>(in, out, d.n, d.k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status_any(const TimeState *ts, int batch, int32_t *flag, cudaStream_t s) {
+  status_any_kernel<<<1, 256, 0, s>>>(ts, batch, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,421 @@
+// kernels_x.cu -- passes along the contiguous x axis, where real-space data exists.
+//
+// Two real rows of the same field are transformed together as one complex pencil
+// z = f_row0 + i f_row1.  Inverse (half spectrum -> real rows): with the truncated half spectra
+// X0, X1 (kx = 0..K), Z[k] = X0[k] + i X1[k] and Z[N-k] = conj(X0[k]) + i conj(X1[k]) for
+// 1 <= k <= K, Z[0] = Re X0[0] + i Re X1[0] (the Hermitian part), zero elsewhere; the real parts
+// of the inverse FFT are row 0 and the imaginary parts row 1.  Forward (real rows -> half
+// spectra): Z = FFT(row0 + i row1), X0[k] = (Z[k] + conj Z[N-k]) / 2 and
+// X1[k] = -i (Z[k] - conj Z[N-k]) / 2, kept for k = 0..K only.
+//
+// The flux kernel is the fused pass of the method: the 7 state fields of a block's rows are
+// brought to the grid, the 12 products of the RHS are formed pointwise in shared memory (no
+// real-space array ever reaches HBM), and their forward transforms leave as truncated half
+// spectra.  Rows are indexed r = z*N + y; a block owns PAIRS consecutive row pairs.
+#include "fft_device.cuh"
+#include "launch_util.cuh"
+
+namespace mhd {
+
+namespace {
+
+constexpr int kMaxThreads = 384;
+
+constexpr int pairs_for(int n) { return (n / 8) >= 16 ? 1 : 16 / (n / 8); }
+
+constexpr int threads_for(int n, int pencils) {
+  // groups of N/8 threads, at most kMaxThreads threads, a multiple of 32
+  int tpp = n / 8;
+  int g = kMaxThreads / tpp;
+  if (g > pencils) g = pencils;
+  int t = g * tpp;
+  return (t + 31) / 32 * 32;
+}
+
+// Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
+// N/8 threads of the block taking one pencil at a time.
+template <int N, int DIR, typename Ptr>
+__device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const cplx64 *__restrict__ tw) {
+  constexpr int TPP = N / 8;
+  const int G = blockDim.x / TPP;
+  const int g = threadIdx.x / TPP, t = threadIdx.x - g * TPP;
+  for (int base = 0; base < np; base += G) {
+    const int id = base + g;
+    const bool active = g < G && id < np;
+    pencil_fft<N, DIR>(ptr(active ? id : 0), t, active, tw);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Fused flux pass
+// ------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict__ out,
+                              const PhysDev *__restrict__ phys, double *__restrict__ smax_part,
+                              int K, int blocks_per_inst, const cplx64 *__restrict__ tw) {
+  extern __shared__ cplx64 sm[];
+  __shared__ double red[32];
+  constexpr int P = N + 1;
+  constexpr int PAIRS = pairs_for(N);
+  constexpr size_t NN = (size_t)N * N;
+  const int NX = K + 1;
+  const int inst = blockIdx.x / blocks_per_inst;
+  const int bl = blockIdx.x - inst * blocks_per_inst;
+  const size_t row0 = (size_t)bl * PAIRS * 2;
+  const int nthr = blockDim.x;
+
+  // 1. load and pack the 7 state fields: pencil (p, f) at sm + (p * 12 + f) * P
+  for (int q = threadIdx.x; q < 7 * PAIRS * NX; q += nthr) {
+    const int k = q % NX;
+    const int r = q / NX;
+    const int f = r % 7, p = r / 7;
+    const cplx64 *src = in + ((size_t)(inst * 7 + f) * NN + row0 + 2 * p) * NX;
+    cplx64 *pen = sm + (p * 12 + f) * P;
+    const cplx64 x0 = src[k], x1 = src[NX + k];
+    if (k == 0) {
+      pen[0] = cplx64{x0.re, x1.re};
+    } else {
+      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
+      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+    }
+  }
+  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
+    const int z = q % (N - 2 * K - 1);
+    const int r = q / (N - 2 * K - 1);
+    const int f = r % 7, p = r / 7;
+    sm[(p * 12 + f) * P + K + 1 + z] = cplx64{0.0, 0.0};
+  }
+  __syncthreads();
+
+  // 2. inverse transforms of the 7 fields
+  fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
+
+  // 3. products on the grid (real part: row 0, imaginary part: row 1)
+  const double cs2 = phys[inst].cs * phys[inst].cs;
+  double smax = 0.0;
+  for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
+    const int p = q / N, j = q - p * N;
+    cplx64 *b = sm + p * 12 * P + j;
+    double v[2][7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) {
+      const cplx64 c = b[f * P];
+      v[0][f] = c.re;
+      v[1][f] = c.im;
+    }
+    double *bd = reinterpret_cast<double *>(b);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double rho = v[h][0];
+      const double mx = v[h][1], my = v[h][2], mz = v[h][3];
+      const double bx = v[h][4], by = v[h][5], bz = v[h][6];
+      const double ux = mx / rho, uy = my / rho, uz = mz / rho;
+      const double b2 = bx * bx + by * by + bz * bz;
+      const double hb = 0.5 * b2;
+      // component h of pencil f at this point is bd[2 * f * P + h]
+      bd[2 * 0 * P + h] = mx * ux + hb - bx * bx;   // T_xx
+      bd[2 * 1 * P + h] = my * uy + hb - by * by;   // T_yy
+      bd[2 * 2 * P + h] = mz * uz + hb - bz * bz;   // T_zz
+      bd[2 * 3 * P + h] = mx * uy - bx * by;        // T_xy
+      bd[2 * 4 * P + h] = mx * uz - bx * bz;        // T_xz
+      bd[2 * 5 * P + h] = my * uz - by * bz;        // T_yz
+      bd[2 * 6 * P + h] = uy * bz - uz * by;        // E_x
+      bd[2 * 7 * P + h] = uz * bx - ux * bz;        // E_y
+      bd[2 * 8 * P + h] = ux * by - uy * bx;        // E_z
+      bd[2 * 9 * P + h] = ux;
+      bd[2 * 10 * P + h] = uy;
+      bd[2 * 11 * P + h] = uz;
+      const double s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 / rho);
+      smax = nan_max(smax, s);
+    }
+  }
+  __syncthreads();
+
+  // 4. forward transforms of the 12 products
+  fft_pencils<N, -1>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+
+  // 5. unpack and store the kept half spectra
+  for (int q = threadIdx.x; q < 12 * PAIRS * NX; q += nthr) {
+    const int k = q % NX;
+    const int r = q / NX;
+    const int f = r % 12, p = r / 12;
+    const cplx64 *pen = sm + (p * 12 + f) * P;
+    const cplx64 z = pen[k], zc = pen[(N - k) & (N - 1)];
+    cplx64 *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
+    dst[k] = cplx64{0.5 * (z.re + zc.re), 0.5 * (z.im - zc.im)};
+    dst[NX + k] = cplx64{0.5 * (z.im + zc.im), 0.5 * (zc.re - z.re)};
+  }
+
+  const double m = block_nan_max(smax, red);
+  if (threadIdx.x == 0) smax_part[(size_t)inst * blocks_per_inst + bl] = m;
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward x transform of an initial state (m = rho u formed first)
+// ------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__restrict__ rho, const double *__restrict__ u,
+                             const double *__restrict__ b, cplx64 *__restrict__ out, int K,
+                             const cplx64 *__restrict__ tw) {
+  extern __shared__ cplx64 sm[];
+  constexpr int P = N + 1;
+  constexpr int PAIRS = pairs_for(N);
+  constexpr size_t NN = (size_t)N * N, N3 = NN * N;
+  const int NX = K + 1;
+  const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
+  const int nthr = blockDim.x;
+
+  for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
+    const int p = q / N, j = q - p * N;
+    const size_t i0 = (row0 + 2 * p) * N + j, i1 = i0 + N;
+    const double r0 = rho[i0], r1 = rho[i1];
+    cplx64 *pen = sm + p * 7 * P + j;
+    pen[0] = cplx64{r0, r1};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      pen[(1 + d) * P] = cplx64{r0 * u[d * N3 + i0], r1 * u[d * N3 + i1]};
+      pen[(4 + d) * P] = cplx64{b[d * N3 + i0], b[d * N3 + i1]};
+    }
+  }
+  __syncthreads();
+  fft_pencils<N, -1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  for (int q = threadIdx.x; q < 7 * PAIRS * NX; q += nthr) {
+    const int k = q % NX;
+    const int r = q / NX;
+    const int f = r % 7, p = r / 7;
+    const cplx64 *pen = sm + (p * 7 + f) * P;
+    const cplx64 z = pen[k], zc = pen[(N - k) & (N - 1)];
+    cplx64 *dst = out + ((size_t)f * NN + row0 + 2 * p) * NX;
+    dst[k] = cplx64{0.5 * (z.re + zc.re), 0.5 * (z.im - zc.im)};
+    dst[NX + k] = cplx64{0.5 * (z.im + zc.im), 0.5 * (zc.re - z.re)};
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Inverse x transform to real rows
+// ------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__restrict__ in, double *__restrict__ out, int nf, int K,
+                             const cplx64 *__restrict__ tw) {
+  extern __shared__ cplx64 sm[];
+  constexpr int P = N + 1;
+  constexpr int PAIRS = pairs_for(N);
+  constexpr size_t NN = (size_t)N * N, N3 = NN * N;
+  const int NX = K + 1;
+  const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
+  const int nthr = blockDim.x;
+
+  for (int q = threadIdx.x; q < nf * PAIRS * NX; q += nthr) {
+    const int k = q % NX;
+    const int r = q / NX;
+    const int f = r % nf, p = r / nf;
+    const cplx64 *src = in + ((size_t)f * NN + row0 + 2 * p) * NX;
+    cplx64 *pen = sm + (p * nf + f) * P;
+    const cplx64 x0 = src[k], x1 = src[NX + k];
+    if (k == 0) {
+      pen[0] = cplx64{x0.re, x1.re};
+    } else {
+      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
+      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+    }
+  }
+  for (int q = threadIdx.x; q < nf * PAIRS * (N - 2 * K - 1); q += nthr) {
+    const int z = q % (N - 2 * K - 1);
+    const int r = q / (N - 2 * K - 1);
+    sm[r * P + K + 1 + z] = cplx64{0.0, 0.0};
+  }
+  __syncthreads();
+  fft_pencils<N, +1>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  for (int q = threadIdx.x; q < nf * PAIRS * N; q += nthr) {
+    const int j = q % N;
+    const int r = q / N;
+    const int f = r % nf, p = r / nf;
+    const cplx64 z = sm[(p * nf + f) * P + j];
+    const size_t i0 = f * N3 + (row0 + 2 * p) * N + j;
+    out[i0] = z.re;
+    out[i0 + N] = z.im;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Inverse x transform of the state with grid diagnostics
+// ------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__restrict__ in, const PhysDev *__restrict__ phys,
+                              double *__restrict__ part, int K, const cplx64 *__restrict__ tw) {
+  extern __shared__ cplx64 sm[];
+  __shared__ double red[32];
+  constexpr int P = N + 1;
+  constexpr int PAIRS = pairs_for(N);
+  constexpr size_t NN = (size_t)N * N;
+  const int NX = K + 1;
+  const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
+  const int nthr = blockDim.x;
+
+  for (int q = threadIdx.x; q < 7 * PAIRS * NX; q += nthr) {
+    const int k = q % NX;
+    const int r = q / NX;
+    const int f = r % 7, p = r / 7;
+    const cplx64 *src = in + ((size_t)f * NN + row0 + 2 * p) * NX;
+    cplx64 *pen = sm + (p * 7 + f) * P;
+    const cplx64 x0 = src[k], x1 = src[NX + k];
+    if (k == 0) {
+      pen[0] = cplx64{x0.re, x1.re};
+    } else {
+      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
+      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+    }
+  }
+  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
+    const int z = q % (N - 2 * K - 1);
+    const int r = q / (N - 2 * K - 1);
+    sm[r * P + K + 1 + z] = cplx64{0.0, 0.0};
+  }
+  __syncthreads();
+  fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+
+  const double cs2 = phys[0].cs * phys[0].cs;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double smax = 0.0;
+  for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
+    const int p = q / N, j = q - p * N;
+    const cplx64 *b = sm + p * 7 * P + j;
+    double v[2][7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) {
+      const cplx64 c = b[f * P];
+      v[0][f] = c.re;
+      v[1][f] = c.im;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double rho = v[h][0];
+      const double ux = v[h][1] / rho, uy = v[h][2] / rho, uz = v[h][3] / rho;
+      const double bx = v[h][4], by = v[h][5], bz = v[h][6];
+      const double u2 = ux * ux + uy * uy + uz * uz;
+      const double b2 = bx * bx + by * by + bz * bz;
+      acc[0] += 0.5 * rho * u2;
+      acc[1] += 0.5 * b2;
+      acc[2] += cs2 * rho * log(rho);
+      acc[3] += ux * bx + uy * by + uz * bz;
+      acc[4] += sqrt(u2);
+      acc[5] += sqrt(b2);
+      smax = nan_max(smax, sqrt(u2) + sqrt(cs2 + b2 / rho));
+    }
+  }
+  for (int i = 0; i < 6; ++i) {
+    const double s = block_sum(acc[i], red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 8 + i] = s;
+  }
+  const double m = block_nan_max(smax, red);
+  if (threadIdx.x == 0) {
+    part[(size_t)blockIdx.x * 8 + 6] = m;
+    part[(size_t)blockIdx.x * 8 + 7] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------------
+namespace {
+
+template <int N>
+cudaError_t flux_n(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *part, const Dims &d,
+                   const cplx64 *tw, cudaStream_t s) {
+  constexpr int PAIRS = pairs_for(N);
+  const int bpi = N * N / (2 * PAIRS);
+  const int threads = threads_for(N, 12 * PAIRS);
+  const size_t smem = (size_t)12 * PAIRS * (N + 1) * sizeof(cplx64);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_smem<flux_x_kernel<N>>((int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long long blocks = (long long)bpi * d.batch;
+  flux_x_kernel<N><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t set_n(const double *rho, const double *u, const double *b, cplx64 *out, const Dims &d,
+                  const cplx64 *tw, cudaStream_t s) {
+  constexpr int PAIRS = pairs_for(N);
+  const int blocks = N * N / (2 * PAIRS);
+  const int threads = threads_for(N, 7 * PAIRS);
+  const size_t smem = (size_t)7 * PAIRS * (N + 1) * sizeof(cplx64);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_smem<set_x_kernel<N>>((int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  set_x_kernel<N><<<blocks, threads, smem, s>>>(rho, u, b, out, d.k, tw);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cplx64 *tw, cudaStream_t s) {
+  constexpr int PAIRS = pairs_for(N);
+  const int blocks = N * N / (2 * PAIRS);
+  const int threads = threads_for(N, nf * PAIRS);
+  const size_t smem = (size_t)nf * PAIRS * (N + 1) * sizeof(cplx64);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_smem<get_x_kernel<N>>((int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  get_x_kernel<N><<<blocks, threads, smem, s>>>(in, out, nf, d.k, tw);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t diag_n(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,
+                   const cplx64 *tw, cudaStream_t s) {
+  constexpr int PAIRS = pairs_for(N);
+  const int blocks = N * N / (2 * PAIRS);
+  const int threads = threads_for(N, 7 * PAIRS);
+  const size_t smem = (size_t)7 * PAIRS * (N + 1) * sizeof(cplx64);
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_smem<diag_x_kernel<N>>((int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  diag_x_kernel<N><<<blocks, threads, smem, s>>>(in, phys, part, d.k, tw);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define MHD_DISPATCH_N(n, call)     \
+  switch (n) {                      \
+    case 16: { constexpr int N = 16; return call; }     \
+    case 32: { constexpr int N = 32; return call; }     \
+    case 64: { constexpr int N = 64; return call; }     \
+    case 128: { constexpr int N = 128; return call; }   \
+    case 256: { constexpr int N = 256; return call; }   \
+    case 512: { constexpr int N = 512; return call; }   \
+    case 1024: { constexpr int N = 1024; return call; } \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+int flux_x_blocks_per_instance(int n) { return n * n / (2 * pairs_for(n)); }
+int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
+
+cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
+                          const Dims &d, const cplx64 *tw, cudaStream_t s) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_part, d, tw, s)));
+}
+
+cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,
+                         const Dims &d, const cplx64 *tw, cudaStream_t s) {
+  MHD_DISPATCH_N(d.n, (set_n<N>(rho, u, b, out, d, tw, s)));
+}
+
+cudaError_t launch_get_x(const cplx64 *in, double *out, int nfields, const Dims &d,
+                         const cplx64 *tw, cudaStream_t s) {
+  MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s)));
+}
+
+cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,
+                          const cplx64 *tw, cudaStream_t s) {
+  MHD_DISPATCH_N(d.n, (diag_n<N>(in, phys, part, d, tw, s)));
+}
+
+}  // namespace mhd

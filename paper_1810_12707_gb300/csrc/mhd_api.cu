@@ -1,0 +1,561 @@
+// mhd_api.cu -- the C ABI (include/mhd.h): context, device memory, and the order of the passes.
+//
+// One time step of every instance (paper: pseudo-spectral RHS of section "Three dimensional
+// numerical tests" and the Adams-Bashforth step of section "Code G-MHD3D") is six kernels:
+//   1. inverse z   state S [b][7][kz'][ky'][kx]  -> W1 [b][7][z][ky'][kx]
+//   2. inverse y   W1                            -> W2 [b][7][z][y][kx]
+//   3. flux x      W2 (inverse x, 12 products, forward x; CFL partials) -> W1 [b][12][z][y][kx]
+//   4. step size   CFL partials -> dt, AB2 coefficients, time advance (per instance)
+//   5. forward y   W1 -> W2 [b][12][z][ky'][kx]
+//   6. forward z   W2 -> W1 [b][12][kz'][ky'][kx]
+//   7. assemble    W1 + S + H -> S (AB2 update), H (this step's RHS)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mhd.h"
+#include "mhd_internal.h"
+
+using mhd::cplx64;
+
+struct mhd_ctx {
+  mhd_params p;
+  mhd::Dims d;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double dt_fixed = 0.0, cfl_adv = 0.2, cfl_visc = 0.5;
+  std::vector<mhd_phys> phys_host;
+  std::vector<char> is_set;
+  mhd::PhysDev *phys = nullptr;
+  cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
+  size_t w1_len = 0, w2_len = 0;  // complex values
+  double *part = nullptr;
+  size_t part_len = 0;
+  mhd::TimeState *ts = nullptr;
+  mhd::StepCoef *coef = nullptr;
+  double *diag_out = nullptr;
+  int32_t *flag = nullptr;
+  std::vector<void *> allocs;
+  std::string err;
+  // profiling: events bracketing each launch of mhd_step, resolved at read time
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks;  // (kernel kind, index of the start event)
+  double prof_ms[8] = {0};
+  int64_t prof_count[8] = {0};
+};
+
+namespace {
+const char *const kKernelNames[7] = {"inverse_z", "inverse_y", "flux_x", "step_dt", "forward_y", "forward_z",
+                                     "assemble_ab2"};
+}
+
+namespace {
+
+mhd_status fail(mhd_ctx *c, mhd_status st, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(c, MHD_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                     \
+  } while (0)
+
+// Makes the context's device current for the duration of a call and restores the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool valid_n(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
+
+struct Sizes {
+  size_t S, W1, W2, part;
+};
+
+Sizes sizes_for(const mhd::Dims &d) {
+  const size_t n = d.n, nx = d.nx, nk = d.nk, b = d.batch;
+  Sizes s;
+  s.S = b * 7 * d.spec;
+  size_t w1 = b * 7 * n * nk * nx;
+  w1 = std::max(w1, b * 12 * n * n * nx);
+  w1 = std::max(w1, b * 12 * d.spec);
+  w1 = std::max(w1, (7 * n * n * n + 1) / 2);  // real 7 N^3 staging (set/get/rhs)
+  w1 = std::max(w1, n * n * (n / 2 + 1));      // expanded spectrum
+  size_t w2 = b * 7 * n * n * nx;
+  w2 = std::max(w2, b * 12 * n * nk * nx);
+  w2 = std::max(w2, 7 * d.spec);
+  s.W1 = w1;
+  s.W2 = w2;
+  s.part = std::max((size_t)b * mhd::flux_x_blocks_per_instance(d.n), (size_t)mhd::diag_x_blocks(d.n) * 8);
+  return s;
+}
+
+size_t footprint(const mhd::Dims &d) {
+  const Sizes s = sizes_for(d);
+  return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + s.part * sizeof(double) +
+         d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) + 64 * sizeof(double);
+}
+
+void *dalloc(mhd_ctx *c, size_t bytes) {
+  void *p = nullptr;
+  if (c->p.dev_alloc) {
+    p = c->p.dev_alloc(bytes, c->p.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+void free_all(mhd_ctx *c) {
+  for (void *p : c->allocs) {
+    if (c->p.dev_free) c->p.dev_free(p, c->p.alloc_user);
+    else cudaFree(p);
+  }
+  c->allocs.clear();
+}
+
+// W_N^m = exp(-2 pi i m / N) for m < N from first-octant values and exact symmetries, so that
+// W^{N/4} = -i, W^{N/2} = -1 and W^{3N/4} = i hold exactly.
+std::vector<cplx64> twiddles(int n) {
+  const int q4 = n / 4, q8 = n / 8;
+  std::vector<long double> C(q8 + 1), Sn(q8 + 1);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int r = 0; r <= q8; ++r) {
+    C[r] = cosl(two_pi * r / n);
+    Sn[r] = sinl(two_pi * r / n);
+  }
+  C[0] = 1.0L;
+  Sn[0] = 0.0L;
+  std::vector<cplx64> w(n);
+  for (int m = 0; m < n; ++m) {
+    const int quad = m / q4, r = m % q4;
+    double cs, sn;
+    if (r <= q8) {
+      cs = (double)C[r];
+      sn = (double)Sn[r];
+    } else {
+      cs = (double)Sn[q4 - r];
+      sn = (double)C[q4 - r];
+    }
+    double c2 = cs, s2 = sn;  // rotate by quad quarter turns: angle + quad * pi/2
+    if (quad == 1) { c2 = -sn; s2 = cs; }
+    if (quad == 2) { c2 = -cs; s2 = -sn; }
+    if (quad == 3) { c2 = sn; s2 = -cs; }
+    w[m] = cplx64{c2, -s2};
+  }
+  return w;
+}
+
+mhd_status check_inst(mhd_ctx *c, int inst) {
+  if (!c) return MHD_EINVAL;
+  if (inst < 0 || inst >= c->d.batch) return fail(c, MHD_EINVAL, "instance %d out of range [0, %d)", inst, c->d.batch);
+  return MHD_OK;
+}
+
+mhd::Dims one(const mhd_ctx *c) {
+  mhd::Dims d = c->d;
+  d.batch = 1;
+  return d;
+}
+
+// inverse z then inverse y of 7 fields of one instance: S-layout `src` -> W2 [7][z][y][kx]
+mhd_status inverse_zy(mhd_ctx *c, const cplx64 *src) {
+  const mhd::Dims &d = c->d;
+  CK(mhd::launch_col_inverse(src, c->W1, d.n, 7, d.nk * d.nx, c->tw, c->stream));
+  CK(mhd::launch_col_inverse(c->W1, c->W2, d.n, 7 * d.n, d.nx, c->tw, c->stream));
+  return MHD_OK;
+}
+
+mhd_status copy_out(mhd_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return MHD_OK;
+}
+
+// Inverse-transform 7 truncated spectra (S layout) of one instance into real rho/m/B outputs.
+mhd_status spectra_to_real(mhd_ctx *c, const cplx64 *src, double *a, double *b3, double *c3, int on_device) {
+  const size_t n3 = (size_t)c->d.n * c->d.n * c->d.n;
+  mhd_status st = inverse_zy(c, src);
+  if (st) return st;
+  double *real = reinterpret_cast<double *>(c->W1);
+  CK(mhd::launch_get_x(c->W2, real, 7, one(c), c->tw, c->stream));
+  if ((st = copy_out(c, a, real, n3 * sizeof(double), on_device))) return st;
+  if ((st = copy_out(c, b3, real + n3, 3 * n3 * sizeof(double), on_device))) return st;
+  if ((st = copy_out(c, c3, real + 4 * n3, 3 * n3 * sizeof(double), on_device))) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mhd_footprint_bytes(int32_t n, int32_t precision, int32_t batch) {
+  if (!valid_n(n) || batch < 1 || precision != MHD_FP64) return 0;
+  return footprint(mhd::make_dims(n, batch));
+}
+
+const char *mhd_last_error(const mhd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void mhd_destroy(mhd_ctx *ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    free_all(ctx);
+  }
+  delete ctx;
+}
+
+mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
+  if (!out) return MHD_EINVAL;
+  *out = nullptr;
+  if (!p || !phys) return MHD_EINVAL;
+  if (!valid_n(p->n) || p->batch < 1 || p->precision != MHD_FP64 || p->reserved0 != 0) return MHD_EINVAL;
+  if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return MHD_EINVAL;
+  for (int i = 0; i < p->batch; ++i) {
+    if (!(phys[i].nu >= 0.0) || !(phys[i].eta >= 0.0) || !(phys[i].cs > 0.0) || !isfinite(phys[i].nu) ||
+        !isfinite(phys[i].eta) || !isfinite(phys[i].cs))
+      return MHD_EINVAL;
+  }
+  if (!(isfinite(p->dt))) return MHD_EINVAL;
+  mhd_ctx *c = new (std::nothrow) mhd_ctx;
+  if (!c) return MHD_ENOMEM;
+  c->p = *p;
+  c->d = mhd::make_dims(p->n, p->batch);
+  c->stream = (cudaStream_t)p->stream;
+  c->dt_fixed = p->dt > 0.0 ? p->dt : 0.0;
+  c->cfl_adv = p->cfl_adv > 0.0 ? p->cfl_adv : 0.2;
+  c->cfl_visc = p->cfl_visc > 0.0 ? p->cfl_visc : 0.5;
+  c->phys_host.assign(phys, phys + p->batch);
+  c->is_set.assign(p->batch, 0);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return MHD_ECUDA;
+  }
+  const Sizes s = sizes_for(c->d);
+  c->w1_len = s.W1;
+  c->w2_len = s.W2;
+  c->part_len = s.part;
+  bool ok = (c->S = (cplx64 *)dalloc(c, s.S * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->H = (cplx64 *)dalloc(c, s.S * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->W1 = (cplx64 *)dalloc(c, s.W1 * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->W2 = (cplx64 *)dalloc(c, s.W2 * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->tw = (cplx64 *)dalloc(c, (size_t)c->d.n * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
+  ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
+  ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
+  ok = ok && (c->phys = (mhd::PhysDev *)dalloc(c, p->batch * sizeof(mhd::PhysDev))) != nullptr;
+  ok = ok && (c->diag_out = (double *)dalloc(c, 32 * sizeof(double))) != nullptr;
+  ok = ok && (c->flag = (int32_t *)dalloc(c, 4 * sizeof(int32_t))) != nullptr;
+  if (!ok) {
+    free_all(c);
+    delete c;
+    return MHD_ENOMEM;
+  }
+  std::vector<mhd::PhysDev> pd(p->batch);
+  for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs};
+  const std::vector<cplx64> w = twiddles(c->d.n);
+  cudaError_t e = cudaMemcpyAsync(c->phys, pd.data(), pd.size() * sizeof(mhd::PhysDev), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w.data(), w.size() * sizeof(cplx64), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return MHD_ECUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const double *u, const double *b,
+                         int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!rho || !u || !b) return fail(c, MHD_EINVAL, "null input");
+  DeviceGuard g(c->device);
+  const mhd::Dims &d = c->d;
+  const size_t n3 = (size_t)d.n * d.n * d.n;
+  const double *r = rho, *uu = u, *bb = b;
+  if (!on_device) {
+    double *real = reinterpret_cast<double *>(c->W1);
+    CK(cudaMemcpyAsync(real, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(real + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(real + 4 * n3, b, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    r = real;
+    uu = real + n3;
+    bb = real + 4 * n3;
+  }
+  cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
+  cplx64 *Hi = c->H + (size_t)inst * 7 * d.spec;
+  CK(mhd::launch_set_x(r, uu, bb, c->W2, one(c), c->tw, c->stream));
+  CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 7 * d.n, d.nx, 1.0, c->tw, c->stream));
+  CK(mhd::launch_col_forward(c->W1, Si, d.n, 7, d.nk * d.nx, 1.0 / ((double)n3), c->tw, c->stream));
+  CK(cudaMemsetAsync(Hi, 0, 7 * d.spec * sizeof(cplx64), c->stream));
+  CK(cudaMemsetAsync(c->ts + inst, 0, sizeof(mhd::TimeState), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->is_set[inst] = 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, double *b, int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
+  DeviceGuard g(c->device);
+  return spectra_to_real(c, c->S + (size_t)inst * 7 * c->d.spec, rho, m, b, on_device);
+}
+
+mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out, int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (field < 0 || field >= 7 || !out) return fail(c, MHD_EINVAL, "bad field or null output");
+  DeviceGuard g(c->device);
+  const mhd::Dims &d = c->d;
+  const size_t full = (size_t)d.n * d.n * (d.n / 2 + 1);
+  CK(mhd::launch_expand_spectrum(c->S + ((size_t)inst * 7 + field) * d.spec, c->W1, d, c->stream));
+  if ((st = copy_out(c, out, c->W1, full * sizeof(cplx64), on_device))) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+// Event marks around the launches of mhd_step while profiling is on.
+static cudaError_t prof_begin(mhd_ctx *c, int kind, bool on) {
+  if (!on) return cudaSuccess;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      c->ev_pool.push_back(e);
+    }
+  }
+  c->ev_marks.push_back({kind, c->ev_used});
+  cudaError_t err = cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  c->ev_used += 2;
+  return err;
+}
+
+static cudaError_t prof_end(mhd_ctx *c, bool on) {
+  if (!on) return cudaSuccess;
+  return cudaEventRecord(c->ev_pool[c->ev_marks.back().second + 1], c->stream);
+}
+
+#define LAUNCH(kind, call)                     \
+  do {                                         \
+    CK(prof_begin(c, kind, prof));             \
+    CK(call);                                  \
+    CK(prof_end(c, prof));                     \
+  } while (0)
+
+// Steps 1-6 of the pass order for the instances in `d` starting at state `S`; leaves the 12
+// product spectra in W1.
+static mhd_status flux_spectra(mhd_ctx *c, const mhd::Dims &d, const cplx64 *S, const mhd::PhysDev *phys,
+                               mhd::TimeState *ts, mhd::StepCoef *coef, bool advance) {
+  const int b = d.batch;
+  const bool prof = advance && c->profiling;
+  LAUNCH(0, mhd::launch_col_inverse(S, c->W1, d.n, b * 7, d.nk * d.nx, c->tw, c->stream));
+  LAUNCH(1, mhd::launch_col_inverse(c->W1, c->W2, d.n, b * 7 * d.n, d.nx, c->tw, c->stream));
+  LAUNCH(2, mhd::launch_flux_x(c->W2, c->W1, phys, c->part, d, c->tw, c->stream));
+  if (advance) {
+    LAUNCH(3, mhd::launch_step_dt(c->part, mhd::flux_x_blocks_per_instance(d.n), phys, ts, coef, d, c->dt_fixed,
+                                  c->cfl_adv, c->cfl_visc, c->stream));
+  }
+  LAUNCH(4, mhd::launch_col_forward(c->W1, c->W2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw, c->stream));
+  LAUNCH(5, mhd::launch_col_forward(c->W2, c->W1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw, c->stream));
+  return MHD_OK;
+}
+
+mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *db, int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!drho || !dm || !db) return fail(c, MHD_EINVAL, "null output");
+  if (!c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
+  DeviceGuard g(c->device);
+  const mhd::Dims d = one(c);
+  const cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
+  if ((st = flux_spectra(c, d, Si, c->phys + inst, nullptr, nullptr, false))) return st;
+  CK(mhd::launch_assemble(c->W1, const_cast<cplx64 *>(Si), nullptr, c->W2, c->phys + inst, nullptr, 0, d, c->stream));
+  // W2 holds the RHS spectra; inverse_zy reads its source before overwriting W2
+  CK(mhd::launch_col_inverse(c->W2, c->W1, d.n, 7, d.nk * d.nx, c->tw, c->stream));
+  CK(mhd::launch_col_inverse(c->W1, c->W2, d.n, 7 * d.n, d.nx, c->tw, c->stream));
+  const size_t n3 = (size_t)d.n * d.n * d.n;
+  double *real = reinterpret_cast<double *>(c->W1);
+  CK(mhd::launch_get_x(c->W2, real, 7, d, c->tw, c->stream));
+  if ((st = copy_out(c, drho, real, n3 * sizeof(double), on_device))) return st;
+  if ((st = copy_out(c, dm, real + n3, 3 * n3 * sizeof(double), on_device))) return st;
+  if ((st = copy_out(c, db, real + 4 * n3, 3 * n3 * sizeof(double), on_device))) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
+  if (!c) return MHD_EINVAL;
+  if (nsteps < 0) return fail(c, MHD_EINVAL, "negative step count");
+  for (int i = 0; i < c->d.batch; ++i)
+    if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
+  DeviceGuard g(c->device);
+  const bool prof = c->profiling;
+  for (int s = 0; s < nsteps; ++s) {
+    mhd_status st = flux_spectra(c, c->d, c->S, c->phys, c->ts, c->coef, true);
+    if (st) return st;
+    LAUNCH(6, mhd::launch_assemble(c->W1, c->S, c->H, nullptr, c->phys, c->coef, 1, c->d, c->stream));
+  }
+  return MHD_OK;
+}
+
+static mhd_status prof_resolve(mhd_ctx *c) {
+  if (c->ev_marks.empty()) return MHD_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  for (const auto &m : c->ev_marks) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev_pool[m.second], c->ev_pool[m.second + 1]));
+    c->prof_ms[m.first] += ms;
+    c->prof_count[m.first] += 1;
+  }
+  c->ev_marks.clear();
+  c->ev_used = 0;
+  return MHD_OK;
+}
+
+mhd_status mhd_profile(mhd_ctx *c, int32_t enable) {
+  if (!c) return MHD_EINVAL;
+  DeviceGuard g(c->device);
+  mhd_status st = prof_resolve(c);
+  if (st) return st;
+  if (enable) {
+    for (int i = 0; i < 8; ++i) {
+      c->prof_ms[i] = 0.0;
+      c->prof_count[i] = 0;
+    }
+  }
+  c->profiling = enable != 0;
+  return MHD_OK;
+}
+
+mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32_t *count) {
+  if (!c || (!out && max > 0) || !count) return MHD_EINVAL;
+  DeviceGuard g(c->device);
+  mhd_status st = prof_resolve(c);
+  if (st) return st;
+  int k = 0;
+  for (int i = 0; i < 7 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
+  *count = k;
+  return MHD_OK;
+}
+
+mhd_status mhd_synchronize(mhd_ctx *c) {
+  if (!c) return MHD_EINVAL;
+  DeviceGuard g(c->device);
+  int32_t any = 0;
+  CK(mhd::launch_status_any(c->ts, c->d.batch, c->flag, c->stream));
+  CK(cudaMemcpyAsync(&any, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return any ? MHD_ENONFINITE : MHD_OK;
+}
+
+mhd_status mhd_diagnostics(mhd_ctx *c, int32_t inst, mhd_diag *out) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!out) return fail(c, MHD_EINVAL, "null output");
+  DeviceGuard g(c->device);
+  const mhd::Dims d = one(c);
+  const cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
+  if ((st = inverse_zy(c, Si))) return st;
+  CK(mhd::launch_diag_x(c->W2, c->phys + inst, c->part, d, c->tw, c->stream));
+  CK(mhd::launch_diag_finish(c->part, mhd::diag_x_blocks(d.n), Si, c->phys + inst, c->ts + inst, c->diag_out, d,
+                             c->stream));
+  double h[24];
+  CK(cudaMemcpyAsync(h, c->diag_out, 19 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof *out);
+  out->ke = h[0];
+  out->me = h[1];
+  out->eint = h[2];
+  out->cross_hel = h[3];
+  out->mean_speed = h[4];
+  out->mean_bmag = h[5];
+  out->smax = h[6];
+  out->mean_rho = h[7];
+  for (int a = 0; a < 3; ++a) {
+    out->mean_m[a] = h[8 + a];
+    out->mean_b[a] = h[11 + a];
+  }
+  out->divb_rms = h[14];
+  out->t = h[15];
+  out->dt = h[16];
+  out->step = (int64_t)h[17];
+  out->status = (int32_t)h[18];
+  const double cs = c->phys_host[inst].cs;
+  out->mach_s = out->mean_speed / cs;
+  out->v_a = out->mean_rho > 0.0 ? out->mean_bmag / sqrt(out->mean_rho) : 0.0;
+  out->mach_a = out->v_a > 0.0 ? out->mean_speed / out->v_a : 0.0;
+  return MHD_OK;
+}
+
+size_t mhd_checkpoint_doubles(const mhd_ctx *c) { return c ? 4 * 7 * c->d.spec + 8 : 0; }
+
+mhd_status mhd_checkpoint(mhd_ctx *c, int32_t inst, double *buf, int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!buf) return fail(c, MHD_EINVAL, "null buffer");
+  DeviceGuard g(c->device);
+  const size_t sp = 7 * c->d.spec;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(buf, c->S + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
+  CK(cudaMemcpyAsync(buf + 2 * sp, c->H + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
+  static_assert(sizeof(mhd::TimeState) <= 8 * sizeof(double), "time state fits the tail");
+  CK(cudaMemcpyAsync(buf + 4 * sp, c->ts + inst, sizeof(mhd::TimeState), k, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+mhd_status mhd_restore(mhd_ctx *c, int32_t inst, const double *buf, int32_t on_device) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!buf) return fail(c, MHD_EINVAL, "null buffer");
+  DeviceGuard g(c->device);
+  const size_t sp = 7 * c->d.spec;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(c->S + (size_t)inst * sp, buf, sp * sizeof(cplx64), k, c->stream));
+  CK(cudaMemcpyAsync(c->H + (size_t)inst * sp, buf + 2 * sp, sp * sizeof(cplx64), k, c->stream));
+  CK(cudaMemcpyAsync(c->ts + inst, buf + 4 * sp, sizeof(mhd::TimeState), k, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->is_set[inst] = 1;
+  return MHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// mhd_internal.h -- declarations shared by the host code and the kernel translation units.
+//
+// Spectral storage keeps only the modes the 2/3 rule retains (|k_x|, |k_y|, |k_z| <= K with
+// K = floor((N-1)/3)), so every stored array is already dealiased:
+//   state / history / RHS  [inst][field][kz' < NK][ky' < NK][kx < NX]
+// with NX = K + 1 (kx = 0..K; the kx < 0 half follows from Hermitian symmetry) and NK = 2K + 1;
+// a kept index j maps to the wavenumber j for j <= K and j - NK (= -K..-1) above.  Between the
+// FFT passes of one step, fields live in scratch buffers with one more axis expanded to N:
+//   after inverse z   [inst][field][z < N][ky' < NK][kx < NX]
+//   after inverse y   [inst][field][z < N][y < N][kx < NX]
+//   after forward x   [inst][flux][z < N][y < N][kx < NX]   (12 product fields)
+//   after forward y   [inst][flux][z < N][ky' < NK][kx < NX]
+//   after forward z   [inst][flux][kz' < NK][ky' < NK][kx < NX]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mhd {
+
+constexpr int kStateFields = 7;  // rho, m_x, m_y, m_z, B_x, B_y, B_z
+constexpr int kFluxFields = 12;  // T_xx T_yy T_zz T_xy T_xz T_yz, E_x E_y E_z, u_x u_y u_z
+
+struct __align__(16) cplx64 {
+  double re, im;
+};
+
+// Per-instance time-stepping state, device resident.
+struct TimeState {
+  double t;        // simulated time
+  double dt_prev;  // step size of the previous step (0 before the first)
+  double dt_last;  // step size of the last completed step, for diagnostics
+  int64_t step;    // steps taken
+  int32_t status;  // 0, or MHD_ENONFINITE once the instance stopped
+  int32_t pad;
+};
+
+// Coefficients of the current step, written by the dt kernel and read by the update kernel:
+// y^{n+1} = y^n + dt (a1 f^n + a0 f^{n-1}); skip != 0 leaves the instance unchanged.
+struct StepCoef {
+  double dt, a1, a0;
+  int32_t skip;
+  int32_t pad;
+};
+
+// Per-instance physical parameters in device memory.
+struct PhysDev {
+  double nu, eta, cs;
+};
+
+struct Dims {
+  int n;      // grid points per axis
+  int k;      // K = floor((n-1)/3)
+  int nx;     // K + 1
+  int nk;     // 2K + 1
+  int batch;  // instances
+  size_t spec;  // complex values of one truncated spectrum: nk * nk * nx
+};
+
+inline Dims make_dims(int n, int batch) {
+  Dims d;
+  d.n = n;
+  d.k = (n - 1) / 3;
+  d.nx = d.k + 1;
+  d.nk = 2 * d.k + 1;
+  d.batch = batch;
+  d.spec = (size_t)d.nk * d.nk * d.nx;
+  return d;
+}
+
+// ---- launchers (each returns the launch status; all work goes on `s`) ----
+
+// Column FFTs along the middle axis of [nslab][L][C]: inverse (sign +1) expands L from the
+// NK kept indices to N; forward (sign -1) keeps only the NK kept outputs and multiplies by
+// `scale`.  `tw` is the table W_N^m = exp(-2 pi i m / N), m < N.
+cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
+                               const cplx64 *tw, cudaStream_t s);
+cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
+                               double scale, const cplx64 *tw, cudaStream_t s);
+
+// Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
+// grid, forward real transforms of the 12 product fields (kx <= K kept), and per-block maxima of
+// |u| + c_f into `smax_part` ([batch][x_blocks(n)]).
+cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
+                          const Dims &d, const cplx64 *tw, cudaStream_t s);
+int flux_x_blocks_per_instance(int n);
+
+// Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
+// the momentum m = rho u formed first: [7][N^3] real of ONE instance -> [7][z][y][kx <= K].
+cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,
+                         const Dims &d, const cplx64 *tw, cudaStream_t s);
+// Inverse real transform along x of `nfields` fields of one instance: [f][z][y][kx <= K] ->
+// real [f][N^3].
+cudaError_t launch_get_x(const cplx64 *in, double *out, int nfields, const Dims &d,
+                         const cplx64 *tw, cudaStream_t s);
+// Inverse x pass of the 7 state fields of one instance with per-block partial sums of the grid
+// diagnostics: part[block][8] = (sum ke, me, eint, u.B, |u|, |B|, max s, unused).
+cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,
+                          const cplx64 *tw, cudaStream_t s);
+int diag_x_blocks(int n);
+
+// dt of every instance from the CFL partials (or the fixed dt), the AB2 coefficients of this
+// step, and the advance of the per-instance time state.
+cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys,
+                           TimeState *ts, StepCoef *coef, const Dims &d, double dt_fixed,
+                           double cfl_adv, double cfl_visc, cudaStream_t s);
+
+// Spectral assembly of the RHS from the 12 product spectra (scaled by N^-3) and the state.
+// mode 0: write the RHS to `rhs_out`; mode 1: AB2 update of `state` and `hist` with `coef`.
+cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                            cudaStream_t s);
+
+// Final reduction of the diagnostic partials of one instance plus the spectral terms; writes
+// 24 doubles to `out` (see mhd_api.cu for the order).
+cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state,
+                               const PhysDev *phys, const TimeState *ts, double *out,
+                               const Dims &d, cudaStream_t s);
+
+// Expand one truncated spectrum to the full half-complex layout [N][N][N/2+1] (zeros outside).
+cudaError_t launch_expand_spectrum(const cplx64 *in, cplx64 *out, const Dims &d, cudaStream_t s);
+
+// Any instance with a non-zero status -> *flag = 1.
+cudaError_t launch_status_any(const TimeState *ts, int batch, int32_t *flag, cudaStream_t s);
+
+}  // namespace mhd
