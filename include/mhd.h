@@ -178,6 +178,26 @@ typedef struct {
 MHD_API mhd_status mhd_profile(mhd_ctx *ctx, int32_t enable);
 MHD_API mhd_status mhd_profile_read(mhd_ctx *ctx, mhd_kernel_time *out, int32_t max, int32_t *count);
 
+/* Right-hand side of one state that allocates no memory.  For callers that must not call
+ * cudaMalloc when they need it (a host framework that already owns the device memory pool, or a
+ * latency-bound loop that cannot take the device synchronisation an allocation may bring).  The
+ * paper has no counterpart; this is a service of the library.
+ *   n               16 or 32 (at most 32): anything else returns MHD_EINVAL before any GPU work
+ *   phys            host pointer to the instance's nu, eta, cs
+ *   rho, u, b       DEVICE pointers: real-space rho (N^3), u (3 N^3), B (3 N^3) as for
+ *                   mhd_set_state (m = rho u, projection onto the 2/3-rule modes)
+ *   drho, dm, db    DEVICE pointers receiving what mhd_rhs returns for that state
+ *   stream          cudaStream_t to queue the work on (NULL = legacy default stream)
+ * Intermediate spectra live in one file-scope device array of about 4.7 MB that every GPU which
+ * loads the library keeps until the process exits.  The first call on a device resolves that
+ * array's address and uploads its twiddle tables; make it before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's contents, so calls that overlap on the
+ * GPU race; none of it needs to start at zero.  The call queues its work and returns without
+ * synchronising: the outputs are valid once the stream has reached that point.  MHD_ECUDA if a
+ * CUDA call fails. */
+MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, const double *rho, const double *u,
+                                   const double *b, double *drho, double *dm, double *db, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4
 EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "mhd_set_state",
            "mhd_get_state", "mhd_rhs", "mhd_get_spectrum", "mhd_step", "mhd_synchronize",
            "mhd_diagnostics", "mhd_checkpoint_doubles", "mhd_checkpoint", "mhd_restore", "mhd_profile",
-           "mhd_profile_read")
+           "mhd_profile_read", "mhd_rhs_noalloc")
 
 
 class MhdError(RuntimeError):
@@ -109,6 +109,8 @@ def load_library(path: str = LIBRARY):
     lib.mhd_profile.argtypes = [P, I32]
     lib.mhd_profile_read.restype = I32
     lib.mhd_profile_read.argtypes = [P, ctypes.POINTER(MhdKernelTime), I32, ctypes.POINTER(I32)]
+    lib.mhd_rhs_noalloc.restype = I32
+    lib.mhd_rhs_noalloc.argtypes = [I32, ctypes.POINTER(MhdPhys), P, P, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -311,3 +313,27 @@ def mhd_profile_read(ctx: Context) -> dict:
     cnt = ctypes.c_int32()
     _check(ctx, load_library().mhd_profile_read(ctx.handle, arr, 16, ctypes.byref(cnt)))
     return {arr[i].name.decode(): (arr[i].total_ms, arr[i].launches) for i in range(cnt.value)}
+
+
+def mhd_rhs_noalloc(n: int, phys, rho, u, b, stream=None):
+    """RHS of one real-space state (CUDA float64 tensors) without any allocation inside the
+    library (only the output tensors are allocated, here, by PyTorch).  n is 16 or 32.  Queued on
+    `stream` (default: PyTorch's current stream); returns (drho, dm, dB) as CUDA tensors."""
+    torch = _torch()
+    shape3, shapev = (n, n, n), (3, n, n, n)
+    args = []
+    for a, shp in ((rho, shape3), (u, shapev), (b, shapev)):
+        if not _is_device(a):
+            raise ValueError("mhd_rhs_noalloc takes CUDA tensors")
+        args.append(_in_ptr(a, shp)[0])
+    outs = [torch.empty(shape3, dtype=torch.float64, device="cuda"),
+            torch.empty(shapev, dtype=torch.float64, device="cuda"),
+            torch.empty(shapev, dtype=torch.float64, device="cuda")]
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ph = MhdPhys(*[float(v) for v in phys])
+    st = load_library().mhd_rhs_noalloc(int(n), ctypes.byref(ph), *args, *[o.data_ptr() for o in outs],
+                                        ctypes.c_void_p(stream) if stream else None)
+    if st != MHD_OK:
+        raise MhdError(st, "mhd_rhs_noalloc failed")
+    return tuple(outs)
