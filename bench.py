@@ -37,6 +37,7 @@ UNIT = "grid-point-steps/s"
 # memory) -> 256^3 / 0.22 grid-point-steps/s.  Another machine: context for the ratio only.
 PAPER_256_V100 = 256 ** 3 / 0.22
 FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
 def peaks():
@@ -49,9 +50,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(n: int):
+def workload(n: int, ic: str = "abc"):
     from paper_1810_12707_gb300 import inputs
+    if ic == "tg":
+        # Taylor-Green, Mach 0.3, seeded random B at energy 1e-3, nu = eta = 1e-3
+        return inputs.taylor_green(n, seed=2, b_energy=1e-3, mach=0.3, nu=1e-3, eta=1e-3)
+    if ic == "ot":
+        return inputs.orszag_tang(n, seed=0, mach=0.1, nu=1e-2, eta=1e-2)
     return inputs.abc_dynamo(n, seed=1, b_energy=1e-5, mach=0.1, nu=2e-3, eta=2e-3)
+
+
+IC_NAMES = {"abc": ("abc_dynamo", "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", 0.1, 2e-3),
+            "tg": ("taylor_green", "Taylor-Green + seed-2 random B (|k|<=4, E_B=1e-3)", 0.3, 1e-3),
+            "ot": ("orszag_tang", "Orszag-Tang type + seed-0 1e-3 perturbation", 0.1, 1e-2)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -59,20 +70,20 @@ def workload(n: int):
 # HBM reads + writes of the pass; flops count 5 N log2 N per complex FFT of length N plus the
 # pointwise arithmetic.
 # ---------------------------------------------------------------------------------------------
-def kernel_model(n: int, batch: int = 1):
+def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
     k = (n - 1) // 3
     nx, nk = k + 1, 2 * k + 1
     spec = nk * nk * nx
-    c = 16.0
+    c = 16.0 if precision == "fp64" else 8.0  # complex value of the passes; the state is FP64
     fft = 5.0 * n * math.log2(n)
     m = {
-        "inverse_z": (7 * (spec + n * nk * nx) * c, 7 * nk * nx * fft),
+        "inverse_z": (7 * (spec * 16 + n * nk * nx * c), 7 * nk * nx * fft),
         "inverse_y": (7 * (n * nk * nx + n * n * nx) * c, 7 * n * nx * fft),
         "flux_x": ((7 + 12) * n * n * nx * c, (7 + 12) * (n * n / 2) * fft + 49.0 * n ** 3),
         "step_dt": (8.0 * n * n / 2, 0.0),
         "forward_y": (12 * (n * n * nx + n * nk * nx) * c, 12 * n * nx * fft),
         "forward_z": (12 * (n * nk * nx + spec) * c, 12 * nk * nx * fft),
-        "assemble_ab2": ((12 + 7 + 7 + 7 + 7) * spec * c, 110.0 * spec),
+        "assemble_ab2": (12 * spec * c + (7 + 7 + 7 + 7) * spec * 16, 110.0 * spec),
     }
     return {key: (b * batch, f * batch) for key, (b, f) in m.items()}
 
@@ -133,10 +144,10 @@ def dist_env():
     return world, rank, local
 
 
-def time_oracle(n: int, steps: int, budget_s: float = 30.0):
+def time_oracle(n: int, steps: int, budget_s: float = 30.0, ic_name: str = "abc"):
     """Time the CPU oracle on the same workload: `steps` AB2 steps after one untimed set_state."""
     from oracle import oracle
-    ic = workload(n)
+    ic = workload(n, ic_name)
     o = oracle.Oracle(n, ic.nu, ic.eta, ic.cs, dt=0.0)
     o.set_state(ic.rho, ic.u, ic.b)
     done, t0 = 0, time.perf_counter()
@@ -156,18 +167,18 @@ def run_reference(args):
     n = args.n
     # each bench step is one oracle step of the same workload; the run is capped at about three
     # minutes of CPU work in total
-    _, _, t_one, _ = time_oracle(n, 1)
+    _, _, t_one, _ = time_oracle(n, 1, ic_name=args.ic)
     budget = 180.0
     k = max(1, min(args.steps, int(budget / max(t_one, 1e-9))))
-    value, done, el, cores = time_oracle(n, k, budget_s=budget)
+    value, done, el, cores = time_oracle(n, k, budget_s=budget, ic_name=args.ic)
+    name, desc, mach, visc = IC_NAMES[args.ic]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": done, "warmup": 1, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": value / PAPER_256_V100 if n == 256 else None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"abc_dynamo_{n}^3_fp64", "n": n, "batch": 1, "precision": "fp64",
-                   "ic": "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", "mach": 0.1, "nu": 2e-3,
-                   "eta": 2e-3, "dt": "cfl"},
+        "config": {"workload": f"{name}_{n}^3_{args.precision}", "n": n, "batch": 1, "precision": args.precision,
+                   "ic": desc, "mach": mach, "nu": visc, "eta": visc, "dt": "cfl"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{done} AB2 steps of the {n}^3 workload after set_state (one untimed warm-up step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -194,8 +205,9 @@ def run_ours(args):
     from paper_1810_12707_gb300 import mhd
 
     n, K, W = args.n, args.steps, args.warmup
-    ic = workload(n)
-    ctx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0)
+    prec = mhd.MHD_FP64 if args.precision == "fp64" else mhd.MHD_FP32_MIXED
+    ic = workload(n, args.ic)
+    ctx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0, precision=prec)
     mhd.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
     stream = torch.cuda.current_stream()
 
@@ -240,7 +252,7 @@ def run_ours(args):
     h_b[...] = ic.b
     lib = mhd.load_library()
     o_rho, o_m, o_b = pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))
-    ectx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0)
+    ectx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0, precision=prec)
     mhd.mhd_set_state(ectx, 0, h_rho, h_u, h_b)
     mhd.mhd_step(ectx, 2)
     lib.mhd_get_state(ectx.handle, 0, o_rho.ctypes.data, o_m.ctypes.data, o_b.ctypes.data, 0)
@@ -263,7 +275,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest share of device time)
     hbm, hbm_src = peaks()
-    model = kernel_model(n)
+    model = kernel_model(n, 1, args.precision)
+    alu_peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
     per = {}
     for name, (tot, cnt) in prof.items():
         if cnt:
@@ -274,11 +287,12 @@ def run_ours(args):
     top = max(per, key=lambda k: per[k]["share"])
     tb, tf = model[top]
     t_mem = tb / (hbm * 1e9)
-    t_alu = tf / (FP64_PEAK_TFLOPS * 1e12)
+    t_alu = tf / (alu_peak * 1e12)
     if t_alu >= t_mem:
-        roof = {"bound": "alu", "achieved": per[top]["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": per[top]["tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)"}
+        roof = {"bound": "alu", "achieved": per[top]["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": per[top]["tflops"] / alu_peak, "traffic": None,
+                "peak_source": ("FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)" if args.precision == "fp64"
+                                else "FP32 FMA units x clock (probe 74.4 TFLOP/s)")}
     else:
         roof = {"bound": "hbm", "achieved": per[top]["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": per[top]["gbs"] / hbm, "traffic": None, "peak_source": f"{hbm_src} copy"}
@@ -287,19 +301,20 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, done, el, cores = time_oracle(n, 2, budget_s=30.0)
+        v, done, el, cores = time_oracle(n, 2, budget_s=30.0, ic_name=args.ic)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{done} AB2 steps of the {n}^3 workload after an untimed set_state ({el:.1f} s)"}
 
+    name, desc, mach, visc = IC_NAMES[args.ic]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / (world * PAPER_256_V100) if n == 256 else None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"abc_dynamo_{n}^3_fp64", "n": n, "batch": 1, "precision": "fp64",
-                       "ic": "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", "mach": 0.1, "nu": 2e-3,
-                       "eta": 2e-3, "dt": "cfl", "l2": "per-step working set > L2 (no flush)",
+            "dtype": "f64" if args.precision == "fp64" else "f32 (fp64 state/update)", "data": "synthetic",
+            "config": {"workload": f"{name}_{n}^3_{args.precision}", "n": n, "batch": 1, "precision": args.precision,
+                       "ic": desc, "mach": mach, "nu": visc, "eta": visc, "dt": "cfl",
+                       "l2": "per-step working set > L2 (no flush)",
                        "parallelism": f"replicas x{world}",
                        "baseline": "paper Table III 256^3 V100 0.22 s/step (other hardware, context)"},
             "roofline": roof,
@@ -325,6 +340,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--ic", choices=("abc", "tg", "ot"), default="abc")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

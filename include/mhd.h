@@ -56,7 +56,10 @@ typedef enum {
 } mhd_status;
 
 typedef enum {
-  MHD_FP64 = 0 /* IEEE double everywhere */
+  MHD_FP64 = 0,       /* IEEE double everywhere */
+  MHD_FP32_MIXED = 1  /* FFT passes and grid products in FP32; state, history, AB2 update, the
+                         pressure and dissipation terms, CFL dt, k = 0 modes and all diagnostics
+                         in FP64 */
 } mhd_precision;
 
 typedef struct mhd_ctx mhd_ctx;

@@ -9,21 +9,32 @@
 
 namespace mhd {
 
-__device__ __forceinline__ cplx64 c_add(cplx64 a, cplx64 b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cplx64 c_sub(cplx64 a, cplx64 b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cplx64 c_scale(cplx64 a, double s) { return {a.re * s, a.im * s}; }
+template <typename C>
+__device__ __forceinline__ C c_add(C a, C b) { return {a.re + b.re, a.im + b.im}; }
+template <typename C>
+__device__ __forceinline__ C c_sub(C a, C b) { return {a.re - b.re, a.im - b.im}; }
+template <typename C>
+__device__ __forceinline__ C c_scale(C a, typename C::value_type s) { return {a.re * s, a.im * s}; }
 // a * w
-__device__ __forceinline__ cplx64 c_mul(cplx64 a, cplx64 w) {
+template <typename C>
+__device__ __forceinline__ C c_mul(C a, C w) {
   return {a.re * w.re - a.im * w.im, a.re * w.im + a.im * w.re};
 }
 // a * conj(w)
-__device__ __forceinline__ cplx64 c_mulc(cplx64 a, cplx64 w) {
+template <typename C>
+__device__ __forceinline__ C c_mulc(C a, C w) {
   return {a.re * w.re + a.im * w.im, a.im * w.re - a.re * w.im};
 }
 // a * (DIR i)
-template <int DIR>
-__device__ __forceinline__ cplx64 c_mul_i(cplx64 a) {
-  return DIR > 0 ? cplx64{-a.im, a.re} : cplx64{a.im, -a.re};
+template <int DIR, typename C>
+__device__ __forceinline__ C c_mul_i(C a) {
+  return DIR > 0 ? C{-a.im, a.re} : C{a.im, -a.re};
+}
+// precision conversion
+template <typename CT, typename CF>
+__device__ __forceinline__ CT c_cvt(CF a) {
+  using R = typename CT::value_type;
+  return CT{(R)a.re, (R)a.im};
 }
 
 // NaN-propagating maximum (a non-finite CFL speed must reach the step-size kernel).
@@ -35,17 +46,17 @@ __device__ __forceinline__ double nan_max(double a, double b) {
 
 // ---- DFTs of length 2, 4, 8 on registers, natural order in and out ----
 
-template <int DIR>
-__device__ __forceinline__ void dft2(cplx64 *v) {
-  const cplx64 a = v[0], b = v[1];
+template <int DIR, typename C>
+__device__ __forceinline__ void dft2(C *v) {
+  const C a = v[0], b = v[1];
   v[0] = c_add(a, b);
   v[1] = c_sub(a, b);
 }
 
-template <int DIR>
-__device__ __forceinline__ void dft4(cplx64 *v) {
-  const cplx64 s0 = c_add(v[0], v[2]), d0 = c_sub(v[0], v[2]);
-  const cplx64 s1 = c_add(v[1], v[3]), d1 = c_mul_i<DIR>(c_sub(v[1], v[3]));
+template <int DIR, typename C>
+__device__ __forceinline__ void dft4(C *v) {
+  const C s0 = c_add(v[0], v[2]), d0 = c_sub(v[0], v[2]);
+  const C s1 = c_add(v[1], v[3]), d1 = c_mul_i<DIR>(c_sub(v[1], v[3]));
   v[0] = c_add(s0, s1);
   v[2] = c_sub(s0, s1);
   v[1] = c_add(d0, d1);
@@ -54,19 +65,20 @@ __device__ __forceinline__ void dft4(cplx64 *v) {
 
 // Length 8 by one decimation-in-frequency split: b_j = a_j + a_{j+4} feeds the even outputs,
 // c_j = (a_j - a_{j+4}) W8^j the odd ones, each through a length-4 DFT.
-template <int DIR>
-__device__ __forceinline__ void dft8(cplx64 *v) {
-  constexpr double h = 0.70710678118654752440;  // sqrt(2) / 2
-  cplx64 b[4], c[4];
+template <int DIR, typename C>
+__device__ __forceinline__ void dft8(C *v) {
+  using R = typename C::value_type;
+  constexpr R h = (R)0.70710678118654752440;  // sqrt(2) / 2
+  C b[4], c[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     b[j] = c_add(v[j], v[j + 4]);
     c[j] = c_sub(v[j], v[j + 4]);
   }
   // W8^1 = h (1 + DIR i), W8^2 = DIR i, W8^3 = h (-1 + DIR i)
-  c[1] = cplx64{h * (c[1].re - DIR * c[1].im), h * (c[1].im + DIR * c[1].re)};
+  c[1] = C{h * (c[1].re - DIR * c[1].im), h * (c[1].im + DIR * c[1].re)};
   c[2] = c_mul_i<DIR>(c[2]);
-  c[3] = cplx64{h * (-c[3].re - DIR * c[3].im), h * (-c[3].im + DIR * c[3].re)};
+  c[3] = C{h * (-c[3].re - DIR * c[3].im), h * (-c[3].im + DIR * c[3].re)};
   dft4<DIR>(b);
   dft4<DIR>(c);
 #pragma unroll
@@ -76,8 +88,8 @@ __device__ __forceinline__ void dft8(cplx64 *v) {
   }
 }
 
-template <int R, int DIR>
-__device__ __forceinline__ void dft_small(cplx64 *v) {
+template <int R, int DIR, typename C>
+__device__ __forceinline__ void dft_small(C *v) {
   if constexpr (R == 8) dft8<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v);
   else dft2<DIR>(v);
@@ -96,15 +108,14 @@ __device__ __forceinline__ void dft_small(cplx64 *v) {
 //
 // Every thread of the block must call this (it contains __syncthreads); threads with
 // `active == false` only take part in the barriers.
-template <int N, int DIR, int NS>
-__device__ __forceinline__ void stockham_stages(cplx64 *buf, int t, bool active,
-                                                const cplx64 *__restrict__ tw) {
+template <int N, int DIR, int NS, typename C>
+__device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
     constexpr int R = (N / NS >= 8) ? 8 : N / NS;
     constexpr int NB = 8 / R;
     constexpr int TPP = N / 8;
     constexpr int TWSTEP = N / (NS * R);
-    cplx64 v[8];
+    C v[8];
     if (active) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -112,9 +123,9 @@ __device__ __forceinline__ void stockham_stages(cplx64 *buf, int t, bool active,
         const int k = j % NS;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          cplx64 x = buf[j + r * (N / R)];
+          C x = buf[j + r * (N / R)];
           if (NS > 1 && r > 0) {
-            const cplx64 w = tw[r * k * TWSTEP];
+            const C w = tw[r * k * TWSTEP];
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
           }
           v[b * R + r] = x;
@@ -125,7 +136,7 @@ __device__ __forceinline__ void stockham_stages(cplx64 *buf, int t, bool active,
     if (active) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        dft_small<R, DIR>(v + b * R);
+        dft_small<R, DIR, C>(v + b * R);
         const int j = t + b * TPP;
         const int k = j % NS;
         const int base = (j / NS) * NS * R + k;
@@ -134,13 +145,13 @@ __device__ __forceinline__ void stockham_stages(cplx64 *buf, int t, bool active,
       }
     }
     __syncthreads();
-    stockham_stages<N, DIR, NS * R>(buf, t, active, tw);
+    stockham_stages<N, DIR, NS * R, C>(buf, t, active, tw);
   }
 }
 
-template <int N, int DIR>
-__device__ __forceinline__ void pencil_fft(cplx64 *buf, int t, bool active, const cplx64 *__restrict__ tw) {
-  stockham_stages<N, DIR, 1>(buf, t, active, tw);
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void pencil_fft(C *buf, int t, bool active, const C *__restrict__ tw) {
+  stockham_stages<N, DIR, 1, C>(buf, t, active, tw);
 }
 
 // FFT index of kept index j (0..2K) along a truncated axis: j for j <= K, else j - (2K+1) + N.

@@ -15,10 +15,12 @@
 
 namespace mhd {
 
-template <int N, int DIR>
-__global__ void col_fft_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict__ out, int ntiles,
-                               int tc, int cols, int K, double scale, const cplx64 *__restrict__ tw) {
-  extern __shared__ cplx64 sm[];
+// CI, CO: element types in and out; CC: type of the transform arithmetic (= the output's).
+template <int N, int DIR, typename CI, typename CO, typename CC>
+__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tc,
+                               int cols, int K, double scale, const CC *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CC *sm = reinterpret_cast<CC *>(smem_raw);
   constexpr int TPP = N / 8;
   constexpr int P = N + 1;
   const int NK = 2 * K + 1;
@@ -29,12 +31,12 @@ __global__ void col_fft_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict
   const int c0 = tile * tc;
   const int nthr = blockDim.x;
 
-  const cplx64 *src = in + slab * (size_t)lin * cols;
+  const CI *src = in + slab * (size_t)lin * cols;
   for (int q = threadIdx.x; q < lin * tc; q += nthr) {
     const int l = q / tc, c = q - l * tc;
     const int col = c0 + c;
-    cplx64 v = {0.0, 0.0};
-    if (col < cols) v = src[(size_t)l * cols + col];
+    CC v = {0, 0};
+    if (col < cols) v = c_cvt<CC>(src[(size_t)l * cols + col]);
     const int f = DIR > 0 ? kept_to_fft(l, K, N) : l;
     sm[c * P + f] = v;
   }
@@ -42,7 +44,7 @@ __global__ void col_fft_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict
     const int nz = N - NK;  // FFT indices K+1 .. N-K-1 are outside the kept set
     for (int q = threadIdx.x; q < nz * tc; q += nthr) {
       const int l = q / tc, c = q - l * tc;
-      sm[c * P + K + 1 + l] = cplx64{0.0, 0.0};
+      sm[c * P + K + 1 + l] = CC{0, 0};
     }
   }
   __syncthreads();
@@ -50,17 +52,17 @@ __global__ void col_fft_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict
   const int pencil = threadIdx.x / TPP;
   const int t = threadIdx.x - pencil * TPP;
   const bool active = pencil < tc && c0 + pencil < cols;
-  pencil_fft<N, DIR>(sm + (active ? pencil : 0) * P, t, active, tw);
+  pencil_fft<N, DIR, CC>(sm + (active ? pencil : 0) * P, t, active, tw);
 
-  cplx64 *dst = out + slab * (size_t)lout * cols;
+  CO *dst = out + slab * (size_t)lout * cols;
   for (int q = threadIdx.x; q < lout * tc; q += nthr) {
     const int l = q / tc, c = q - l * tc;
     const int col = c0 + c;
     if (col < cols) {
       const int f = DIR > 0 ? l : kept_to_fft(l, K, N);
-      cplx64 v = sm[c * P + f];
-      if (DIR < 0) v = c_scale(v, scale);
-      dst[(size_t)l * cols + col] = v;
+      CC v = sm[c * P + f];
+      if (DIR < 0) v = c_scale(v, (typename CC::value_type)scale);
+      dst[(size_t)l * cols + col] = c_cvt<CO>(v);
     }
   }
 }
@@ -78,27 +80,28 @@ int pick_tc(int n, int cols) {
   return tc < 1 ? 1 : tc;
 }
 
-template <int N, int DIR>
-cudaError_t launch_col_n(const cplx64 *in, cplx64 *out, int nslab, int cols, double scale,
-                         const cplx64 *tw, cudaStream_t s) {
+template <int N, int DIR, typename CI, typename CO>
+cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
+                         cudaStream_t s) {
   const int K = (N - 1) / 3;
   const int tc = pick_tc(N, cols);
   const int ntiles = (cols + tc - 1) / tc;
-  const size_t smem = (size_t)tc * (N + 1) * sizeof(cplx64);
+  const size_t smem = (size_t)tc * (N + 1) * sizeof(CO);
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<col_fft_kernel<N, DIR>>((int)smem);
+    cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO>>((int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (long long)nslab * ntiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  col_fft_kernel<N, DIR><<<(unsigned)blocks, tc * (N / 8), smem, s>>>(in, out, ntiles, tc, cols, K, scale, tw);
+  col_fft_kernel<N, DIR, CI, CO, CO><<<(unsigned)blocks, tc * (N / 8), smem, s>>>(in, out, ntiles, tc, cols, K,
+                                                                                 scale, tw);
   return cudaGetLastError();
 }
 
-template <int DIR>
-cudaError_t launch_col(const cplx64 *in, cplx64 *out, int n, int nslab, int cols, double scale,
-                       const cplx64 *tw, cudaStream_t s) {
+template <int DIR, typename CI, typename CO>
+cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale, const CO *tw,
+                       cudaStream_t s) {
   switch (n) {
     case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s);
     case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s);
@@ -117,9 +120,20 @@ cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, 
                                const cplx64 *tw, cudaStream_t s) {
   return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
 }
-
+cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
+                               const cplx32 *tw, cudaStream_t s) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
+}
+cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
+                               const cplx32 *tw, cudaStream_t s) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
+}
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                double scale, const cplx64 *tw, cudaStream_t s) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s);
+}
+cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
+                               double scale, const cplx32 *tw, cudaStream_t s) {
   return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s);
 }
 

@@ -14,7 +14,10 @@
 
 namespace mhd {
 
-__global__ void assemble_kernel(const cplx64 *__restrict__ flux, cplx64 *__restrict__ state,
+// FC: element type of the product spectra (FP64, or FP32 in the mixed mode); everything else,
+// the state, the history and the arithmetic, is FP64.
+template <typename FC>
+__global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict__ state,
                                 cplx64 *__restrict__ hist, cplx64 *__restrict__ rhs_out,
                                 const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
                                 int mode, int K, int batch, double inv_n3) {
@@ -34,12 +37,12 @@ __global__ void assemble_kernel(const cplx64 *__restrict__ flux, cplx64 *__restr
     const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
 
     const cplx64 *S = state + (size_t)inst * 7 * spec + m;
-    const cplx64 *F = flux + (size_t)inst * 12 * spec + m;
+    const FC *F = flux + (size_t)inst * 12 * spec + m;
     cplx64 y[7], f[12];
 #pragma unroll
     for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
+    for (int q = 0; q < 12; ++q) f[q] = c_scale(c_cvt<cplx64>(F[q * spec]), inv_n3);
     const cplx64 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
     const cplx64 Ex = f[6], Ey = f[7], Ez = f[8];
 
@@ -227,14 +230,27 @@ static unsigned grid_for(size_t total, int threads) {
   return (unsigned)(b == 0 ? 1 : b);
 }
 
+template <typename FC>
+static cudaError_t assemble_any(const FC *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
+                                const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                                cudaStream_t s) {
+  const size_t total = d.spec * d.batch;
+  const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
+  assemble_kernel<FC><<<grid_for(total, 256), 256, 0, s>>>(flux, state, hist, rhs_out, phys, coef, mode, d.k,
+                                                           d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
                             const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
                             cudaStream_t s) {
-  const size_t total = d.spec * d.batch;
-  const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
-  assemble_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, state, hist, rhs_out, phys, coef, mode, d.k,
-                                                       d.batch, inv_n3);
-  return cudaGetLastError();
+  return assemble_any(flux, state, hist, rhs_out, phys, coef, mode, d, s);
+}
+
+cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                            cudaStream_t s) {
+  return assemble_any(flux, state, hist, rhs_out, phys, coef, mode, d, s);
 }
 
 cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys, TimeState *ts,

@@ -34,15 +34,15 @@ constexpr int threads_for(int n, int pencils) {
 
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
 // N/8 threads of the block taking one pencil at a time.
-template <int N, int DIR, typename Ptr>
-__device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const cplx64 *__restrict__ tw) {
+template <int N, int DIR, typename Ptr, typename C>
+__device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
   constexpr int TPP = N / 8;
   const int G = blockDim.x / TPP;
   const int g = threadIdx.x / TPP, t = threadIdx.x - g * TPP;
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, C>(ptr(active ? id : 0), t, active, tw);
   }
 }
 
@@ -51,11 +51,15 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const cplx64 *__res
 // ------------------------------------------------------------------------------------------
 // Fused flux pass
 // ------------------------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__restrict__ in, cplx64 *__restrict__ out,
+// C: complex type of the data and of all arithmetic (cplx64 or cplx32); the CFL maxima are
+// combined in FP64.
+template <int N, typename C>
+__global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, double *__restrict__ smax_part,
-                              int K, int blocks_per_inst, const cplx64 *__restrict__ tw) {
-  extern __shared__ cplx64 sm[];
+                              int K, int blocks_per_inst, const C *__restrict__ tw) {
+  using R = typename C::value_type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *sm = reinterpret_cast<C *>(smem_raw);
   __shared__ double red[32];
   constexpr int P = N + 1;
   constexpr int PAIRS = pairs_for(N);
@@ -71,21 +75,21 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__res
     const int k = q % NX;
     const int r = q / NX;
     const int f = r % 7, p = r / 7;
-    const cplx64 *src = in + ((size_t)(inst * 7 + f) * NN + row0 + 2 * p) * NX;
-    cplx64 *pen = sm + (p * 12 + f) * P;
-    const cplx64 x0 = src[k], x1 = src[NX + k];
+    const C *src = in + ((size_t)(inst * 7 + f) * NN + row0 + 2 * p) * NX;
+    C *pen = sm + (p * 12 + f) * P;
+    const C x0 = src[k], x1 = src[NX + k];
     if (k == 0) {
-      pen[0] = cplx64{x0.re, x1.re};
+      pen[0] = C{x0.re, x1.re};
     } else {
-      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
-      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+      pen[k] = C{x0.re - x1.im, x0.im + x1.re};
+      pen[N - k] = C{x0.re + x1.im, x1.re - x0.im};
     }
   }
   for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
     const int z = q % (N - 2 * K - 1);
     const int r = q / (N - 2 * K - 1);
     const int f = r % 7, p = r / 7;
-    sm[(p * 12 + f) * P + K + 1 + z] = cplx64{0.0, 0.0};
+    sm[(p * 12 + f) * P + K + 1 + z] = C{0, 0};
   }
   __syncthreads();
 
@@ -93,27 +97,27 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__res
   fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
 
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
-  const double cs2 = phys[inst].cs * phys[inst].cs;
+  const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
   double smax = 0.0;
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
-    cplx64 *b = sm + p * 12 * P + j;
-    double v[2][7];
+    C *b = sm + p * 12 * P + j;
+    R v[2][7];
 #pragma unroll
     for (int f = 0; f < 7; ++f) {
-      const cplx64 c = b[f * P];
+      const C c = b[f * P];
       v[0][f] = c.re;
       v[1][f] = c.im;
     }
-    double *bd = reinterpret_cast<double *>(b);
+    R *bd = reinterpret_cast<R *>(b);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const double rho = v[h][0];
-      const double mx = v[h][1], my = v[h][2], mz = v[h][3];
-      const double bx = v[h][4], by = v[h][5], bz = v[h][6];
-      const double ux = mx / rho, uy = my / rho, uz = mz / rho;
-      const double b2 = bx * bx + by * by + bz * bz;
-      const double hb = 0.5 * b2;
+      const R rho = v[h][0];
+      const R mx = v[h][1], my = v[h][2], mz = v[h][3];
+      const R bx = v[h][4], by = v[h][5], bz = v[h][6];
+      const R ux = mx / rho, uy = my / rho, uz = mz / rho;
+      const R b2 = bx * bx + by * by + bz * bz;
+      const R hb = (R)0.5 * b2;
       // component h of pencil f at this point is bd[2 * f * P + h]
       bd[2 * 0 * P + h] = mx * ux + hb - bx * bx;   // T_xx
       bd[2 * 1 * P + h] = my * uy + hb - by * by;   // T_yy
@@ -127,8 +131,8 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__res
       bd[2 * 9 * P + h] = ux;
       bd[2 * 10 * P + h] = uy;
       bd[2 * 11 * P + h] = uz;
-      const double s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 / rho);
-      smax = nan_max(smax, s);
+      const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 / rho);
+      smax = nan_max(smax, (double)s);
     }
   }
   __syncthreads();
@@ -137,15 +141,16 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const cplx64 *__res
   fft_pencils<N, -1>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
 
   // 5. unpack and store the kept half spectra
+  const R half = (R)0.5;
   for (int q = threadIdx.x; q < 12 * PAIRS * NX; q += nthr) {
     const int k = q % NX;
     const int r = q / NX;
     const int f = r % 12, p = r / 12;
-    const cplx64 *pen = sm + (p * 12 + f) * P;
-    const cplx64 z = pen[k], zc = pen[(N - k) & (N - 1)];
-    cplx64 *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
-    dst[k] = cplx64{0.5 * (z.re + zc.re), 0.5 * (z.im - zc.im)};
-    dst[NX + k] = cplx64{0.5 * (z.im + zc.im), 0.5 * (zc.re - z.re)};
+    const C *pen = sm + (p * 12 + f) * P;
+    const C z = pen[k], zc = pen[(N - k) & (N - 1)];
+    C *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
+    dst[k] = C{half * (z.re + zc.re), half * (z.im - zc.im)};
+    dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
   }
 
   const double m = block_nan_max(smax, red);
@@ -159,7 +164,8 @@ template <int N>
 __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__restrict__ rho, const double *__restrict__ u,
                              const double *__restrict__ b, cplx64 *__restrict__ out, int K,
                              const cplx64 *__restrict__ tw) {
-  extern __shared__ cplx64 sm[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = N + 1;
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
@@ -199,7 +205,8 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
 template <int N>
 __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__restrict__ in, double *__restrict__ out, int nf, int K,
                              const cplx64 *__restrict__ tw) {
-  extern __shared__ cplx64 sm[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = N + 1;
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
@@ -245,7 +252,8 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
 template <int N>
 __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__restrict__ in, const PhysDev *__restrict__ phys,
                               double *__restrict__ part, int K, const cplx64 *__restrict__ tw) {
-  extern __shared__ cplx64 sm[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   __shared__ double red[32];
   constexpr int P = N + 1;
   constexpr int PAIRS = pairs_for(N);
@@ -321,19 +329,19 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
 // ------------------------------------------------------------------------------------------
 namespace {
 
-template <int N>
-cudaError_t flux_n(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *part, const Dims &d,
-                   const cplx64 *tw, cudaStream_t s) {
+template <int N, typename C>
+cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, double *part, const Dims &d, const C *tw,
+                   cudaStream_t s) {
   constexpr int PAIRS = pairs_for(N);
   const int bpi = N * N / (2 * PAIRS);
   const int threads = threads_for(N, 12 * PAIRS);
-  const size_t smem = (size_t)12 * PAIRS * (N + 1) * sizeof(cplx64);
+  const size_t smem = (size_t)12 * PAIRS * (N + 1) * sizeof(C);
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<flux_x_kernel<N>>((int)smem);
+    cudaError_t e = ensure_smem<flux_x_kernel<N, C>>((int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (long long)bpi * d.batch;
-  flux_x_kernel<N><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw);
+  flux_x_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw);
   return cudaGetLastError();
 }
 
@@ -400,6 +408,11 @@ int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
 
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
                           const Dims &d, const cplx64 *tw, cudaStream_t s) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_part, d, tw, s)));
+}
+
+cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, double *smax_part,
+                          const Dims &d, const cplx32 *tw, cudaStream_t s) {
   MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_part, d, tw, s)));
 }
 

@@ -23,6 +23,7 @@
 #include "mhd.h"
 #include "mhd_internal.h"
 
+using mhd::cplx32;
 using mhd::cplx64;
 
 struct mhd_ctx {
@@ -34,8 +35,10 @@ struct mhd_ctx {
   std::vector<mhd_phys> phys_host;
   std::vector<char> is_set;
   mhd::PhysDev *phys = nullptr;
+  int precision = MHD_FP64;
   cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
-  size_t w1_len = 0, w2_len = 0;  // complex values
+  cplx32 *tw32 = nullptr;
+  size_t w1_len = 0, w2_len = 0;  // bytes / 16
   double *part = nullptr;
   size_t part_len = 0;
   mhd::TimeState *ts = nullptr;
@@ -96,31 +99,36 @@ struct DeviceGuard {
 
 bool valid_n(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
 
+// Buffer sizes in 16-byte units (one FP64 complex).  The step of all instances runs in the
+// context's precision (8-byte complex values in the mixed mode); set/get/diagnostics and the
+// inverse transform of an RHS run one instance at a time in FP64.
 struct Sizes {
   size_t S, W1, W2, part;
 };
 
-Sizes sizes_for(const mhd::Dims &d) {
+Sizes sizes_for(const mhd::Dims &d, int precision) {
   const size_t n = d.n, nx = d.nx, nk = d.nk, b = d.batch;
+  const size_t elem = precision == MHD_FP64 ? 16 : 8;
   Sizes s;
   s.S = b * 7 * d.spec;
-  size_t w1 = b * 7 * n * nk * nx;
-  w1 = std::max(w1, b * 12 * n * n * nx);
-  w1 = std::max(w1, b * 12 * d.spec);
-  w1 = std::max(w1, (7 * n * n * n + 1) / 2);  // real 7 N^3 staging (set/get/rhs)
-  w1 = std::max(w1, n * n * (n / 2 + 1));      // expanded spectrum
-  size_t w2 = b * 7 * n * n * nx;
-  w2 = std::max(w2, b * 12 * n * nk * nx);
-  w2 = std::max(w2, 7 * d.spec);
-  s.W1 = w1;
-  s.W2 = w2;
+  // step (all instances, working precision)
+  size_t w1 = std::max(std::max(7 * n * nk * nx, 12 * n * n * nx), 12 * d.spec) * b * elem;
+  size_t w2 = std::max(7 * n * n * nx, 12 * n * nk * nx) * b * elem;
+  // one instance in FP64
+  w1 = std::max(w1, std::max(7 * n * nk * nx, 12 * n * n * nx) * 16);
+  w1 = std::max(w1, 7 * n * n * n * 8);         // real 7 N^3 staging (set/get/rhs)
+  w1 = std::max(w1, n * n * (n / 2 + 1) * 16);  // expanded spectrum
+  w2 = std::max(w2, std::max(7 * n * n * nx, 12 * n * nk * nx) * 16);
+  w2 = std::max(w2, 7 * d.spec * 16);            // RHS spectra of one instance
+  s.W1 = (w1 + 15) / 16;
+  s.W2 = (w2 + 15) / 16;
   s.part = std::max((size_t)b * mhd::flux_x_blocks_per_instance(d.n), (size_t)mhd::diag_x_blocks(d.n) * 8);
   return s;
 }
 
-size_t footprint(const mhd::Dims &d) {
-  const Sizes s = sizes_for(d);
-  return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + s.part * sizeof(double) +
+size_t footprint(const mhd::Dims &d, int precision) {
+  const Sizes s = sizes_for(d, precision);
+  return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + d.n * sizeof(cplx32) + s.part * sizeof(double) +
          d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) + 64 * sizeof(double);
 }
 
@@ -220,8 +228,8 @@ mhd_status spectra_to_real(mhd_ctx *c, const cplx64 *src, double *a, double *b3,
 extern "C" {
 
 size_t mhd_footprint_bytes(int32_t n, int32_t precision, int32_t batch) {
-  if (!valid_n(n) || batch < 1 || precision != MHD_FP64) return 0;
-  return footprint(mhd::make_dims(n, batch));
+  if (!valid_n(n) || batch < 1 || (precision != MHD_FP64 && precision != MHD_FP32_MIXED)) return 0;
+  return footprint(mhd::make_dims(n, batch), precision);
 }
 
 const char *mhd_last_error(const mhd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -241,7 +249,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (!out) return MHD_EINVAL;
   *out = nullptr;
   if (!p || !phys) return MHD_EINVAL;
-  if (!valid_n(p->n) || p->batch < 1 || p->precision != MHD_FP64 || p->reserved0 != 0) return MHD_EINVAL;
+  if (!valid_n(p->n) || p->batch < 1 || p->reserved0 != 0) return MHD_EINVAL;
+  if (p->precision != MHD_FP64 && p->precision != MHD_FP32_MIXED) return MHD_EINVAL;
   if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return MHD_EINVAL;
   for (int i = 0; i < p->batch; ++i) {
     if (!(phys[i].nu >= 0.0) || !(phys[i].eta >= 0.0) || !(phys[i].cs > 0.0) || !isfinite(phys[i].nu) ||
@@ -253,6 +262,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (!c) return MHD_ENOMEM;
   c->p = *p;
   c->d = mhd::make_dims(p->n, p->batch);
+  c->precision = p->precision;
   c->stream = (cudaStream_t)p->stream;
   c->dt_fixed = p->dt > 0.0 ? p->dt : 0.0;
   c->cfl_adv = p->cfl_adv > 0.0 ? p->cfl_adv : 0.2;
@@ -263,7 +273,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
     delete c;
     return MHD_ECUDA;
   }
-  const Sizes s = sizes_for(c->d);
+  const Sizes s = sizes_for(c->d, c->precision);
   c->w1_len = s.W1;
   c->w2_len = s.W2;
   c->part_len = s.part;
@@ -272,6 +282,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->W1 = (cplx64 *)dalloc(c, s.W1 * sizeof(cplx64))) != nullptr;
   ok = ok && (c->W2 = (cplx64 *)dalloc(c, s.W2 * sizeof(cplx64))) != nullptr;
   ok = ok && (c->tw = (cplx64 *)dalloc(c, (size_t)c->d.n * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
@@ -286,8 +297,11 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   std::vector<mhd::PhysDev> pd(p->batch);
   for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs};
   const std::vector<cplx64> w = twiddles(c->d.n);
+  std::vector<cplx32> w32(w.size());
+  for (size_t i = 0; i < w.size(); ++i) w32[i] = cplx32{(float)w[i].re, (float)w[i].im};
   cudaError_t e = cudaMemcpyAsync(c->phys, pd.data(), pd.size() * sizeof(mhd::PhysDev), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w.data(), w.size() * sizeof(cplx64), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw32, w32.data(), w32.size() * sizeof(cplx32), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
@@ -352,6 +366,8 @@ mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out
   return MHD_OK;
 }
 
+}  // extern "C"
+
 // Event marks around the launches of mhd_step while profiling is on.
 static cudaError_t prof_begin(mhd_ctx *c, int kind, bool on) {
   if (!on) return cudaSuccess;
@@ -383,21 +399,44 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 
 // Steps 1-6 of the pass order for the instances in `d` starting at state `S`; leaves the 12
 // product spectra in W1.
-static mhd_status flux_spectra(mhd_ctx *c, const mhd::Dims &d, const cplx64 *S, const mhd::PhysDev *phys,
-                               mhd::TimeState *ts, mhd::StepCoef *coef, bool advance) {
+// CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.
+template <typename CF>
+static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const cplx64 *S, const mhd::PhysDev *phys,
+                                 mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
-  LAUNCH(0, mhd::launch_col_inverse(S, c->W1, d.n, b * 7, d.nk * d.nx, c->tw, c->stream));
-  LAUNCH(1, mhd::launch_col_inverse(c->W1, c->W2, d.n, b * 7 * d.n, d.nx, c->tw, c->stream));
-  LAUNCH(2, mhd::launch_flux_x(c->W2, c->W1, phys, c->part, d, c->tw, c->stream));
+  CF *w1 = reinterpret_cast<CF *>(c->W1);
+  CF *w2 = reinterpret_cast<CF *>(c->W2);
+  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream));
+  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream));
+  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, c->part, d, tw, c->stream));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(c->part, mhd::flux_x_blocks_per_instance(d.n), phys, ts, coef, d, c->dt_fixed,
                                   c->cfl_adv, c->cfl_visc, c->stream));
   }
-  LAUNCH(4, mhd::launch_col_forward(c->W1, c->W2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw, c->stream));
-  LAUNCH(5, mhd::launch_col_forward(c->W2, c->W1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw, c->stream));
+  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream));
+  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream));
   return MHD_OK;
 }
+
+// Steps 1-6, then step 7: assembly into `rhs_out` (mode 0) or the AB2 update (mode 1).
+static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, cplx64 *S, cplx64 *H, cplx64 *rhs_out,
+                              const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, int mode) {
+  const bool advance = mode == 1;
+  const bool prof = advance && c->profiling;
+  mhd_status st;
+  if (c->precision == MHD_FP64) {
+    if ((st = flux_spectra_t<cplx64>(c, d, S, phys, ts, coef, advance, c->tw))) return st;
+    LAUNCH(6, mhd::launch_assemble(c->W1, S, H, rhs_out, phys, coef, mode, d, c->stream));
+  } else {
+    if ((st = flux_spectra_t<cplx32>(c, d, S, phys, ts, coef, advance, c->tw32))) return st;
+    LAUNCH(6, mhd::launch_assemble(reinterpret_cast<const cplx32 *>(c->W1), S, H, rhs_out, phys, coef, mode, d,
+                                   c->stream));
+  }
+  return MHD_OK;
+}
+
+extern "C" {
 
 mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *db, int32_t on_device) {
   mhd_status st = check_inst(c, inst);
@@ -406,9 +445,8 @@ mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *d
   if (!c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
   DeviceGuard g(c->device);
   const mhd::Dims d = one(c);
-  const cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
-  if ((st = flux_spectra(c, d, Si, c->phys + inst, nullptr, nullptr, false))) return st;
-  CK(mhd::launch_assemble(c->W1, const_cast<cplx64 *>(Si), nullptr, c->W2, c->phys + inst, nullptr, 0, d, c->stream));
+  cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
+  if ((st = rhs_or_step(c, d, Si, nullptr, c->W2, c->phys + inst, nullptr, nullptr, 0))) return st;
   // W2 holds the RHS spectra; inverse_zy reads its source before overwriting W2
   CK(mhd::launch_col_inverse(c->W2, c->W1, d.n, 7, d.nk * d.nx, c->tw, c->stream));
   CK(mhd::launch_col_inverse(c->W1, c->W2, d.n, 7 * d.n, d.nx, c->tw, c->stream));
@@ -428,11 +466,9 @@ mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
   for (int i = 0; i < c->d.batch; ++i)
     if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
   DeviceGuard g(c->device);
-  const bool prof = c->profiling;
   for (int s = 0; s < nsteps; ++s) {
-    mhd_status st = flux_spectra(c, c->d, c->S, c->phys, c->ts, c->coef, true);
+    mhd_status st = rhs_or_step(c, c->d, c->S, c->H, nullptr, c->phys, c->ts, c->coef, 1);
     if (st) return st;
-    LAUNCH(6, mhd::launch_assemble(c->W1, c->S, c->H, nullptr, c->phys, c->coef, 1, c->d, c->stream));
   }
   return MHD_OK;
 }

@@ -22,9 +22,13 @@ namespace mhd {
 constexpr int kStateFields = 7;  // rho, m_x, m_y, m_z, B_x, B_y, B_z
 constexpr int kFluxFields = 12;  // T_xx T_yy T_zz T_xy T_xz T_yz, E_x E_y E_z, u_x u_y u_z
 
-struct __align__(16) cplx64 {
-  double re, im;
+template <typename R>
+struct alignas(2 * sizeof(R)) cplx {
+  using value_type = R;
+  R re, im;
 };
+using cplx64 = cplx<double>;
+using cplx32 = cplx<float>;
 
 // Per-instance time-stepping state, device resident.
 struct TimeState {
@@ -70,20 +74,32 @@ inline Dims make_dims(int n, int batch) {
 }
 
 // ---- launchers (each returns the launch status; all work goes on `s`) ----
+// The FFT passes exist in two precisions: FP64 throughout, and FP32 arithmetic and storage
+// (the first inverse pass reads the FP64 state and writes FP32).  The transform arithmetic runs
+// in the precision of the output; `tw` is the table W_N^m = exp(-2 pi i m / N), m < N, rounded to
+// that precision.
 
 // Column FFTs along the middle axis of [nslab][L][C]: inverse (sign +1) expands L from the
 // NK kept indices to N; forward (sign -1) keeps only the NK kept outputs and multiplies by
-// `scale`.  `tw` is the table W_N^m = exp(-2 pi i m / N), m < N.
+// `scale`.
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                const cplx64 *tw, cudaStream_t s);
+cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
+                               const cplx32 *tw, cudaStream_t s);
+cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
+                               const cplx32 *tw, cudaStream_t s);
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                double scale, const cplx64 *tw, cudaStream_t s);
+cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
+                               double scale, const cplx32 *tw, cudaStream_t s);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and per-block maxima of
 // |u| + c_f into `smax_part` ([batch][x_blocks(n)]).
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
                           const Dims &d, const cplx64 *tw, cudaStream_t s);
+cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, double *smax_part,
+                          const Dims &d, const cplx32 *tw, cudaStream_t s);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
@@ -109,6 +125,9 @@ cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *p
 // Spectral assembly of the RHS from the 12 product spectra (scaled by N^-3) and the state.
 // mode 0: write the RHS to `rhs_out`; mode 1: AB2 update of `state` and `hist` with `coef`.
 cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                            cudaStream_t s);
+cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
                             const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
                             cudaStream_t s);
 

@@ -22,6 +22,7 @@ LIBRARY = os.path.join(_PKG, "libmhd_gb300.so")
 
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ESTATE, MHD_ENONFINITE, MHD_ETIMEOUT, MHD_EBUSY = range(8)
 MHD_FP64 = 0
+MHD_FP32_MIXED = 1
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_ESTATE",
                 5: "MHD_ENONFINITE", 6: "MHD_ETIMEOUT", 7: "MHD_EBUSY"}
 
