@@ -74,16 +74,21 @@ def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
     k = (n - 1) // 3
     nx, nk = k + 1, 2 * k + 1
     spec = nk * nk * nx
-    c = 16.0 if precision == "fp64" else 8.0  # complex value of the passes; the state is FP64
+    # complex value of the passes: 16 B in FP64, 8 B in the mixed mode, whose state is a pair of
+    # FP32 arrays (hi, lo) and whose history is FP32
+    c = 16.0 if precision == "fp64" else 8.0
+    state_read = 16.0 if precision == "fp64" else 8.0   # the inverse z pass reads hi only
+    # assembly per mode: 12 products + state + history read, state + history written
+    asm = (12 * 16 + 4 * 7 * 16) if precision == "fp64" else (12 + 7 * 2 + 7 + 7 * 3) * 8
     fft = 5.0 * n * math.log2(n)
     m = {
-        "inverse_z": (7 * (spec * 16 + n * nk * nx * c), 7 * nk * nx * fft),
+        "inverse_z": (7 * (spec * state_read + n * nk * nx * c), 7 * nk * nx * fft),
         "inverse_y": (7 * (n * nk * nx + n * n * nx) * c, 7 * n * nx * fft),
         "flux_x": ((7 + 12) * n * n * nx * c, (7 + 12) * (n * n / 2) * fft + 49.0 * n ** 3),
         "step_dt": (8.0 * n * n / 2, 0.0),
         "forward_y": (12 * (n * n * nx + n * nk * nx) * c, 12 * n * nx * fft),
         "forward_z": (12 * (n * nk * nx + spec) * c, 12 * nk * nx * fft),
-        "assemble_ab2": (12 * spec * c + (7 + 7 + 7 + 7) * spec * 16, 110.0 * spec),
+        "assemble_ab2": (asm * spec, 110.0 * spec),
     }
     return {key: (b * batch, f * batch) for key, (b, f) in m.items()}
 

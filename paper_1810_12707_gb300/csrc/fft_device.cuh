@@ -95,6 +95,16 @@ __device__ __forceinline__ void dft_small(C *v) {
   else dft2<DIR>(v);
 }
 
+// ---- shared-memory pencil layout ----
+// A pencil element e lives at sm_idx<C>(e) = e + e / (128 / sizeof(C)): one pad element per 128
+// bytes.  The first Stockham stage writes with a stride of 8 elements; without the pad every lane
+// of a wavefront would hit the same banks.  Pencils are `pencil_pitch` apart, an odd number of
+// elements, so that lanes walking across pencils (the column loads) also spread over the banks.
+template <typename C>
+__host__ __device__ constexpr int sm_idx(int e) { return e + e / (int)(128 / sizeof(C)); }
+template <typename C>
+__host__ __device__ constexpr int pencil_pitch(int n) { return sm_idx<C>(n) | 1; }
+
 // ---- Stockham pencil FFT ----
 //
 // The transform of length N = product of radices (8 while at least 8 points remain, then 4 or
@@ -123,7 +133,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         const int k = j % NS;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          C x = buf[j + r * (N / R)];
+          C x = buf[sm_idx<C>(j + r * (N / R))];
           if (NS > 1 && r > 0) {
             const C w = tw[r * k * TWSTEP];
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
@@ -141,7 +151,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         const int k = j % NS;
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[base + r * NS] = v[b * R + r];
+        for (int r = 0; r < R; ++r) buf[sm_idx<C>(base + r * NS)] = v[b * R + r];
       }
     }
     __syncthreads();

@@ -22,7 +22,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CC *sm = reinterpret_cast<CC *>(smem_raw);
   constexpr int TPP = N / 8;
-  constexpr int P = N + 1;
+  constexpr int P = pencil_pitch<CC>(N);
   const int NK = 2 * K + 1;
   const int lin = DIR > 0 ? NK : N;
   const int lout = DIR > 0 ? N : NK;
@@ -38,13 +38,13 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
     CC v = {0, 0};
     if (col < cols) v = c_cvt<CC>(src[(size_t)l * cols + col]);
     const int f = DIR > 0 ? kept_to_fft(l, K, N) : l;
-    sm[c * P + f] = v;
+    sm[c * P + sm_idx<CC>(f)] = v;
   }
   if (DIR > 0) {
     const int nz = N - NK;  // FFT indices K+1 .. N-K-1 are outside the kept set
     for (int q = threadIdx.x; q < nz * tc; q += nthr) {
       const int l = q / tc, c = q - l * tc;
-      sm[c * P + K + 1 + l] = CC{0, 0};
+      sm[c * P + sm_idx<CC>(K + 1 + l)] = CC{0, 0};
     }
   }
   __syncthreads();
@@ -60,7 +60,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
     const int col = c0 + c;
     if (col < cols) {
       const int f = DIR > 0 ? l : kept_to_fft(l, K, N);
-      CC v = sm[c * P + f];
+      CC v = sm[c * P + sm_idx<CC>(f)];
       if (DIR < 0) v = c_scale(v, (typename CC::value_type)scale);
       dst[(size_t)l * cols + col] = c_cvt<CO>(v);
     }
@@ -86,7 +86,7 @@ cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scal
   const int K = (N - 1) / 3;
   const int tc = pick_tc(N, cols);
   const int ntiles = (cols + tc - 1) / tc;
-  const size_t smem = (size_t)tc * (N + 1) * sizeof(CO);
+  const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO>>((int)smem);
     if (e != cudaSuccess) return e;

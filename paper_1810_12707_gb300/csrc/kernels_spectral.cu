@@ -98,6 +98,112 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict_
   }
 }
 
+// Mixed precision: RHS in FP32 from the FP32 products and the high parts of the state, update of
+// the double-float state (hi, lo) by an error-free two-sum (Knuth), no FP64 arithmetic.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
+  const float s = hi + d;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (d - bb) + lo;  // exact rounding error of hi + d, plus lo
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+__global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, cplx32 *__restrict__ s_hi,
+                                   cplx32 *__restrict__ s_lo, cplx32 *__restrict__ hist,
+                                   cplx64 *__restrict__ rhs_out, const PhysDev *__restrict__ phys,
+                                   const StepCoef *__restrict__ coef, int mode, int K, int batch, float inv_n3) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const size_t total = spec * batch;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(idx / spec);
+    const size_t m = idx - (size_t)inst * spec;
+    if (mode == 1 && coef[inst].skip) continue;
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    const float kx = (float)kxi, ky = (float)kept_wave((int)(t % NK), K), kz = (float)kept_wave((int)(t / NK), K);
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const PhysDev ph = phys[inst];
+    const float nuk2 = (float)ph.nu * k2, etak2 = (float)ph.eta * k2, cs2 = (float)(ph.cs * ph.cs);
+
+    const size_t base7 = (size_t)inst * 7 * spec + m;
+    const cplx32 *F = flux + (size_t)inst * 12 * spec + m;
+    cplx32 y[7], f[12];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) y[q] = s_hi[base7 + q * spec];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
+    const cplx32 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+    const cplx32 Ex = f[6], Ey = f[7], Ez = f[8];
+    cplx32 r[7];
+    {
+      const cplx32 sm = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+      r[0] = cplx32{sm.im, -sm.re};
+    }
+    {
+      const float kk[3] = {kx, ky, kz};
+      const cplx32 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cplx32 g = {kx * T[a][0].re + ky * T[a][1].re + kz * T[a][2].re + kk[a] * cs2 * y[0].re,
+                          kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im + kk[a] * cs2 * y[0].im};
+        const cplx32 u = f[9 + a];
+        r[1 + a] = cplx32{g.im - nuk2 * u.re, -g.re - nuk2 * u.im};
+      }
+    }
+    {
+      const cplx32 c[3] = {{ky * Ez.re - kz * Ey.re, ky * Ez.im - kz * Ey.im},
+                           {kz * Ex.re - kx * Ez.re, kz * Ex.im - kx * Ez.im},
+                           {kx * Ey.re - ky * Ex.re, kx * Ey.im - ky * Ex.im}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        r[4 + a] = cplx32{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
+    }
+    if (mode == 0) {
+      cplx64 *R = rhs_out + (size_t)inst * 7 * spec + m;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) R[q * spec] = c_cvt<cplx64>(r[q]);
+    } else {
+      const StepCoef cf = coef[inst];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        cplx32 inc = {cf.fa1 * r[q].re, cf.fa1 * r[q].im};
+        if (cf.fa0 != 0.f) {
+          const cplx32 h = hist[base7 + q * spec];
+          inc.re += cf.fa0 * h.re;
+          inc.im += cf.fa0 * h.im;
+        }
+        cplx32 lo = s_lo[base7 + q * spec];
+        float hr = y[q].re, hi_ = y[q].im;
+        df_add(hr, lo.re, cf.fdt * inc.re);
+        df_add(hi_, lo.im, cf.fdt * inc.im);
+        s_hi[base7 + q * spec] = cplx32{hr, hi_};
+        s_lo[base7 + q * spec] = lo;
+        hist[base7 + q * spec] = r[q];
+      }
+    }
+  }
+}
+
+__global__ void split_state_kernel(const cplx64 *__restrict__ in, cplx32 *__restrict__ hi, cplx32 *__restrict__ lo,
+                                   size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx64 v = in[i];
+    const float hr = (float)v.re, hm = (float)v.im;
+    hi[i] = cplx32{hr, hm};
+    lo[i] = cplx32{(float)(v.re - (double)hr), (float)(v.im - (double)hm)};
+  }
+}
+
+__global__ void combine_state_kernel(const cplx32 *__restrict__ hi, const cplx32 *__restrict__ lo,
+                                     cplx64 *__restrict__ out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx32 a = hi[i], b = lo[i];
+    out[i] = cplx64{(double)a.re + (double)b.re, (double)a.im + (double)b.im};
+  }
+}
+
 // One block per instance: maximum of the CFL partials, the step size, the Adams-Bashforth
 // coefficients of this step, and the advance of the time state.
 __global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
@@ -111,7 +217,7 @@ __global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
   m = block_nan_max(m, red);
   if (threadIdx.x != 0) return;
   TimeState s = ts[inst];
-  StepCoef c = {0.0, 0.0, 0.0, 1, 0};
+  StepCoef c = {0.0, 0.0, 0.0, 0.f, 0.f, 0.f, 1};
   if (s.status == 0) {
     double dt;
     if (dt_fixed > 0.0) {
@@ -138,6 +244,9 @@ __global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
         c.a1 = 1.0;
         c.a0 = 0.0;
       }
+      c.fdt = (float)c.dt;
+      c.fa1 = (float)c.a1;
+      c.fa0 = (float)c.a0;
       s.t += dt;
       s.dt_prev = dt;
       s.dt_last = dt;
@@ -251,6 +360,26 @@ cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cpl
                             const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
                             cudaStream_t s) {
   return assemble_any(flux, state, hist, rhs_out, phys, coef, mode, d, s);
+}
+
+cudaError_t launch_assemble_df(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, cplx64 *rhs_out,
+                               const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                               cudaStream_t s) {
+  const size_t total = d.spec * d.batch;
+  const float inv_n3 = (float)(1.0 / ((double)d.n * d.n * d.n));
+  assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, s_hi, s_lo, hist, rhs_out, phys, coef, mode, d.k,
+                                                          d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_state(const cplx64 *in, cplx32 *hi, cplx32 *lo, size_t count, cudaStream_t s) {
+  split_state_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, hi, lo, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out, size_t count, cudaStream_t s) {
+  combine_state_kernel<<<grid_for(count, 256), 256, 0, s>>>(hi, lo, out, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys, TimeState *ts,

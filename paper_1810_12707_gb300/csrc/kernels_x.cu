@@ -54,14 +54,14 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // C: complex type of the data and of all arithmetic (cplx64 or cplx32); the CFL maxima are
 // combined in FP64.
 template <int N, typename C>
-__global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
+__global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, double *__restrict__ smax_part,
                               int K, int blocks_per_inst, const C *__restrict__ tw) {
   using R = typename C::value_type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = reinterpret_cast<C *>(smem_raw);
   __shared__ double red[32];
-  constexpr int P = N + 1;
+  constexpr int P = pencil_pitch<C>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
   const int NX = K + 1;
@@ -81,15 +81,15 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict
     if (k == 0) {
       pen[0] = C{x0.re, x1.re};
     } else {
-      pen[k] = C{x0.re - x1.im, x0.im + x1.re};
-      pen[N - k] = C{x0.re + x1.im, x1.re - x0.im};
+      pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
+      pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
     }
   }
   for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
     const int z = q % (N - 2 * K - 1);
     const int r = q / (N - 2 * K - 1);
     const int f = r % 7, p = r / 7;
-    sm[(p * 12 + f) * P + K + 1 + z] = C{0, 0};
+    sm[(p * 12 + f) * P + sm_idx<C>(K + 1 + z)] = C{0, 0};
   }
   __syncthreads();
 
@@ -98,10 +98,10 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict
 
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
   const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
-  double smax = 0.0;
+  R smax = 0;
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
-    C *b = sm + p * 12 * P + j;
+    C *b = sm + p * 12 * P + sm_idx<C>(j);
     R v[2][7];
 #pragma unroll
     for (int f = 0; f < 7; ++f) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict
       bd[2 * 10 * P + h] = uy;
       bd[2 * 11 * P + h] = uz;
       const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 / rho);
-      smax = nan_max(smax, (double)s);
+      smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
     }
   }
   __syncthreads();
@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(kMaxThreads) flux_x_kernel(const C *__restrict
     const int r = q / NX;
     const int f = r % 12, p = r / 12;
     const C *pen = sm + (p * 12 + f) * P;
-    const C z = pen[k], zc = pen[(N - k) & (N - 1)];
+    const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
     C *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
     dst[k] = C{half * (z.re + zc.re), half * (z.im - zc.im)};
     dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
   }
 
-  const double m = block_nan_max(smax, red);
+  const double m = block_nan_max((double)smax, red);
   if (threadIdx.x == 0) smax_part[(size_t)inst * blocks_per_inst + bl] = m;
 }
 
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
                              const cplx64 *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
-  constexpr int P = N + 1;
+  constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
   const int NX = K + 1;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
     const int p = q / N, j = q - p * N;
     const size_t i0 = (row0 + 2 * p) * N + j, i1 = i0 + N;
     const double r0 = rho[i0], r1 = rho[i1];
-    cplx64 *pen = sm + p * 7 * P + j;
+    cplx64 *pen = sm + p * 7 * P + sm_idx<cplx64>(j);
     pen[0] = cplx64{r0, r1};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
     const int r = q / NX;
     const int f = r % 7, p = r / 7;
     const cplx64 *pen = sm + (p * 7 + f) * P;
-    const cplx64 z = pen[k], zc = pen[(N - k) & (N - 1)];
+    const cplx64 z = pen[sm_idx<cplx64>(k)], zc = pen[sm_idx<cplx64>((N - k) & (N - 1))];
     cplx64 *dst = out + ((size_t)f * NN + row0 + 2 * p) * NX;
     dst[k] = cplx64{0.5 * (z.re + zc.re), 0.5 * (z.im - zc.im)};
     dst[NX + k] = cplx64{0.5 * (z.im + zc.im), 0.5 * (zc.re - z.re)};
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
                              const cplx64 *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
-  constexpr int P = N + 1;
+  constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
   const int NX = K + 1;
@@ -224,14 +224,14 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     if (k == 0) {
       pen[0] = cplx64{x0.re, x1.re};
     } else {
-      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
-      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+      pen[sm_idx<cplx64>(k)] = cplx64{x0.re - x1.im, x0.im + x1.re};
+      pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
     }
   }
   for (int q = threadIdx.x; q < nf * PAIRS * (N - 2 * K - 1); q += nthr) {
     const int z = q % (N - 2 * K - 1);
     const int r = q / (N - 2 * K - 1);
-    sm[r * P + K + 1 + z] = cplx64{0.0, 0.0};
+    sm[r * P + sm_idx<cplx64>(K + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
   fft_pencils<N, +1>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     const int j = q % N;
     const int r = q / N;
     const int f = r % nf, p = r / nf;
-    const cplx64 z = sm[(p * nf + f) * P + j];
+    const cplx64 z = sm[(p * nf + f) * P + sm_idx<cplx64>(j)];
     const size_t i0 = f * N3 + (row0 + 2 * p) * N + j;
     out[i0] = z.re;
     out[i0 + N] = z.im;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   __shared__ double red[32];
-  constexpr int P = N + 1;
+  constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
   const int NX = K + 1;
@@ -272,14 +272,14 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
     if (k == 0) {
       pen[0] = cplx64{x0.re, x1.re};
     } else {
-      pen[k] = cplx64{x0.re - x1.im, x0.im + x1.re};
-      pen[N - k] = cplx64{x0.re + x1.im, x1.re - x0.im};
+      pen[sm_idx<cplx64>(k)] = cplx64{x0.re - x1.im, x0.im + x1.re};
+      pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
     }
   }
   for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
     const int z = q % (N - 2 * K - 1);
     const int r = q / (N - 2 * K - 1);
-    sm[r * P + K + 1 + z] = cplx64{0.0, 0.0};
+    sm[r * P + sm_idx<cplx64>(K + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
   fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
   double smax = 0.0;
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
-    const cplx64 *b = sm + p * 7 * P + j;
+    const cplx64 *b = sm + p * 7 * P + sm_idx<cplx64>(j);
     double v[2][7];
 #pragma unroll
     for (int f = 0; f < 7; ++f) {
@@ -335,7 +335,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, double *part, const
   constexpr int PAIRS = pairs_for(N);
   const int bpi = N * N / (2 * PAIRS);
   const int threads = threads_for(N, 12 * PAIRS);
-  const size_t smem = (size_t)12 * PAIRS * (N + 1) * sizeof(C);
+  const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<flux_x_kernel<N, C>>((int)smem);
     if (e != cudaSuccess) return e;
@@ -351,7 +351,7 @@ cudaError_t set_n(const double *rho, const double *u, const double *b, cplx64 *o
   constexpr int PAIRS = pairs_for(N);
   const int blocks = N * N / (2 * PAIRS);
   const int threads = threads_for(N, 7 * PAIRS);
-  const size_t smem = (size_t)7 * PAIRS * (N + 1) * sizeof(cplx64);
+  const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<set_x_kernel<N>>((int)smem);
     if (e != cudaSuccess) return e;
@@ -365,7 +365,7 @@ cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cp
   constexpr int PAIRS = pairs_for(N);
   const int blocks = N * N / (2 * PAIRS);
   const int threads = threads_for(N, nf * PAIRS);
-  const size_t smem = (size_t)nf * PAIRS * (N + 1) * sizeof(cplx64);
+  const size_t smem = (size_t)nf * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<get_x_kernel<N>>((int)smem);
     if (e != cudaSuccess) return e;
@@ -380,7 +380,7 @@ cudaError_t diag_n(const cplx64 *in, const PhysDev *phys, double *part, const Di
   constexpr int PAIRS = pairs_for(N);
   const int blocks = N * N / (2 * PAIRS);
   const int threads = threads_for(N, 7 * PAIRS);
-  const size_t smem = (size_t)7 * PAIRS * (N + 1) * sizeof(cplx64);
+  const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<diag_x_kernel<N>>((int)smem);
     if (e != cudaSuccess) return e;

@@ -38,6 +38,7 @@ struct mhd_ctx {
   int precision = MHD_FP64;
   cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
   cplx32 *tw32 = nullptr;
+  cplx64 *S64 = nullptr;  // mixed precision: FP64 copy of one instance's state for set/get/diagnostics
   size_t w1_len = 0, w2_len = 0;  // bytes / 16
   double *part = nullptr;
   size_t part_len = 0;
@@ -196,6 +197,26 @@ mhd::Dims one(const mhd_ctx *c) {
   return d;
 }
 
+// State of instance `inst`.  FP64: S is [b][7][spec] complex doubles.  Mixed: the same bytes hold
+// S_hi [b][7][spec] then S_lo [b][7][spec] (FP32 complex), and H holds [b][7][spec] FP32 complex.
+cplx64 *state64(mhd_ctx *c, int inst) { return c->S + (size_t)inst * 7 * c->d.spec; }
+cplx32 *state_hi(mhd_ctx *c, int inst) { return reinterpret_cast<cplx32 *>(c->S) + (size_t)inst * 7 * c->d.spec; }
+cplx32 *state_lo(mhd_ctx *c, int inst) {
+  return reinterpret_cast<cplx32 *>(c->S) + ((size_t)c->d.batch + inst) * 7 * c->d.spec;
+}
+cplx32 *hist32(mhd_ctx *c, int inst) { return reinterpret_cast<cplx32 *>(c->H) + (size_t)inst * 7 * c->d.spec; }
+
+// FP64 spectra of instance `inst` for the FP64 utility chains (the mixed state is combined first).
+mhd_status state_fp64(mhd_ctx *c, int inst, const cplx64 **out) {
+  if (c->precision == MHD_FP64) {
+    *out = state64(c, inst);
+    return MHD_OK;
+  }
+  CK(mhd::launch_combine_state(state_hi(c, inst), state_lo(c, inst), c->S64, 7 * c->d.spec, c->stream));
+  *out = c->S64;
+  return MHD_OK;
+}
+
 // inverse z then inverse y of 7 fields of one instance: S-layout `src` -> W2 [7][z][y][kx]
 mhd_status inverse_zy(mhd_ctx *c, const cplx64 *src) {
   const mhd::Dims &d = c->d;
@@ -283,6 +304,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->W2 = (cplx64 *)dalloc(c, s.W2 * sizeof(cplx64))) != nullptr;
   ok = ok && (c->tw = (cplx64 *)dalloc(c, (size_t)c->d.n * sizeof(cplx64))) != nullptr;
   ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
+  if (c->precision != MHD_FP64) ok = ok && (c->S64 = (cplx64 *)dalloc(c, 7 * c->d.spec * sizeof(cplx64))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
@@ -333,12 +355,17 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
     uu = real + n3;
     bb = real + 4 * n3;
   }
-  cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
-  cplx64 *Hi = c->H + (size_t)inst * 7 * d.spec;
+  const bool fp64 = c->precision == MHD_FP64;
+  cplx64 *Si = fp64 ? state64(c, inst) : c->S64;
   CK(mhd::launch_set_x(r, uu, bb, c->W2, one(c), c->tw, c->stream));
   CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 7 * d.n, d.nx, 1.0, c->tw, c->stream));
   CK(mhd::launch_col_forward(c->W1, Si, d.n, 7, d.nk * d.nx, 1.0 / ((double)n3), c->tw, c->stream));
-  CK(cudaMemsetAsync(Hi, 0, 7 * d.spec * sizeof(cplx64), c->stream));
+  if (fp64) {
+    CK(cudaMemsetAsync(c->H + (size_t)inst * 7 * d.spec, 0, 7 * d.spec * sizeof(cplx64), c->stream));
+  } else {
+    CK(mhd::launch_split_state(c->S64, state_hi(c, inst), state_lo(c, inst), 7 * d.spec, c->stream));
+    CK(cudaMemsetAsync(hist32(c, inst), 0, 7 * d.spec * sizeof(cplx32), c->stream));
+  }
   CK(cudaMemsetAsync(c->ts + inst, 0, sizeof(mhd::TimeState), c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->is_set[inst] = 1;
@@ -350,7 +377,9 @@ mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, doubl
   if (st) return st;
   if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
   DeviceGuard g(c->device);
-  return spectra_to_real(c, c->S + (size_t)inst * 7 * c->d.spec, rho, m, b, on_device);
+  const cplx64 *src = nullptr;
+  if ((st = state_fp64(c, inst, &src))) return st;
+  return spectra_to_real(c, src, rho, m, b, on_device);
 }
 
 mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out, int32_t on_device) {
@@ -360,7 +389,9 @@ mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out
   DeviceGuard g(c->device);
   const mhd::Dims &d = c->d;
   const size_t full = (size_t)d.n * d.n * (d.n / 2 + 1);
-  CK(mhd::launch_expand_spectrum(c->S + ((size_t)inst * 7 + field) * d.spec, c->W1, d, c->stream));
+  const cplx64 *src = nullptr;
+  if ((st = state_fp64(c, inst, &src))) return st;
+  CK(mhd::launch_expand_spectrum(src + (size_t)field * d.spec, c->W1, d, c->stream));
   if ((st = copy_out(c, out, c->W1, full * sizeof(cplx64), on_device))) return st;
   CK(cudaStreamSynchronize(c->stream));
   return MHD_OK;
@@ -400,8 +431,8 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 // Steps 1-6 of the pass order for the instances in `d` starting at state `S`; leaves the 12
 // product spectra in W1.
 // CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.
-template <typename CF>
-static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const cplx64 *S, const mhd::PhysDev *phys,
+template <typename CF, typename CS>
+static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, const mhd::PhysDev *phys,
                                  mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
@@ -419,19 +450,24 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const cplx64 *S
   return MHD_OK;
 }
 
-// Steps 1-6, then step 7: assembly into `rhs_out` (mode 0) or the AB2 update (mode 1).
-static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, cplx64 *S, cplx64 *H, cplx64 *rhs_out,
+// Steps 1-6, then step 7: assembly into `rhs_out` (mode 0) or the AB2 update (mode 1), for the
+// `d.batch` instances starting at `inst0`.
+static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 *rhs_out,
                               const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, int mode) {
   const bool advance = mode == 1;
   const bool prof = advance && c->profiling;
   mhd_status st;
   if (c->precision == MHD_FP64) {
-    if ((st = flux_spectra_t<cplx64>(c, d, S, phys, ts, coef, advance, c->tw))) return st;
+    cplx64 *S = state64(c, inst0);
+    cplx64 *H = mode == 1 ? c->H + (size_t)inst0 * 7 * d.spec : nullptr;
+    if ((st = flux_spectra_t<cplx64>(c, d, (const cplx64 *)S, phys, ts, coef, advance, c->tw))) return st;
     LAUNCH(6, mhd::launch_assemble(c->W1, S, H, rhs_out, phys, coef, mode, d, c->stream));
   } else {
-    if ((st = flux_spectra_t<cplx32>(c, d, S, phys, ts, coef, advance, c->tw32))) return st;
-    LAUNCH(6, mhd::launch_assemble(reinterpret_cast<const cplx32 *>(c->W1), S, H, rhs_out, phys, coef, mode, d,
-                                   c->stream));
+    cplx32 *hi = state_hi(c, inst0), *lo = state_lo(c, inst0);
+    cplx32 *H = mode == 1 ? hist32(c, inst0) : nullptr;
+    if ((st = flux_spectra_t<cplx32>(c, d, (const cplx32 *)hi, phys, ts, coef, advance, c->tw32))) return st;
+    LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), hi, lo, H, rhs_out, phys, coef, mode,
+                                      d, c->stream));
   }
   return MHD_OK;
 }
@@ -445,8 +481,7 @@ mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *d
   if (!c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
   DeviceGuard g(c->device);
   const mhd::Dims d = one(c);
-  cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
-  if ((st = rhs_or_step(c, d, Si, nullptr, c->W2, c->phys + inst, nullptr, nullptr, 0))) return st;
+  if ((st = rhs_or_step(c, d, inst, c->W2, c->phys + inst, nullptr, nullptr, 0))) return st;
   // W2 holds the RHS spectra; inverse_zy reads its source before overwriting W2
   CK(mhd::launch_col_inverse(c->W2, c->W1, d.n, 7, d.nk * d.nx, c->tw, c->stream));
   CK(mhd::launch_col_inverse(c->W1, c->W2, d.n, 7 * d.n, d.nx, c->tw, c->stream));
@@ -467,7 +502,7 @@ mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
     if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
   DeviceGuard g(c->device);
   for (int s = 0; s < nsteps; ++s) {
-    mhd_status st = rhs_or_step(c, c->d, c->S, c->H, nullptr, c->phys, c->ts, c->coef, 1);
+    mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
     if (st) return st;
   }
   return MHD_OK;
@@ -529,7 +564,8 @@ mhd_status mhd_diagnostics(mhd_ctx *c, int32_t inst, mhd_diag *out) {
   if (!out) return fail(c, MHD_EINVAL, "null output");
   DeviceGuard g(c->device);
   const mhd::Dims d = one(c);
-  const cplx64 *Si = c->S + (size_t)inst * 7 * d.spec;
+  const cplx64 *Si = nullptr;
+  if ((st = state_fp64(c, inst, &Si))) return st;
   if ((st = inverse_zy(c, Si))) return st;
   CK(mhd::launch_diag_x(c->W2, c->phys + inst, c->part, d, c->tw, c->stream));
   CK(mhd::launch_diag_finish(c->part, mhd::diag_x_blocks(d.n), Si, c->phys + inst, c->ts + inst, c->diag_out, d,
@@ -571,8 +607,17 @@ mhd_status mhd_checkpoint(mhd_ctx *c, int32_t inst, double *buf, int32_t on_devi
   DeviceGuard g(c->device);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  CK(cudaMemcpyAsync(buf, c->S + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
-  CK(cudaMemcpyAsync(buf + 2 * sp, c->H + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
+  if (c->precision == MHD_FP64) {
+    CK(cudaMemcpyAsync(buf, state64(c, inst), sp * sizeof(cplx64), k, c->stream));
+    CK(cudaMemcpyAsync(buf + 2 * sp, c->H + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(buf, state_hi(c, inst), sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(buf + sp, state_lo(c, inst), sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(buf + 2 * sp, hist32(c, inst), sp * sizeof(cplx32), k, c->stream));
+    // the FP32 history fills half of its slot; the rest is written as zeros
+    if (on_device) CK(cudaMemsetAsync(buf + 3 * sp, 0, sp * sizeof(cplx32), c->stream));
+    else memset(buf + 3 * sp, 0, sp * sizeof(cplx32));
+  }
   static_assert(sizeof(mhd::TimeState) <= 8 * sizeof(double), "time state fits the tail");
   CK(cudaMemcpyAsync(buf + 4 * sp, c->ts + inst, sizeof(mhd::TimeState), k, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -586,8 +631,14 @@ mhd_status mhd_restore(mhd_ctx *c, int32_t inst, const double *buf, int32_t on_d
   DeviceGuard g(c->device);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(c->S + (size_t)inst * sp, buf, sp * sizeof(cplx64), k, c->stream));
-  CK(cudaMemcpyAsync(c->H + (size_t)inst * sp, buf + 2 * sp, sp * sizeof(cplx64), k, c->stream));
+  if (c->precision == MHD_FP64) {
+    CK(cudaMemcpyAsync(state64(c, inst), buf, sp * sizeof(cplx64), k, c->stream));
+    CK(cudaMemcpyAsync(c->H + (size_t)inst * sp, buf + 2 * sp, sp * sizeof(cplx64), k, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(state_hi(c, inst), buf, sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(state_lo(c, inst), buf + sp, sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(hist32(c, inst), buf + 2 * sp, sp * sizeof(cplx32), k, c->stream));
+  }
   CK(cudaMemcpyAsync(c->ts + inst, buf + 4 * sp, sizeof(mhd::TimeState), k, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->is_set[inst] = 1;

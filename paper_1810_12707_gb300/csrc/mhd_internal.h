@@ -44,8 +44,8 @@ struct TimeState {
 // y^{n+1} = y^n + dt (a1 f^n + a0 f^{n-1}); skip != 0 leaves the instance unchanged.
 struct StepCoef {
   double dt, a1, a0;
+  float fdt, fa1, fa0;  // the same, rounded once, for the mixed-precision update
   int32_t skip;
-  int32_t pad;
 };
 
 // Per-instance physical parameters in device memory.
@@ -130,6 +130,17 @@ cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cpl
 cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
                             const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
                             cudaStream_t s);
+
+// Mixed precision keeps the state as double-float pairs: S_hi and S_lo ([inst][7][spec] FP32
+// complex each, hi + lo carrying a 48-bit significand) and the history in FP32.  The update
+// y <- y + dt (a1 f + a0 h) adds the FP32 increment to (hi, lo) with an error-free two-sum.
+// mode 0 writes the RHS (FP64) to `rhs_out`; mode 1 updates hi, lo and hist.
+cudaError_t launch_assemble_df(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, cplx64 *rhs_out,
+                               const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
+                               cudaStream_t s);
+// FP64 spectra <-> (hi, lo) pairs of `count` complex values.
+cudaError_t launch_split_state(const cplx64 *in, cplx32 *hi, cplx32 *lo, size_t count, cudaStream_t s);
+cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out, size_t count, cudaStream_t s);
 
 // Final reduction of the diagnostic partials of one instance plus the spectral terms; writes
 // 24 doubles to `out` (see mhd_api.cu for the order).

@@ -118,17 +118,18 @@ def test_batched_instances_match_separate_oracles(lib, oracle_mod):
         assert abs(lib.mhd_diagnostics(ctx, i)["t"] - o.diagnostics()["t"]) <= 1e-12
 
 
-def test_checkpoint_restore_is_bitwise(lib):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_restore_is_bitwise(lib, precision):
     ic = inputs.orszag_tang(32, seed=5)
-    a = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)])
+    a = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], precision=precision)
     lib.mhd_set_state(a, 0, ic.rho, ic.u, ic.b)
     lib.mhd_step(a, 20)
     ref = lib.mhd_get_state(a, 0)
-    b = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)])
+    b = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], precision=precision)
     lib.mhd_set_state(b, 0, ic.rho, ic.u, ic.b)
     lib.mhd_step(b, 10)
     ck = lib.mhd_checkpoint(b, 0)
-    c = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)])
+    c = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], precision=precision)
     lib.mhd_restore(c, 0, ck)
     lib.mhd_step(c, 10)
     for g, e in zip(lib.mhd_get_state(c, 0), ref):
@@ -136,11 +137,12 @@ def test_checkpoint_restore_is_bitwise(lib):
     assert lib.mhd_diagnostics(c, 0)["step"] == 20
 
 
-def test_runs_are_deterministic(lib):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_runs_are_deterministic(lib, precision):
     ic = random_state(32, 3)
     out = []
     for _ in range(2):
-        ctx = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)])
+        ctx = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], precision=precision)
         lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
         lib.mhd_step(ctx, 10)
         out.append(lib.mhd_get_state(ctx, 0))
@@ -148,12 +150,13 @@ def test_runs_are_deterministic(lib):
         assert np.array_equal(g, e)
 
 
-def test_nonfinite_instance_stops_and_reports(lib):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_instance_stops_and_reports(lib, precision):
     n = 16
     ic = random_state(n, 4)
     rho = ic.rho.copy()
     rho[3, 4, 5] = np.nan  # spreads to every mode of the projected state
-    ctx = lib.mhd_init(n, [(ic.nu, ic.eta, ic.cs), (ic.nu, ic.eta, ic.cs)])
+    ctx = lib.mhd_init(n, [(ic.nu, ic.eta, ic.cs), (ic.nu, ic.eta, ic.cs)], precision=precision)
     lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
     lib.mhd_set_state(ctx, 1, rho, ic.u, ic.b)
     before = lib.mhd_checkpoint(ctx, 1)
