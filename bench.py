@@ -1,13 +1,19 @@
 #!/usr/bin/env python
 """Throughput benchmark of the MHD time step on GB300.
 
-Workload (default): N = 256^3 FP64 dynamo run -- ABC flow (A = B = C = 1, k_f = 1), Mach 0.1
-(Cs = 10), seed magnetic field of random |k| <= 4 modes at energy <|B|^2>/2 = 1e-5 from seed 1,
-nu = eta = 2e-3, rho0 = 1, CFL-limited dt.  One bench step is one Adams-Bashforth step of the whole
-hot path (inverse transforms, fluxes, forward transforms, spectral assembly, CFL dt, update).
-The per-step working set (about 2.4 GB) is far larger than the 129 MB L2, so no flush is needed.
+Default workload (`--config abc256`): N = 256^3 FP64 dynamo run -- ABC flow (A = B = C = 1,
+k_f = 1), Mach 0.1 (Cs = 10), seed magnetic field of random |k| <= 4 modes at energy
+<|B|^2>/2 = 1e-5 from seed 1, nu = eta = 2e-3, rho0 = 1, CFL-limited dt.  Other configurations:
+`ot32` (Orszag-Tang type, 32^3 FP64, fixed dt 1e-3), `tg512` (Taylor-Green, 512^3, mixed
+precision), `ens64` (64 independent 64^3 Orszag-Tang instances with their own seeds, nu, eta and
+Mach, mixed precision, one batched launch per kernel, CUDA-graph replay).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl ours|reference]
+One bench step is one Adams-Bashforth step of every instance through the whole hot path (inverse
+transforms, fluxes, forward transforms, spectral assembly, CFL dt, update).  The per-step
+working set of the default configuration (2.4 GB) is far larger than the 129 MB L2, so no flush
+is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs an independent replica (the
 instances share nothing), the timed region is bracketed by barriers and the slowest rank's time
@@ -29,8 +35,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-import numpy as np  # noqa: E402
-
 METRIC = "MHD grid-point-steps/s & HBM GB/s vs peak; served p50/p99 at rel err ≤1e-5"
 UNIT = "grid-point-steps/s"
 # Paper, Table III: 256^3 on a Tesla V100 at 0.22 s per step (FP64, OpenACC + cuFFT, unified
@@ -38,6 +42,19 @@ UNIT = "grid-point-steps/s"
 PAPER_256_V100 = 256 ** 3 / 0.22
 FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+
+CONFIGS = {
+    "abc256": dict(n=256, batch=1, precision="fp64", ic="abc", dt=0.0),
+    "ot32": dict(n=32, batch=1, precision="fp64", ic="ot", dt=1e-3),
+    "tg512": dict(n=512, batch=1, precision="fp32", ic="tg", dt=0.0),
+    "ens64": dict(n=64, batch=64, precision="fp32", ic="ens", dt=0.0),
+}
+IC_DESC = {
+    "abc": ("abc_dynamo", "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5), Mach 0.1, nu=eta=2e-3"),
+    "tg": ("taylor_green", "Taylor-Green + seed-2 random B (|k|<=4, E_B=1e-3), Mach 0.3, nu=eta=1e-3"),
+    "ot": ("orszag_tang", "Orszag-Tang type + seed-0 1e-3 perturbation, Mach 0.1, nu=eta=1e-2"),
+    "ens": ("ensemble_orszag_tang", "Orszag-Tang type, seeds 1000.., nu,eta log-U[1e-3,1e-2], Mach U[0.05,0.5] (rng 4)"),
+}
 
 
 def peaks():
@@ -50,25 +67,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(n: int, ic: str = "abc"):
+def workload(n: int, ic: str, batch: int = 1):
+    """List of `batch` initial conditions."""
     from paper_1810_12707_gb300 import inputs
     if ic == "tg":
-        # Taylor-Green, Mach 0.3, seeded random B at energy 1e-3, nu = eta = 1e-3
-        return inputs.taylor_green(n, seed=2, b_energy=1e-3, mach=0.3, nu=1e-3, eta=1e-3)
+        return [inputs.taylor_green(n, seed=2, b_energy=1e-3, mach=0.3, nu=1e-3, eta=1e-3)] * batch
     if ic == "ot":
-        return inputs.orszag_tang(n, seed=0, mach=0.1, nu=1e-2, eta=1e-2)
-    return inputs.abc_dynamo(n, seed=1, b_energy=1e-5, mach=0.1, nu=2e-3, eta=2e-3)
-
-
-IC_NAMES = {"abc": ("abc_dynamo", "ABC A=B=C=1 + seed-1 random B (|k|<=4, E_B=1e-5)", 0.1, 2e-3),
-            "tg": ("taylor_green", "Taylor-Green + seed-2 random B (|k|<=4, E_B=1e-3)", 0.3, 1e-3),
-            "ot": ("orszag_tang", "Orszag-Tang type + seed-0 1e-3 perturbation", 0.1, 1e-2)}
+        return [inputs.orszag_tang(n, seed=0, mach=0.1, nu=1e-2, eta=1e-2)] * batch
+    if ic == "ens":
+        nu, eta, mach = inputs.ensemble_params(batch, seed=4)
+        return [inputs.orszag_tang(n, seed=1000 + i, mach=float(mach[i]), nu=float(nu[i]), eta=float(eta[i]))
+                for i in range(batch)]
+    return [inputs.abc_dynamo(n, seed=1, b_energy=1e-5, mach=0.1, nu=2e-3, eta=2e-3)] * batch
 
 
 # ---------------------------------------------------------------------------------------------
-# Algorithmic work per launch of each kernel (FP64: 16-byte complex).  Bytes are the compulsory
-# HBM reads + writes of the pass; flops count 5 N log2 N per complex FFT of length N plus the
-# pointwise arithmetic.
+# Algorithmic work per launch of each kernel.  Bytes are the compulsory HBM reads + writes of the
+# pass; flops count 5 N log2 N per complex FFT of length N plus the pointwise arithmetic.
 # ---------------------------------------------------------------------------------------------
 def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
     k = (n - 1) // 3
@@ -100,7 +115,8 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.proc = None
         self.dev = device_index
 
@@ -149,11 +165,13 @@ def dist_env():
     return world, rank, local
 
 
-def time_oracle(n: int, steps: int, budget_s: float = 30.0, ic_name: str = "abc"):
-    """Time the CPU oracle on the same workload: `steps` AB2 steps after one untimed set_state."""
+def time_oracle(cfg, steps: int, budget_s: float = 30.0):
+    """Time the CPU oracle on the same workload: `steps` AB2 steps of the first instance after one
+    untimed set_state.  Returns grid-point-steps/s."""
     from oracle import oracle
-    ic = workload(n, ic_name)
-    o = oracle.Oracle(n, ic.nu, ic.eta, ic.cs, dt=0.0)
+    ic = workload(cfg["n"], cfg["ic"], 1)[0]
+    n = cfg["n"]
+    o = oracle.Oracle(n, ic.nu, ic.eta, ic.cs, dt=cfg["dt"])
     o.set_state(ic.rho, ic.u, ic.b)
     done, t0 = 0, time.perf_counter()
     while done < steps:
@@ -165,34 +183,41 @@ def time_oracle(n: int, steps: int, budget_s: float = 30.0, ic_name: str = "abc"
     return n ** 3 * done / el, done, el, oracle.num_threads()
 
 
-def run_reference(args):
+def config_block(name, cfg, world):
+    ic_name, desc = IC_DESC[cfg["ic"]]
+    n, b = cfg["n"], cfg["batch"]
+    return {"workload": f"{name}: {b} x {ic_name} {n}^3 {cfg['precision']}", "n": n, "batch": b,
+            "precision": cfg["precision"], "ic": desc, "dt": cfg["dt"] if cfg["dt"] > 0 else "cfl",
+            "l2": "per-step working set > L2 (no flush)" if b * n ** 3 >= 128 ** 3 * 8 else "working set may fit L2",
+            "parallelism": f"replicas x{world}",
+            "baseline": "paper Table III 256^3 V100 0.22 s/step (other hardware, context)"}
+
+
+def run_reference(args, name, cfg):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n = args.n
-    # each bench step is one oracle step of the same workload; the run is capped at about three
-    # minutes of CPU work in total
-    _, _, t_one, _ = time_oracle(n, 1, ic_name=args.ic)
+    n = cfg["n"]
+    # each bench step is one oracle step of (the first instance of) the same workload; the run is
+    # capped at about three minutes of CPU work in total
+    _, _, t_one, _ = time_oracle(cfg, 1)
     budget = 180.0
     k = max(1, min(args.steps, int(budget / max(t_one, 1e-9))))
-    value, done, el, cores = time_oracle(n, k, budget_s=budget, ic_name=args.ic)
-    name, desc, mach, visc = IC_NAMES[args.ic]
+    value, done, el, cores = time_oracle(cfg, k, budget_s=budget)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": done, "warmup": 1, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": value / PAPER_256_V100 if n == 256 else None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"{name}_{n}^3_{args.precision}", "n": n, "batch": 1, "precision": args.precision,
-                   "ic": desc, "mach": mach, "nu": visc, "eta": visc, "dt": "cfl"},
+        "data": "synthetic", "config": config_block(name, cfg, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{done} AB2 steps of the {n}^3 workload after set_state (one untimed warm-up step)"},
+                         "sample": f"{done} AB2 steps of one {n}^3 instance after set_state (one untimed warm-up step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
+def run_ours(args, name, cfg):
     import torch
 
     world, rank, local = dist_env()
@@ -209,17 +234,27 @@ def run_ours(args):
         dist.barrier()
     from paper_1810_12707_gb300 import mhd
 
-    n, K, W = args.n, args.steps, args.warmup
-    prec = mhd.MHD_FP64 if args.precision == "fp64" else mhd.MHD_FP32_MIXED
-    ic = workload(n, args.ic)
-    ctx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0, precision=prec)
-    mhd.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+    n, batch, K, W = cfg["n"], cfg["batch"], args.steps, args.warmup
+    prec = mhd.MHD_FP64 if cfg["precision"] == "fp64" else mhd.MHD_FP32_MIXED
+    ics = workload(n, cfg["ic"], batch)
+    phys = [(ic.nu, ic.eta, ic.cs) for ic in ics]
+    ctx = mhd.mhd_init(n, phys, dt=cfg["dt"], precision=prec)
+    for i, ic in enumerate(ics):
+        mhd.mhd_set_state(ctx, i, ic.rho, ic.u, ic.b)
     stream = torch.cuda.current_stream()
 
+    # per-kernel device times from a profiled run (direct launches, events on the library's
+    # stream) of K steps, after the warm-up
     mhd.mhd_step(ctx, W)
     if mhd.mhd_synchronize(ctx) != mhd.MHD_OK:
         raise RuntimeError("non-finite state during warm-up")
+    mhd.mhd_profile(ctx, True)
+    mhd.mhd_step(ctx, K)
+    prof = mhd.mhd_profile_read(ctx)
+    mhd.mhd_profile(ctx, False)
 
+    # the timed region: K steps as the library runs them (CUDA-graph replay)
+    mhd.mhd_step(ctx, 2)
     sampler = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -227,7 +262,6 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    mhd.mhd_profile(ctx, True)
     e0.record(stream)
     for _ in range(K):
         mhd.mhd_step(ctx, 1)
@@ -237,58 +271,67 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    prof = mhd.mhd_profile_read(ctx)
-    mhd.mhd_profile(ctx, False)
     st = mhd.mhd_synchronize(ctx)
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * n ** 3 * K / (ms / 1e3)
+    pts = batch * n ** 3
+    value = world * pts * K / (ms / 1e3)
     diag = mhd.mhd_diagnostics(ctx, 0)
 
-    # end to end through the C ABI with pinned host buffers: per step, H2D of the state
-    # (rho, u, B), one step, D2H of the state (rho, m, B)
+    # end to end through the C ABI with pinned host buffers: per step, H2D of every instance's
+    # state (rho, u, B), one step, D2H of every instance's state (rho, m, B)
     E = max(1, min(K, args.e2e_steps))
     pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-    h_rho, h_u, h_b = pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))
-    h_rho[...] = ic.rho
-    h_u[...] = ic.u
-    h_b[...] = ic.b
     lib = mhd.load_library()
-    o_rho, o_m, o_b = pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))
-    ectx = mhd.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], dt=0.0, precision=prec)
-    mhd.mhd_set_state(ectx, 0, h_rho, h_u, h_b)
-    mhd.mhd_step(ectx, 2)
-    lib.mhd_get_state(ectx.handle, 0, o_rho.ctypes.data, o_m.ctypes.data, o_b.ctypes.data, 0)
+    hs = []
+    for ic in ics[: min(batch, 64)]:
+        h = (pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n)))
+        h[0][...] = ic.rho
+        h[1][...] = ic.u
+        h[2][...] = ic.b
+        hs.append(h)
+    outs = [(pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))) for _ in range(len(hs))]
+    ectx = mhd.mhd_init(n, phys, dt=cfg["dt"], precision=prec)
+
+    def e2e_step():
+        for i in range(batch):
+            h = hs[i % len(hs)]
+            assert lib.mhd_set_state(ectx.handle, i, h[0].ctypes.data, h[1].ctypes.data, h[2].ctypes.data, 0) == 0
+        assert lib.mhd_step(ectx.handle, 1) == 0
+        for i in range(batch):
+            o = outs[i % len(outs)]
+            assert lib.mhd_get_state(ectx.handle, i, o[0].ctypes.data, o[1].ctypes.data, o[2].ctypes.data, 0) == 0
+
+    e2e_step()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(E):
-        assert lib.mhd_set_state(ectx.handle, 0, h_rho.ctypes.data, h_u.ctypes.data, h_b.ctypes.data, 0) == 0
-        assert lib.mhd_step(ectx.handle, 1) == 0
-        assert lib.mhd_get_state(ectx.handle, 0, o_rho.ctypes.data, o_m.ctypes.data, o_b.ctypes.data, 0) == 0
+        e2e_step()
     te = time.perf_counter() - t0
     if dist:
         t = torch.tensor([te], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         te = float(t.item())
-    e2e = {"value": world * n ** 3 * E / te, "unit": UNIT, "h2d_bytes_per_step": 7 * n ** 3 * 8,
-           "d2h_bytes_per_step": 7 * n ** 3 * 8, "steps": E}
+    e2e = {"value": world * pts * E / te, "unit": UNIT, "h2d_bytes_per_step": 7 * pts * 8,
+           "d2h_bytes_per_step": 7 * pts * 8, "steps": E}
     mhd.mhd_destroy(ectx)
 
     # roofline of the dominant kernel (largest share of device time)
     hbm, hbm_src = peaks()
-    model = kernel_model(n, 1, args.precision)
-    alu_peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
+    model = kernel_model(n, batch, cfg["precision"])
+    alu_peak = FP64_PEAK_TFLOPS if cfg["precision"] == "fp64" else FP32_PEAK_TFLOPS
+    total_ms = sum(v[0] for v in prof.values())
     per = {}
-    for name, (tot, cnt) in prof.items():
+    for kname, (tot, cnt) in prof.items():
         if cnt:
-            b, f = model[name]
+            b, f = model[kname]
             avg = tot / cnt
-            per[name] = {"avg_ms": avg, "share": tot / max(sum(v[0] for v in prof.values()), 1e-30),
-                         "gbs": b / (avg * 1e-3) / 1e9, "tflops": f / (avg * 1e-3) / 1e12}
+            per[kname] = {"avg_ms": avg, "share": tot / max(total_ms, 1e-30),
+                          "gbs": b / (avg * 1e-3) / 1e9, "tflops": f / (avg * 1e-3) / 1e12}
     top = max(per, key=lambda k: per[k]["share"])
     tb, tf = model[top]
     t_mem = tb / (hbm * 1e9)
@@ -296,32 +339,29 @@ def run_ours(args):
     if t_alu >= t_mem:
         roof = {"bound": "alu", "achieved": per[top]["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": per[top]["tflops"] / alu_peak, "traffic": None,
-                "peak_source": ("FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)" if args.precision == "fp64"
+                "peak_source": ("FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)" if prec == mhd.MHD_FP64
                                 else "FP32 FMA units x clock (probe 74.4 TFLOP/s)")}
     else:
         roof = {"bound": "hbm", "achieved": per[top]["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": per[top]["gbs"] / hbm, "traffic": None, "peak_source": f"{hbm_src} copy"}
     roof.update({"kernel": top, "algorithmic_bytes": tb, "algorithmic_flops": tf,
-                 "achieved_gbs": per[top]["gbs"], "frac_hbm_of_measured": per[top]["gbs"] / hbm})
+                 "achieved_gbs": per[top]["gbs"], "frac_hbm_of_measured": per[top]["gbs"] / hbm,
+                 "step_model_bytes": sum(v[0] for v in model.values()),
+                 "step_frac_hbm": sum(v[0] for v in model.values()) / (ms / K * 1e-3) / 1e9 / hbm})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, done, el, cores = time_oracle(n, 2, budget_s=30.0, ic_name=args.ic)
+        v, done, el, cores = time_oracle(cfg, 2, budget_s=30.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{done} AB2 steps of the {n}^3 workload after an untimed set_state ({el:.1f} s)"}
+               "sample": f"{done} AB2 steps of one {n}^3 instance after an untimed set_state ({el:.1f} s)"}
 
-    name, desc, mach, visc = IC_NAMES[args.ic]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / (world * PAPER_256_V100) if n == 256 else None,
-            "dtype": "f64" if args.precision == "fp64" else "f32 (fp64 state/update)", "data": "synthetic",
-            "config": {"workload": f"{name}_{n}^3_{args.precision}", "n": n, "batch": 1, "precision": args.precision,
-                       "ic": desc, "mach": mach, "nu": visc, "eta": visc, "dt": "cfl",
-                       "l2": "per-step working set > L2 (no flush)",
-                       "parallelism": f"replicas x{world}",
-                       "baseline": "paper Table III 256^3 V100 0.22 s/step (other hardware, context)"},
+            "vs_baseline": value / (world * PAPER_256_V100) if (n == 256 and batch == 1) else None,
+            "dtype": "f64" if prec == mhd.MHD_FP64 else "f32 (double-float state)", "data": "synthetic",
+            "config": config_block(name, cfg, world),
             "roofline": roof,
             "kernels": per,
             "cpu_baseline": cpu,
@@ -343,18 +383,25 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="abc256")
+    ap.add_argument("--n", type=int)
+    ap.add_argument("--batch", type=int)
+    ap.add_argument("--precision", choices=("fp64", "fp32"))
+    ap.add_argument("--ic", choices=("abc", "tg", "ot", "ens"))
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
-    ap.add_argument("--ic", choices=("abc", "tg", "ot"), default="abc")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config])
+    for key in ("n", "batch", "precision", "ic"):
+        if getattr(args, key) is not None:
+            cfg[key] = getattr(args, key)
+    name = args.config
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
-        return run_reference(args)
-    return run_ours(args)
+        return run_reference(args, name, cfg)
+    return run_ours(args, name, cfg)
 
 
 if __name__ == "__main__":

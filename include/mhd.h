@@ -168,6 +168,22 @@ MHD_API size_t mhd_checkpoint_doubles(const mhd_ctx *ctx);
 MHD_API mhd_status mhd_checkpoint(mhd_ctx *ctx, int32_t inst, double *buf, int32_t on_device);
 MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, int32_t on_device);
 
+/* Execution options of a context (mhd_set_option).  Changing one discards the captured step.
+ *   MHD_OPT_CUDA_GRAPH     1 (default): mhd_step captures one step as a CUDA graph on its first
+ *                          call (after one direct step) and replays it; 0: direct launches.
+ *                          Profiling (mhd_profile) always uses direct launches.
+ *   MHD_OPT_TILE_INV_Z ... MHD_OPT_TILE_FWD_Z: columns per block of the four column FFT passes
+ *                          (inverse z, inverse y, forward y, forward z); 0 (default) = chosen by
+ *                          the library; otherwise 1..64 (an autotuner sets these). */
+enum {
+  MHD_OPT_CUDA_GRAPH = 0,
+  MHD_OPT_TILE_INV_Z = 1,
+  MHD_OPT_TILE_INV_Y = 2,
+  MHD_OPT_TILE_FWD_Y = 3,
+  MHD_OPT_TILE_FWD_Z = 4
+};
+MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
+
 /* Per-kernel device time of mhd_step, for measurement.  While profiling is on, every kernel that
  * mhd_step launches is bracketed by CUDA events on the context's stream.  mhd_profile(ctx, 1)
  * clears the totals and starts recording, mhd_profile(ctx, 0) stops.  mhd_profile_read

@@ -82,9 +82,12 @@ int pick_tc(int n, int cols) {
 
 template <int N, int DIR, typename CI, typename CO>
 cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
-                         cudaStream_t s) {
+                         cudaStream_t s, int tile) {
   const int K = (N - 1) / 3;
-  const int tc = pick_tc(N, cols);
+  int tc = tile > 0 ? tile : pick_tc(N, cols);
+  while (tc * (N / 8) > 1024) tc /= 2;
+  if (tc > cols) tc = cols;
+  if (tc < 1) tc = 1;
   const int ntiles = (cols + tc - 1) / tc;
   const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
   if (smem > 48 * 1024) {
@@ -101,15 +104,15 @@ cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scal
 
 template <int DIR, typename CI, typename CO>
 cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale, const CO *tw,
-                       cudaStream_t s) {
+                       cudaStream_t s, int tile) {
   switch (n) {
-    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s);
-    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s);
+    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s, tile);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -117,24 +120,24 @@ cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double
 }  // namespace
 
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
+                               const cplx64 *tw, cudaStream_t s, int tile) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
 }
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
+                               const cplx32 *tw, cudaStream_t s, int tile) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
 }
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s);
+                               const cplx32 *tw, cudaStream_t s, int tile) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
 }
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile);
 }
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile);
 }
 
 }  // namespace mhd

@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
       const R rho = v[h][0];
       const R mx = v[h][1], my = v[h][2], mz = v[h][3];
       const R bx = v[h][4], by = v[h][5], bz = v[h][6];
-      const R ux = mx / rho, uy = my / rho, uz = mz / rho;
+      const R ir = (R)1 / rho;
+      const R ux = mx * ir, uy = my * ir, uz = mz * ir;
       const R b2 = bx * bx + by * by + bz * bz;
       const R hb = (R)0.5 * b2;
       // component h of pencil f at this point is bd[2 * f * P + h]
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
       bd[2 * 9 * P + h] = ux;
       bd[2 * 10 * P + h] = uy;
       bd[2 * 11 * P + h] = uz;
-      const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 / rho);
+      const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 * ir);
       smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
     }
   }

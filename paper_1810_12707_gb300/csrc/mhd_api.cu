@@ -48,6 +48,12 @@ struct mhd_ctx {
   int32_t *flag = nullptr;
   std::vector<void *> allocs;
   std::string err;
+  // options and the captured step
+  bool use_graph = true;
+  int tile[4] = {0, 0, 0, 0};
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool stepped_direct = false;
   // profiling: events bracketing each launch of mhd_step, resolved at read time
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -261,6 +267,8 @@ void mhd_destroy(mhd_ctx *ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     free_all(ctx);
   }
   delete ctx;
@@ -438,15 +446,15 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, co
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
   CF *w2 = reinterpret_cast<CF *>(c->W2);
-  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream));
-  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream));
+  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0]));
+  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1]));
   LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, c->part, d, tw, c->stream));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(c->part, mhd::flux_x_blocks_per_instance(d.n), phys, ts, coef, d, c->dt_fixed,
                                   c->cfl_adv, c->cfl_visc, c->stream));
   }
-  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream));
-  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream));
+  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2]));
+  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3]));
   return MHD_OK;
 }
 
@@ -501,7 +509,38 @@ mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
   for (int i = 0; i < c->d.batch; ++i)
     if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
   DeviceGuard g(c->device);
-  for (int s = 0; s < nsteps; ++s) {
+  int s = 0;
+  if (c->use_graph && !c->profiling && nsteps > 0) {
+    if (!c->graph_exec) {
+      // one direct step first (it also raises the kernels' shared-memory limits, which is not a
+      // stream operation), then capture one step on a private stream and instantiate it
+      if (!c->stepped_direct) {
+        mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+        if (st) return st;
+        c->stepped_direct = true;
+        ++s;
+      }
+      if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = c->stream;
+      c->stream = c->cap_stream;
+      CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      c->stream = user;
+      if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      CK(e);
+      e = cudaGraphInstantiateWithFlags(&c->graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(e);
+    }
+    for (; s < nsteps; ++s) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    return MHD_OK;
+  }
+  for (; s < nsteps; ++s) {
     mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
     if (st) return st;
   }
@@ -545,6 +584,26 @@ mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32
   int k = 0;
   for (int i = 0; i < 7 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
   *count = k;
+  return MHD_OK;
+}
+
+mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
+  if (!c) return MHD_EINVAL;
+  DeviceGuard g(c->device);
+  if (option == MHD_OPT_CUDA_GRAPH) {
+    if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "graph option must be 0 or 1");
+    c->use_graph = value != 0;
+  } else if (option >= MHD_OPT_TILE_INV_Z && option <= MHD_OPT_TILE_FWD_Z) {
+    if (value < 0 || value > 64) return fail(c, MHD_EINVAL, "tile must be 0..64");
+    c->tile[option - MHD_OPT_TILE_INV_Z] = (int)value;
+  } else {
+    return fail(c, MHD_EINVAL, "unknown option %d", option);
+  }
+  if (c->graph_exec) {
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGraphExecDestroy(c->graph_exec));
+    c->graph_exec = nullptr;
+  }
   return MHD_OK;
 }
 

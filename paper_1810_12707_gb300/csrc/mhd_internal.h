@@ -82,16 +82,17 @@ inline Dims make_dims(int n, int batch) {
 // Column FFTs along the middle axis of [nslab][L][C]: inverse (sign +1) expands L from the
 // NK kept indices to N; forward (sign -1) keeps only the NK kept outputs and multiplies by
 // `scale`.
+// `tile` > 0 forces the number of columns per block (else the library's choice).
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s);
+                               const cplx64 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s);
+                               const cplx32 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s);
+                               const cplx32 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile = 0);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and per-block maxima of

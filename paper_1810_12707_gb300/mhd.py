@@ -23,13 +23,14 @@ LIBRARY = os.path.join(_PKG, "libmhd_gb300.so")
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ESTATE, MHD_ENONFINITE, MHD_ETIMEOUT, MHD_EBUSY = range(8)
 MHD_FP64 = 0
 MHD_FP32_MIXED = 1
+MHD_OPT_CUDA_GRAPH, MHD_OPT_TILE_INV_Z, MHD_OPT_TILE_INV_Y, MHD_OPT_TILE_FWD_Y, MHD_OPT_TILE_FWD_Z = range(5)
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_ESTATE",
                 5: "MHD_ENONFINITE", 6: "MHD_ETIMEOUT", 7: "MHD_EBUSY"}
 
 EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "mhd_set_state",
            "mhd_get_state", "mhd_rhs", "mhd_get_spectrum", "mhd_step", "mhd_synchronize",
            "mhd_diagnostics", "mhd_checkpoint_doubles", "mhd_checkpoint", "mhd_restore", "mhd_profile",
-           "mhd_profile_read", "mhd_rhs_noalloc")
+           "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option")
 
 
 class MhdError(RuntimeError):
@@ -110,6 +111,8 @@ def load_library(path: str = LIBRARY):
     lib.mhd_profile.argtypes = [P, I32]
     lib.mhd_profile_read.restype = I32
     lib.mhd_profile_read.argtypes = [P, ctypes.POINTER(MhdKernelTime), I32, ctypes.POINTER(I32)]
+    lib.mhd_set_option.restype = I32
+    lib.mhd_set_option.argtypes = [P, I32, ctypes.c_int64]
     lib.mhd_rhs_noalloc.restype = I32
     lib.mhd_rhs_noalloc.argtypes = [I32, ctypes.POINTER(MhdPhys), P, P, P, P, P, P, P]
     _lib = lib
@@ -267,6 +270,10 @@ def mhd_get_spectrum(ctx: Context, inst: int, field: int, device: bool = False):
 
 def mhd_step(ctx: Context, nsteps: int = 1) -> None:
     _check(ctx, load_library().mhd_step(ctx.handle, int(nsteps)))
+
+
+def mhd_set_option(ctx: Context, option: int, value: int) -> None:
+    _check(ctx, load_library().mhd_set_option(ctx.handle, int(option), int(value)))
 
 
 def mhd_synchronize(ctx: Context) -> int:

@@ -179,3 +179,56 @@ def test_invalid_arguments_are_rejected(lib):
         lib.mhd_step(ctx, 1)  # no state yet
     with pytest.raises(lib.MhdError):
         lib.mhd_get_state(ctx, 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_direct_launches(lib, precision):
+    ic = random_state(32, 21)
+    out = []
+    for graph in (0, 1):
+        ctx = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], precision=precision)
+        lib.mhd_set_option(ctx, lib.MHD_OPT_CUDA_GRAPH, graph)
+        lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+        lib.mhd_step(ctx, 3)
+        lib.mhd_step(ctx, 9)
+        out.append(lib.mhd_get_state(ctx, 0))
+        assert lib.mhd_diagnostics(ctx, 0)["step"] == 12
+    for g, e in zip(*out):
+        assert np.array_equal(g, e)
+
+
+def test_tile_options_leave_results_bitwise_unchanged(lib):
+    ic = random_state(64, 22)
+    out = []
+    for tiles in ((0, 0, 0, 0), (3, 5, 7, 64), (1, 1, 1, 1)):
+        ctx = lib.mhd_init(64, [(ic.nu, ic.eta, ic.cs)], precision=1)
+        for opt, v in zip((lib.MHD_OPT_TILE_INV_Z, lib.MHD_OPT_TILE_INV_Y, lib.MHD_OPT_TILE_FWD_Y,
+                           lib.MHD_OPT_TILE_FWD_Z), tiles):
+            lib.mhd_set_option(ctx, opt, v)
+        lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+        lib.mhd_step(ctx, 5)
+        out.append(lib.mhd_get_state(ctx, 0))
+    for other in out[1:]:
+        for g, e in zip(other, out[0]):
+            assert np.array_equal(g, e)
+    with pytest.raises(lib.MhdError):
+        lib.mhd_set_option(ctx, lib.MHD_OPT_TILE_INV_Z, 65)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_instance_result_is_the_same_alone_and_in_a_batch(lib, precision):
+    """Every kernel treats instances independently, so a run in a batch of different instances is
+    bitwise the run alone."""
+    n = 32
+    ics = [inputs.orszag_tang(n, seed=s, mach=m, nu=nu, eta=eta)
+           for s, m, nu, eta in ((7, 0.1, 1e-2, 2e-3), (8, 0.4, 3e-3, 8e-3), (9, 0.05, 5e-3, 1e-3), (10, 0.2, 1e-3, 1e-3))]
+    mix = lib.mhd_init(n, [(ic.nu, ic.eta, ic.cs) for ic in ics], precision=precision)
+    for i, ic in enumerate(ics):
+        lib.mhd_set_state(mix, i, ic.rho, ic.u, ic.b)
+    lib.mhd_step(mix, 15)
+    for i, ic in enumerate(ics):
+        alone = lib.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], precision=precision)
+        lib.mhd_set_state(alone, 0, ic.rho, ic.u, ic.b)
+        lib.mhd_step(alone, 15)
+        for g, e in zip(lib.mhd_get_state(mix, i), lib.mhd_get_state(alone, 0)):
+            assert np.array_equal(g, e)
