@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -378,6 +380,59 @@ def run_ours(args, name, cfg):
     return 0
 
 
+def run_serve(args):
+    """Serving configuration: Poisson stream of run requests (N in {32,64,128,256} with weights
+    .4/.3/.2/.1, ABC or Orszag-Tang, nu, eta ~ U[1e-3,1e-2], Mach ~ U[0.05,0.5], 100-1000 steps,
+    mixed precision) served with continuous batching at 0.8x and 1.2x the measured capacity."""
+    import torch
+
+    from paper_1810_12707_gb300 import build_lib
+    build_lib.build()
+    from paper_1810_12707_gb300 import mhd, serving
+
+    torch.cuda.set_device(0)
+    free, _ = torch.cuda.mem_get_info()
+    slots = serving.plan_slots(free, precision=mhd.MHD_FP32_MIXED)
+    cache = serving.ICCache()
+    probe = serving.make_requests(400, rate=1.0, seed=5)
+    for r in probe:  # every (N, kind, seed) initial state, generated before any timing
+        cache.get(r)
+    srv = serving.Server(slots, k=args.serve_k, cache=cache)
+    capacity = serving.measure_capacity(srv, probe, duration_s=args.capacity_s)
+    mean_work = float(np.mean([r.work for r in probe]))
+    cap_rate = capacity / mean_work
+    loads = {}
+    checked, equal = 0, 0
+    for frac, seed in ((0.8, 5), (1.2, 6)):
+        reqs = serving.make_requests(args.requests, rate=frac * cap_rate, seed=seed)
+        keep = []
+        if frac == 0.8:  # outputs of one request of each size for the alone-versus-mix check
+            for n in serving.SIZES:
+                rid = next((r.rid for r in reqs if r.n == n), None)
+                if rid is not None:
+                    keep.append(rid)
+        stats = srv.run(reqs, keep_outputs=keep)
+        loads[f"{frac}x"] = dict(stats.summary(), rate_req_s=frac * cap_rate)
+        for rid in keep:
+            alone = serving.run_alone(reqs[rid], cache=cache)
+            checked += 1
+            equal += all(np.array_equal(g, e) for g, e in zip(stats.outputs[rid], alone))
+    srv.close()
+    hi = loads["1.2x"]
+    line = {
+        "metric": METRIC, "value": hi["throughput"], "unit": UNIT, "n_gpus": 1, "steps": args.requests,
+        "warmup": 0, "ms_per_step": hi["step_latency_ms_p50"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (double-float state)", "data": "synthetic",
+        "config": {"workload": f"serve: {args.requests} Poisson requests per load, N in {list(serving.SIZES)}",
+                   "slots": slots, "k_steps_per_round": args.serve_k, "precision": "fp32",
+                   "admission": "slots sized from free HBM at start", "free_hbm_bytes": free},
+        "serving": {"capacity_pts_steps_s": capacity, "capacity_req_s": cap_rate, "mean_request_work": mean_work,
+                    "loads": loads, "alone_vs_mix": f"{equal}/{checked} bitwise equal"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +446,13 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving configuration instead")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--serve-k", type=int, default=10)
+    ap.add_argument("--capacity-s", type=float, default=10.0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     cfg = dict(CONFIGS[args.config])
     for key in ("n", "batch", "precision", "ic"):
         if getattr(args, key) is not None:

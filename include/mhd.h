@@ -197,6 +197,37 @@ typedef struct {
 MHD_API mhd_status mhd_profile(mhd_ctx *ctx, int32_t enable);
 MHD_API mhd_status mhd_profile_read(mhd_ctx *ctx, mhd_kernel_time *out, int32_t max, int32_t *count);
 
+/* ---- Serving pools ----
+ * A pool holds up to p->batch instances ("slots") of one grid size and precision, all resident in
+ * device memory, and steps the live ones together (continuous batching): runs are admitted while
+ * others are in flight and retired as they finish, and every run's result is bitwise the result
+ * it would have alone (instances never interact).  Internally the live instances are kept
+ * contiguous: retiring one moves the last live instance into its place, so slot handles stay
+ * valid while positions change.  Each live count gets its own captured CUDA graph. */
+typedef struct mhd_pool mhd_pool;
+/* p->batch = number of slots; p->dt, cfl_*, stream, allocator as for mhd_init. */
+MHD_API mhd_status mhd_pool_create(const mhd_params *p, mhd_pool **out);
+MHD_API void mhd_pool_destroy(mhd_pool *pool);
+MHD_API const char *mhd_pool_last_error(const mhd_pool *pool);
+/* Admit a run: state from real-space rho, u, B (as mhd_set_state), parameters `phys`, and a budget
+ * of `nsteps` >= 1 steps after which it stops advancing.  *slot receives its handle.  MHD_EBUSY
+ * when every slot is in use.  Synchronises. */
+MHD_API mhd_status mhd_pool_admit(mhd_pool *pool, const mhd_phys *phys, const double *rho, const double *u,
+                                  const double *b, int32_t on_device, int64_t nsteps, int32_t *slot);
+/* Advance every live run by k steps (runs at their budget or stopped by a non-finite state do not
+ * change).  Asynchronous. */
+MHD_API mhd_status mhd_pool_step(mhd_pool *pool, int32_t k);
+/* Per slot handle (arrays of p->batch entries): steps taken (-1 for a free slot), status, and
+ * whether the run is finished (budget reached or stopped).  Synchronises. */
+MHD_API mhd_status mhd_pool_progress(mhd_pool *pool, int64_t *steps, int32_t *status, int32_t *finished);
+/* Diagnostics of the run in `slot`.  Synchronises. */
+MHD_API mhd_status mhd_pool_diagnostics(mhd_pool *pool, int32_t slot, mhd_diag *out);
+/* Copy out the run's real-space rho, m, B (skipped if any pointer is NULL) and free its slot.
+ * Synchronises. */
+MHD_API mhd_status mhd_pool_retire(mhd_pool *pool, int32_t slot, double *rho, double *m, double *b,
+                                   int32_t on_device);
+MHD_API mhd_status mhd_pool_info(const mhd_pool *pool, int32_t *live, int32_t *max_slots);
+
 /* Right-hand side of one state that allocates no memory.  For callers that must not call
  * cudaMalloc when they need it (a host framework that already owns the device memory pool, or a
  * latency-bound loop that cannot take the device synchronisation an allocation may bring).  The

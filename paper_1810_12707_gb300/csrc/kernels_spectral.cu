@@ -218,7 +218,7 @@ __global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
   if (threadIdx.x != 0) return;
   TimeState s = ts[inst];
   StepCoef c = {0.0, 0.0, 0.0, 0.f, 0.f, 0.f, 1};
-  if (s.status == 0) {
+  if (s.status == 0 && (s.step_limit == 0 || s.step < s.step_limit)) {
     double dt;
     if (dt_fixed > 0.0) {
       dt = dt_fixed;

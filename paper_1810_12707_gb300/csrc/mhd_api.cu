@@ -53,7 +53,9 @@ struct mhd_ctx {
   int tile[4] = {0, 0, 0, 0};
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
-  bool stepped_direct = false;
+  // serving pools: only the first `live` instances are stepped (-1: all), one graph per count
+  int live = -1;
+  std::vector<cudaGraphExec_t> pool_graphs;
   // profiling: events bracketing each launch of mhd_step, resolved at read time
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -212,6 +214,15 @@ cplx32 *state_lo(mhd_ctx *c, int inst) {
 }
 cplx32 *hist32(mhd_ctx *c, int inst) { return reinterpret_cast<cplx32 *>(c->H) + (size_t)inst * 7 * c->d.spec; }
 
+void drop_graphs(mhd_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  for (auto &g : c->pool_graphs) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
 // FP64 spectra of instance `inst` for the FP64 utility chains (the mixed state is combined first).
 mhd_status state_fp64(mhd_ctx *c, int inst, const cplx64 **out) {
   if (c->precision == MHD_FP64) {
@@ -267,7 +278,7 @@ void mhd_destroy(mhd_ctx *ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     free_all(ctx);
   }
@@ -503,48 +514,59 @@ mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *d
   return MHD_OK;
 }
 
-mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
-  if (!c) return MHD_EINVAL;
-  if (nsteps < 0) return fail(c, MHD_EINVAL, "negative step count");
-  for (int i = 0; i < c->d.batch; ++i)
-    if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
-  DeviceGuard g(c->device);
+}  // extern "C"
+
+// Advance the first `nb` instances `nsteps` steps, replaying the CUDA graph kept in *graph (captured
+// on first use after one direct step) unless graphs are off or profiling is on.
+static mhd_status step_prefix(mhd_ctx *c, int nb, int32_t nsteps, cudaGraphExec_t *graph) {
+  if (nb <= 0 || nsteps <= 0) return MHD_OK;
+  mhd::Dims d = c->d;
+  d.batch = nb;
   int s = 0;
-  if (c->use_graph && !c->profiling && nsteps > 0) {
-    if (!c->graph_exec) {
+  if (c->use_graph && !c->profiling) {
+    if (!*graph) {
       // one direct step first (it also raises the kernels' shared-memory limits, which is not a
       // stream operation), then capture one step on a private stream and instantiate it
-      if (!c->stepped_direct) {
-        mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
-        if (st) return st;
-        c->stepped_direct = true;
-        ++s;
-      }
+      mhd_status st = rhs_or_step(c, d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+      if (st) return st;
+      ++s;
       if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
       cudaStream_t user = c->stream;
       c->stream = c->cap_stream;
       CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-      mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
-      cudaGraph_t graph = nullptr;
-      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      st = rhs_or_step(c, d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
       c->stream = user;
       if (st) {
-        if (graph) cudaGraphDestroy(graph);
+        if (g) cudaGraphDestroy(g);
         return st;
       }
       CK(e);
-      e = cudaGraphInstantiateWithFlags(&c->graph_exec, graph, 0);
-      cudaGraphDestroy(graph);
+      e = cudaGraphInstantiateWithFlags(graph, g, 0);
+      cudaGraphDestroy(g);
       CK(e);
     }
-    for (; s < nsteps; ++s) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    for (; s < nsteps; ++s) CK(cudaGraphLaunch(*graph, c->stream));
     return MHD_OK;
   }
   for (; s < nsteps; ++s) {
-    mhd_status st = rhs_or_step(c, c->d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+    mhd_status st = rhs_or_step(c, d, 0, nullptr, c->phys, c->ts, c->coef, 1);
     if (st) return st;
   }
   return MHD_OK;
+}
+
+extern "C" {
+
+mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
+  if (!c) return MHD_EINVAL;
+  if (nsteps < 0) return fail(c, MHD_EINVAL, "negative step count");
+  if (c->live >= 0) return fail(c, MHD_ESTATE, "context belongs to a pool: use mhd_pool_step");
+  for (int i = 0; i < c->d.batch; ++i)
+    if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
+  DeviceGuard g(c->device);
+  return step_prefix(c, c->d.batch, nsteps, &c->graph_exec);
 }
 
 static mhd_status prof_resolve(mhd_ctx *c) {
@@ -599,11 +621,8 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   } else {
     return fail(c, MHD_EINVAL, "unknown option %d", option);
   }
-  if (c->graph_exec) {
-    CK(cudaStreamSynchronize(c->stream));
-    CK(cudaGraphExecDestroy(c->graph_exec));
-    c->graph_exec = nullptr;
-  }
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
   return MHD_OK;
 }
 
@@ -701,6 +720,176 @@ mhd_status mhd_restore(mhd_ctx *c, int32_t inst, const double *buf, int32_t on_d
   CK(cudaMemcpyAsync(c->ts + inst, buf + 4 * sp, sizeof(mhd::TimeState), k, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->is_set[inst] = 1;
+  return MHD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Serving pools
+// ------------------------------------------------------------------------------------------
+}  // extern "C"
+
+struct mhd_pool {
+  mhd_ctx *ctx = nullptr;
+  std::vector<int> pos_of;     // slot handle -> instance position (-1: free)
+  std::vector<int> handle_at;  // instance position -> slot handle
+};
+
+// Copy instance `from` onto position `to` (state, history, time state, parameters).
+static mhd_status move_instance(mhd_ctx *c, int from, int to) {
+  const size_t sp = 7 * c->d.spec;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (c->precision == MHD_FP64) {
+    CK(cudaMemcpyAsync(state64(c, to), state64(c, from), sp * sizeof(cplx64), k, c->stream));
+    CK(cudaMemcpyAsync(c->H + (size_t)to * sp, c->H + (size_t)from * sp, sp * sizeof(cplx64), k, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(state_hi(c, to), state_hi(c, from), sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(state_lo(c, to), state_lo(c, from), sp * sizeof(cplx32), k, c->stream));
+    CK(cudaMemcpyAsync(hist32(c, to), hist32(c, from), sp * sizeof(cplx32), k, c->stream));
+  }
+  CK(cudaMemcpyAsync(c->ts + to, c->ts + from, sizeof(mhd::TimeState), k, c->stream));
+  CK(cudaMemcpyAsync(c->phys + to, c->phys + from, sizeof(mhd::PhysDev), k, c->stream));
+  c->phys_host[to] = c->phys_host[from];
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+static mhd_status pool_position(mhd_pool *p, int32_t slot, int *pos) {
+  if (!p) return MHD_EINVAL;
+  if (slot < 0 || slot >= (int)p->pos_of.size() || p->pos_of[slot] < 0)
+    return fail(p->ctx, MHD_EINVAL, "slot %d is not in use", slot);
+  *pos = p->pos_of[slot];
+  return MHD_OK;
+}
+
+extern "C" {
+
+mhd_status mhd_pool_create(const mhd_params *params, mhd_pool **out) {
+  if (!out) return MHD_EINVAL;
+  *out = nullptr;
+  if (!params || params->batch < 1) return MHD_EINVAL;
+  std::vector<mhd_phys> ph(params->batch, mhd_phys{0.0, 0.0, 1.0});
+  mhd_ctx *c = nullptr;
+  mhd_status st = mhd_init(params, ph.data(), &c);
+  if (st) return st;
+  mhd_pool *p = new (std::nothrow) mhd_pool;
+  if (!p) {
+    mhd_destroy(c);
+    return MHD_ENOMEM;
+  }
+  p->ctx = c;
+  c->live = 0;
+  c->pool_graphs.assign(params->batch + 1, nullptr);
+  p->pos_of.assign(params->batch, -1);
+  p->handle_at.assign(params->batch, -1);
+  *out = p;
+  return MHD_OK;
+}
+
+void mhd_pool_destroy(mhd_pool *p) {
+  if (!p) return;
+  mhd_destroy(p->ctx);
+  delete p;
+}
+
+const char *mhd_pool_last_error(const mhd_pool *p) { return p ? mhd_last_error(p->ctx) : "null pool"; }
+
+mhd_status mhd_pool_admit(mhd_pool *p, const mhd_phys *phys, const double *rho, const double *u, const double *b,
+                          int32_t on_device, int64_t nsteps, int32_t *slot) {
+  if (!p || !phys || !slot) return MHD_EINVAL;
+  mhd_ctx *c = p->ctx;
+  if (nsteps < 1) return fail(c, MHD_EINVAL, "a run needs at least one step");
+  if (!(phys->nu >= 0.0) || !(phys->eta >= 0.0) || !(phys->cs > 0.0) || !isfinite(phys->nu) ||
+      !isfinite(phys->eta) || !isfinite(phys->cs))
+    return fail(c, MHD_EINVAL, "bad physical parameters");
+  if (c->live >= c->d.batch) return MHD_EBUSY;
+  int handle = -1;
+  for (int h = 0; h < (int)p->pos_of.size(); ++h)
+    if (p->pos_of[h] < 0) {
+      handle = h;
+      break;
+    }
+  if (handle < 0) return MHD_EBUSY;
+  DeviceGuard g(c->device);
+  const int pos = c->live;
+  const mhd::PhysDev pd{phys->nu, phys->eta, phys->cs};
+  CK(cudaMemcpyAsync(c->phys + pos, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
+  c->phys_host[pos] = *phys;
+  mhd_status st = mhd_set_state(c, pos, rho, u, b, on_device);
+  if (st) return st;
+  const int64_t lim = nsteps;
+  CK(cudaMemcpyAsync(&c->ts[pos].step_limit, &lim, sizeof lim, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  p->pos_of[handle] = pos;
+  p->handle_at[pos] = handle;
+  c->live = pos + 1;
+  *slot = handle;
+  return MHD_OK;
+}
+
+mhd_status mhd_pool_step(mhd_pool *p, int32_t k) {
+  if (!p) return MHD_EINVAL;
+  mhd_ctx *c = p->ctx;
+  if (k < 0) return fail(c, MHD_EINVAL, "negative step count");
+  DeviceGuard g(c->device);
+  return step_prefix(c, c->live, k, &c->pool_graphs[c->live]);
+}
+
+mhd_status mhd_pool_progress(mhd_pool *p, int64_t *steps, int32_t *status, int32_t *finished) {
+  if (!p || !steps || !status || !finished) return MHD_EINVAL;
+  mhd_ctx *c = p->ctx;
+  DeviceGuard g(c->device);
+  std::vector<mhd::TimeState> ts(c->live > 0 ? c->live : 1);
+  if (c->live > 0) {
+    CK(cudaMemcpyAsync(ts.data(), c->ts, c->live * sizeof(mhd::TimeState), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (int h = 0; h < (int)p->pos_of.size(); ++h) {
+    const int pos = p->pos_of[h];
+    if (pos < 0) {
+      steps[h] = -1;
+      status[h] = 0;
+      finished[h] = 0;
+    } else {
+      steps[h] = ts[pos].step;
+      status[h] = ts[pos].status;
+      finished[h] = ts[pos].status != 0 || (ts[pos].step_limit > 0 && ts[pos].step >= ts[pos].step_limit);
+    }
+  }
+  return MHD_OK;
+}
+
+mhd_status mhd_pool_diagnostics(mhd_pool *p, int32_t slot, mhd_diag *out) {
+  int pos = 0;
+  mhd_status st = pool_position(p, slot, &pos);
+  if (st) return st;
+  return mhd_diagnostics(p->ctx, pos, out);
+}
+
+mhd_status mhd_pool_retire(mhd_pool *p, int32_t slot, double *rho, double *m, double *b, int32_t on_device) {
+  int pos = 0;
+  mhd_status st = pool_position(p, slot, &pos);
+  if (st) return st;
+  mhd_ctx *c = p->ctx;
+  DeviceGuard g(c->device);
+  if (rho && m && b) {
+    if ((st = mhd_get_state(c, pos, rho, m, b, on_device))) return st;
+  }
+  const int last = c->live - 1;
+  if (pos != last) {
+    if ((st = move_instance(c, last, pos))) return st;
+    p->handle_at[pos] = p->handle_at[last];
+    p->pos_of[p->handle_at[pos]] = pos;
+  }
+  p->pos_of[slot] = -1;
+  p->handle_at[last] = -1;
+  c->live = last;
+  return MHD_OK;
+}
+
+mhd_status mhd_pool_info(const mhd_pool *p, int32_t *live, int32_t *max_slots) {
+  if (!p || !live || !max_slots) return MHD_EINVAL;
+  *live = p->ctx->live;
+  *max_slots = p->ctx->d.batch;
   return MHD_OK;
 }
 

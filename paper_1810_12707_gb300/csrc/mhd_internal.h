@@ -32,12 +32,13 @@ using cplx32 = cplx<float>;
 
 // Per-instance time-stepping state, device resident.
 struct TimeState {
-  double t;        // simulated time
-  double dt_prev;  // step size of the previous step (0 before the first)
-  double dt_last;  // step size of the last completed step, for diagnostics
-  int64_t step;    // steps taken
-  int32_t status;  // 0, or MHD_ENONFINITE once the instance stopped
+  double t;            // simulated time
+  double dt_prev;      // step size of the previous step (0 before the first)
+  double dt_last;      // step size of the last completed step, for diagnostics
+  int64_t step;        // steps taken
+  int32_t status;      // 0, or MHD_ENONFINITE once the instance stopped
   int32_t pad;
+  int64_t step_limit;  // 0: no limit; else the instance stops advancing at this step count
 };
 
 // Coefficients of the current step, written by the dt kernel and read by the update kernel:

@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4
 EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "mhd_set_state",
            "mhd_get_state", "mhd_rhs", "mhd_get_spectrum", "mhd_step", "mhd_synchronize",
            "mhd_diagnostics", "mhd_checkpoint_doubles", "mhd_checkpoint", "mhd_restore", "mhd_profile",
-           "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option")
+           "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
+           "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
+           "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info")
 
 
 class MhdError(RuntimeError):
@@ -111,6 +113,24 @@ def load_library(path: str = LIBRARY):
     lib.mhd_profile.argtypes = [P, I32]
     lib.mhd_profile_read.restype = I32
     lib.mhd_profile_read.argtypes = [P, ctypes.POINTER(MhdKernelTime), I32, ctypes.POINTER(I32)]
+    lib.mhd_pool_create.restype = I32
+    lib.mhd_pool_create.argtypes = [ctypes.POINTER(MhdParams), ctypes.POINTER(P)]
+    lib.mhd_pool_destroy.restype = None
+    lib.mhd_pool_destroy.argtypes = [P]
+    lib.mhd_pool_last_error.restype = ctypes.c_char_p
+    lib.mhd_pool_last_error.argtypes = [P]
+    lib.mhd_pool_admit.restype = I32
+    lib.mhd_pool_admit.argtypes = [P, ctypes.POINTER(MhdPhys), P, P, P, I32, ctypes.c_int64, ctypes.POINTER(I32)]
+    lib.mhd_pool_step.restype = I32
+    lib.mhd_pool_step.argtypes = [P, I32]
+    lib.mhd_pool_progress.restype = I32
+    lib.mhd_pool_progress.argtypes = [P, P, P, P]
+    lib.mhd_pool_diagnostics.restype = I32
+    lib.mhd_pool_diagnostics.argtypes = [P, I32, ctypes.POINTER(MhdDiag)]
+    lib.mhd_pool_retire.restype = I32
+    lib.mhd_pool_retire.argtypes = [P, I32, P, P, P, I32]
+    lib.mhd_pool_info.restype = I32
+    lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.mhd_set_option.restype = I32
     lib.mhd_set_option.argtypes = [P, I32, ctypes.c_int64]
     lib.mhd_rhs_noalloc.restype = I32
@@ -345,3 +365,110 @@ def mhd_rhs_noalloc(n: int, phys, rho, u, b, stream=None):
     if st != MHD_OK:
         raise MhdError(st, "mhd_rhs_noalloc failed")
     return tuple(outs)
+
+
+# ---- serving pools ----
+
+class Pool:
+    """An ``mhd_pool*`` (see include/mhd.h): slots of one grid size stepped together."""
+
+    def __init__(self, handle: int, n: int, slots: int, keepalive=()):
+        self.handle, self.n, self.slots, self.keepalive = handle, n, slots, keepalive
+
+    def __del__(self):
+        try:
+            mhd_pool_destroy(self)
+        except Exception:
+            pass
+
+
+def _pcheck(pool, status: int):
+    if status != MHD_OK:
+        msg = load_library().mhd_pool_last_error(pool.handle)
+        raise MhdError(status, (msg or b"").decode())
+
+
+def mhd_pool_create(n: int, slots: int, dt: float = 0.0, cfl_adv: float = 0.2, cfl_visc: float = 0.5,
+                    precision: int = MHD_FP32_MIXED, allocator: str = "torch", stream=None) -> Pool:
+    lib = load_library()
+    keep = []
+    alloc = free = None
+    if stream is None:
+        try:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        except ImportError:
+            stream = None
+    if allocator == "torch":
+        alloc, free = _torch_allocator()
+        keep += [alloc, free]
+    p = MhdParams(int(n), int(slots), int(precision), 0, float(dt), float(cfl_adv), float(cfl_visc),
+                  ctypes.c_void_p(stream) if stream else None,
+                  alloc if alloc else ALLOC_FN(), free if free else FREE_FN(), None)
+    h = ctypes.c_void_p()
+    st = lib.mhd_pool_create(ctypes.byref(p), ctypes.byref(h))
+    if st != MHD_OK:
+        raise MhdError(st, "mhd_pool_create failed")
+    return Pool(h.value, int(n), int(slots), tuple(keep))
+
+
+def mhd_pool_destroy(pool: Pool) -> None:
+    if pool.handle:
+        load_library().mhd_pool_destroy(pool.handle)
+        pool.handle = 0
+
+
+def mhd_pool_admit(pool: Pool, phys, rho, u, b, nsteps: int):
+    """Admit a run; returns its slot handle, or None if every slot is busy."""
+    n = pool.n
+    pr, d0, k0 = _in_ptr(rho, (n, n, n))
+    pu, d1, k1 = _in_ptr(u, (3, n, n, n))
+    pb, d2, k2 = _in_ptr(b, (3, n, n, n))
+    ph = MhdPhys(*[float(v) for v in phys])
+    slot = ctypes.c_int32()
+    st = load_library().mhd_pool_admit(pool.handle, ctypes.byref(ph), pr, pu, pb, d0, int(nsteps), ctypes.byref(slot))
+    if st == MHD_EBUSY:
+        return None
+    _pcheck(pool, st)
+    return slot.value
+
+
+def mhd_pool_step(pool: Pool, k: int) -> None:
+    _pcheck(pool, load_library().mhd_pool_step(pool.handle, int(k)))
+
+
+def mhd_pool_progress(pool: Pool):
+    """(steps, status, finished) arrays indexed by slot handle."""
+    steps = np.zeros(pool.slots, dtype=np.int64)
+    status = np.zeros(pool.slots, dtype=np.int32)
+    fin = np.zeros(pool.slots, dtype=np.int32)
+    _pcheck(pool, load_library().mhd_pool_progress(pool.handle, steps.ctypes.data, status.ctypes.data, fin.ctypes.data))
+    return steps, status, fin
+
+
+def mhd_pool_diagnostics(pool: Pool, slot: int) -> dict:
+    d = MhdDiag()
+    _pcheck(pool, load_library().mhd_pool_diagnostics(pool.handle, int(slot), ctypes.byref(d)))
+    out = {name: getattr(d, name) for name, _ in MhdDiag._fields_ if name not in ("mean_m", "mean_b", "reserved")}
+    out["etot"] = d.ke + d.me + d.eint
+    return out
+
+
+def mhd_pool_retire(pool: Pool, slot: int, copy_out: bool = True):
+    """Free the slot; returns (rho, m, B) as numpy arrays (or None with copy_out=False)."""
+    n = pool.n
+    if copy_out:
+        a = np.empty((n, n, n))
+        m = np.empty((3, n, n, n))
+        b = np.empty((3, n, n, n))
+        _pcheck(pool, load_library().mhd_pool_retire(pool.handle, int(slot), a.ctypes.data, m.ctypes.data,
+                                                      b.ctypes.data, 0))
+        return a, m, b
+    _pcheck(pool, load_library().mhd_pool_retire(pool.handle, int(slot), None, None, None, 0))
+    return None
+
+
+def mhd_pool_info(pool: Pool):
+    live, mx = ctypes.c_int32(), ctypes.c_int32()
+    _pcheck(pool, load_library().mhd_pool_info(pool.handle, ctypes.byref(live), ctypes.byref(mx)))
+    return live.value, mx.value
