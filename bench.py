@@ -380,6 +380,36 @@ def run_ours(args, name, cfg):
     return 0
 
 
+def run_plain_cufft(args, name, cfg):
+    """The same configuration on the plain cuFFT build (baseline/cufft_plain.py), device-timed."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "baseline"))
+    from cufft_plain import PlainMHD
+    torch.cuda.set_device(0)
+    n, K, W = cfg["n"], args.steps, args.warmup
+    ic = workload(n, cfg["ic"], 1)[0]
+    dtype = torch.float64 if cfg["precision"] == "fp64" else torch.float32
+    p = PlainMHD(n, ic.nu, ic.eta, ic.cs, dt=cfg["dt"], dtype=dtype)
+    p.set_state(ic.rho, ic.u, ic.b)
+    p.step(W)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    p.step(K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = n ** 3 * K / (ms / 1e3)
+    line = {"impl": "cufft_plain", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_256_V100 if n == 256 else None,
+            "dtype": "f64" if dtype == torch.float64 else "f32", "data": "synthetic",
+            "config": config_block(name, cfg, 1),
+            "note": "full-spectrum cuFFT (torch.fft) per field, unfused elementwise products and update"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Serving configuration: Poisson stream of run requests (N in {32,64,128,256} with weights
     .4/.3/.2/.1, ABC or Orszag-Tang, nu, eta ~ U[1e-3,1e-2], Mach ~ U[0.05,0.5], 100-1000 steps,
@@ -443,7 +473,7 @@ def main():
     ap.add_argument("--batch", type=int)
     ap.add_argument("--precision", choices=("fp64", "fp32"))
     ap.add_argument("--ic", choices=("abc", "tg", "ot", "ens"))
-    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--impl", choices=("ours", "reference", "cufft"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving configuration instead")
@@ -462,6 +492,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, name, cfg)
+    if args.impl == "cufft":
+        return run_plain_cufft(args, name, cfg)
     return run_ours(args, name, cfg)
 
 

@@ -29,7 +29,13 @@
  *   magnetic      Heaviside-Lorentz units: B^2/2 and B(x)B, as in Eq. velocity
  *   pressure      -grad P = -i k Cs^2 rho_hat, taken from the (already dealiased) density spectrum
  *   integrator    Adams-Bashforth of order 2 with variable step (forward Euler on the first step):
- *                 y^{n+1} = y^n + dt_n [ (1 + r/2) f^n - (r/2) f^{n-1} ],  r = dt_n / dt_{n-1}
+ *                 y^{n+1} = y^n + dt_n [ (1 + r/2) f^n - (r/2) f^{n-1} ],  r = dt_n / dt_{n-1};
+ *                 also the classical fourth-order Runge-Kutta method and a predictor-corrector
+ *                 (the paper lists Adams-Bashforth, RK4 and predictor-corrector solvers; its
+ *                 results use Adams-Bashforth).  The predictor-corrector is read as the AB2
+ *                 predictor above followed by one trapezoidal (Adams-Moulton order 2) correction,
+ *                 y^{n+1} = y^n + dt/2 [ f^n + f(y*) ].  Every method takes dt from the CFL
+ *                 condition at y^n.
  *   CFL           dt = min( C_a dx / max_x(|u| + c_f),  C_v / (max(nu, eta) k_max^2) ),
  *                 dx = 2 pi / N, c_f = sqrt(Cs^2 + |B|^2 / rho), k_max = floor((N-1)/3);
  *                 a fixed dt is used instead when one is given.
@@ -208,6 +214,7 @@ typedef struct {
   double nu, eta, cs;   /* viscosity (mu), resistivity, isothermal sound speed */
   double dt_fixed;      /* > 0: fixed step; <= 0: CFL step */
   double cfl_adv, cfl_visc;
+  int integrator;       /* 0 Adams-Bashforth 2, 1 Runge-Kutta 4, 2 predictor-corrector */
 } or_params;
 
 typedef struct {
@@ -216,6 +223,8 @@ typedef struct {
   cplx *state[NSTATE]; /* masked spectra of rho, m, B */
   cplx *hist[NSTATE];  /* f^{n-1}: the RHS of the previous step */
   cplx *rhs[NSTATE];
+  cplx *ystage[NSTATE]; /* intermediate states of the multi-stage methods */
+  cplx *kacc[NSTATE];   /* RK4 weighted sum of the stage derivatives */
   cplx *flux[NFLUX];
   double *real[NSTATE];
   double *rflux[NFLUX];
@@ -230,6 +239,8 @@ static void ctx_free(or_ctx *c) {
     free(c->state[f]);
     free(c->hist[f]);
     free(c->rhs[f]);
+    free(c->ystage[f]);
+    free(c->kacc[f]);
     free(c->real[f]);
   }
   for (int f = 0; f < NFLUX; ++f) {
@@ -241,7 +252,7 @@ static void ctx_free(or_ctx *c) {
 }
 
 or_ctx *or_create(const or_params *p) {
-  if (!p || !is_pow2(p->n) || p->n < 4) return NULL;
+  if (!p || !is_pow2(p->n) || p->n < 4 || p->integrator < 0 || p->integrator > 2) return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   if (!c) return NULL;
   c->p = *p;
@@ -251,6 +262,8 @@ or_ctx *or_create(const or_params *p) {
     ok &= (c->state[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
     ok &= (c->hist[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
     ok &= (c->rhs[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->ystage[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
+    ok &= (c->kacc[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
     ok &= (c->real[f] = (double *)calloc(c->n3, sizeof(double))) != NULL;
   }
   for (int f = 0; f < NFLUX; ++f) {
@@ -342,15 +355,16 @@ int or_set_spectrum(or_ctx *c, int field, const cplx *in) {
  *        m_t,i   = -i sum_j k_j T_ij_hat - i k_i Cs^2 rho_hat - nu |k|^2 u_i_hat
  *        B_t     =  i k x E_hat - eta |k|^2 B_hat
  *   5. multiplication of every RHS spectrum by the 2/3 mask D(k).
- * Also returns max_x(|u| + c_f) over the grid (for the CFL step) in *smax.
+ * The state is `y` and the RHS goes to `out` (7 spectra each).  Also returns max_x(|u| + c_f)
+ * over the grid (for the CFL step) in *smax.
  */
-static int compute_rhs(or_ctx *c, double *smax) {
+static int compute_rhs_of(or_ctx *c, cplx *const *y, cplx *const *out, double *smax) {
   const int n = c->p.n;
   const size_t n3 = c->n3;
   const double cs2 = c->p.cs * c->p.cs;
 
   /* 1. */
-  for (int f = 0; f < NSTATE; ++f) or_inverse_tmp(c->state[f], c->real[f], n, c->tmp);
+  for (int f = 0; f < NSTATE; ++f) or_inverse_tmp(y[f], c->real[f], n, c->tmp);
 
   /* 2. */
   double *plane_max = (double *)calloc((size_t)n, sizeof(double));
@@ -393,20 +407,21 @@ static int compute_rhs(or_ctx *c, double *smax) {
 
   /* 4. and 5. */
   const double nu = c->p.nu, eta = c->p.eta;
+  cplx *const *yv = y;
 #pragma omp parallel for schedule(static)
   for (int z = 0; z < n; ++z) {
     for (int y = 0; y < n; ++y) {
       for (int x = 0; x < n; ++x) {
         const size_t i = ((size_t)z * n + y) * n + x;
         if (!mask23(x, y, z, n)) {
-          for (int f = 0; f < NSTATE; ++f) c->rhs[f][i] = 0.0;
+          for (int f = 0; f < NSTATE; ++f) out[f][i] = 0.0;
           continue;
         }
         const double k[3] = {wavenumber(x, n), wavenumber(y, n), wavenumber(z, n)};
         const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-        const cplx rho = c->state[F_RHO][i];
-        const cplx mh[3] = {c->state[F_MX][i], c->state[F_MY][i], c->state[F_MZ][i]};
-        const cplx Bh[3] = {c->state[F_BX][i], c->state[F_BY][i], c->state[F_BZ][i]};
+        const cplx rho = yv[F_RHO][i];
+        const cplx mh[3] = {yv[F_MX][i], yv[F_MY][i], yv[F_MZ][i]};
+        const cplx Bh[3] = {yv[F_BX][i], yv[F_BY][i], yv[F_BZ][i]};
         /* symmetric momentum-flux tensor T_ij_hat */
         const cplx Txx = c->flux[T_XX][i], Tyy = c->flux[T_YY][i], Tzz = c->flux[T_ZZ][i];
         const cplx Txy = c->flux[T_XY][i], Txz = c->flux[T_XZ][i], Tyz = c->flux[T_YZ][i];
@@ -415,21 +430,23 @@ static int compute_rhs(or_ctx *c, double *smax) {
         const cplx uh[3] = {c->flux[U_X][i], c->flux[U_Y][i], c->flux[U_Z][i]};
 
         /* continuity */
-        c->rhs[F_RHO][i] = -I * (k[0] * mh[0] + k[1] * mh[1] + k[2] * mh[2]);
+        out[F_RHO][i] = -I * (k[0] * mh[0] + k[1] * mh[1] + k[2] * mh[2]);
         /* momentum */
         for (int a = 0; a < 3; ++a) {
           cplx divT = k[0] * T[a][0] + k[1] * T[a][1] + k[2] * T[a][2];
-          c->rhs[F_MX + a][i] = -I * divT - I * k[a] * cs2 * rho - nu * k2 * uh[a];
+          out[F_MX + a][i] = -I * divT - I * k[a] * cs2 * rho - nu * k2 * uh[a];
         }
         /* induction: curl E with E = u x B */
         const cplx curlE[3] = {I * (k[1] * Eh[2] - k[2] * Eh[1]), I * (k[2] * Eh[0] - k[0] * Eh[2]),
                                I * (k[0] * Eh[1] - k[1] * Eh[0])};
-        for (int a = 0; a < 3; ++a) c->rhs[F_BX + a][i] = curlE[a] - eta * k2 * Bh[a];
+        for (int a = 0; a < 3; ++a) out[F_BX + a][i] = curlE[a] - eta * k2 * Bh[a];
       }
     }
   }
   return 0;
 }
+
+static int compute_rhs(or_ctx *c, double *smax) { return compute_rhs_of(c, c->state, c->rhs, smax); }
 
 /* Real-space RHS of the current state: drho (N^3), dm (3 N^3), dB (3 N^3).  State unchanged. */
 int or_rhs(or_ctx *c, double *drho, double *dm, double *db) {
@@ -465,30 +482,68 @@ static double cfl_dt(const or_ctx *c, double smax) {
   return dt;
 }
 
+/* dst = a + w * b for all 7 fields (b may be NULL: dst = a). */
+static void axpy7(cplx *const *dst, cplx *const *a, double w, cplx *const *b, size_t n3) {
+  for (int f = 0; f < NSTATE; ++f) {
+    cplx *d = dst[f];
+    const cplx *x = a[f], *y = b ? b[f] : NULL;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)n3; ++i) d[i] = y ? x[i] + w * y[i] : x[i];
+  }
+}
+
 /*
- * Advance `nsteps` Adams-Bashforth steps (order 2, variable dt; forward Euler when there is no
- * previous RHS).  Returns 0, or 1 if a non-finite value appeared in max(|u| + c_f) or dt (the
- * state is then left at the last finite step).
+ * Advance `nsteps` steps of the configured method.  Returns 0, or 1 if a non-finite value
+ * appeared in max(|u| + c_f) or dt at the start of a step (the state is then left at the last
+ * finite step).
+ *   AB2  y^{n+1} = y^n + dt [(1 + r/2) f^n - (r/2) f^{n-1}]   (Euler when there is no f^{n-1})
+ *   RK4  k1 = f(y), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2), k4 = f(y + dt k3),
+ *        y^{n+1} = y^n + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+ *   PC   y* = AB2 predictor, y^{n+1} = y^n + dt/2 [f^n + f(y*)]
  */
 int or_step(or_ctx *c, int nsteps) {
   const size_t n3 = c->n3;
   for (int s = 0; s < nsteps; ++s) {
     double smax = 0.0;
-    compute_rhs(c, &smax);
+    compute_rhs(c, &smax); /* f^n = f(y^n) in c->rhs */
     const double dt = c->p.dt_fixed > 0.0 ? c->p.dt_fixed : cfl_dt(c, smax);
     if (!isfinite(smax) || !isfinite(dt) || dt <= 0.0) return 1;
-    double a1 = 1.0, a0 = 0.0; /* coefficients of f^n and f^{n-1} */
+    double a1 = 1.0, a0 = 0.0; /* AB2 coefficients of f^n and f^{n-1} */
     if (c->step > 0) {
       const double r = dt / c->dt_prev;
       a1 = 1.0 + 0.5 * r;
       a0 = -0.5 * r;
     }
-    for (int f = 0; f < NSTATE; ++f) {
-      cplx *y = c->state[f], *fn = c->rhs[f], *fo = c->hist[f];
+    if (c->p.integrator == 1) {
+      /* k1 in c->rhs; kacc accumulates k1 + 2 k2 + 2 k3 + k4 */
+      axpy7(c->kacc, c->rhs, 0.0, NULL, n3);
+      const double cstage[3] = {0.5, 0.5, 1.0};
+      for (int st = 0; st < 3; ++st) {
+        axpy7(c->ystage, c->state, cstage[st] * dt, c->rhs, n3);
+        compute_rhs_of(c, c->ystage, c->rhs, NULL);
+        axpy7(c->kacc, c->kacc, st < 2 ? 2.0 : 1.0, c->rhs, n3);
+      }
+      axpy7(c->state, c->state, dt / 6.0, c->kacc, n3);
+    } else {
+      for (int f = 0; f < NSTATE; ++f) {
+        cplx *y = (c->p.integrator == 2) ? c->ystage[f] : c->state[f];
+        const cplx *y0 = c->state[f], *fn = c->rhs[f];
+        cplx *fo = c->hist[f];
 #pragma omp parallel for schedule(static)
-      for (long i = 0; i < (long)n3; ++i) {
-        y[i] = y[i] + dt * (a1 * fn[i] + a0 * fo[i]);
-        fo[i] = fn[i];
+        for (long i = 0; i < (long)n3; ++i) {
+          y[i] = y0[i] + dt * (a1 * fn[i] + a0 * fo[i]);
+          fo[i] = fn[i];
+        }
+      }
+      if (c->p.integrator == 2) {
+        /* corrector: f(y*) into c->rhs, then y^{n+1} = y^n + dt/2 (f^n + f(y*)); f^n is in hist */
+        compute_rhs_of(c, c->ystage, c->rhs, NULL);
+        for (int f = 0; f < NSTATE; ++f) {
+          cplx *y = c->state[f];
+          const cplx *fn = c->hist[f], *fs = c->rhs[f];
+#pragma omp parallel for schedule(static)
+          for (long i = 0; i < (long)n3; ++i) y[i] = y[i] + 0.5 * dt * (fn[i] + fs[i]);
+        }
       }
     }
     c->dt_prev = dt;

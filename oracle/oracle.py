@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("eta", ctypes.c_double),
                 ("cs", ctypes.c_double), ("dt_fixed", ctypes.c_double),
-                ("cfl_adv", ctypes.c_double), ("cfl_visc", ctypes.c_double)]
+                ("cfl_adv", ctypes.c_double), ("cfl_visc", ctypes.c_double), ("integrator", ctypes.c_int)]
 
 
 def _declare(lib):
@@ -149,12 +149,14 @@ def inverse(fh) -> np.ndarray:
 class Oracle:
     """One solver instance of the oracle (see ``mhd_oracle.c`` for the method and readings)."""
 
+    AB2, RK4, PC = 0, 1, 2
+
     def __init__(self, n: int, nu: float, eta: float, cs: float, dt: float = 0.0,
-                 cfl_adv: float = 0.2, cfl_visc: float = 0.5, lib=None):
+                 cfl_adv: float = 0.2, cfl_visc: float = 0.5, lib=None, integrator: int = 0):
         lib = lib if lib is not None else _load()
         self.n = int(n)
         self.params = _Params(self.n, float(nu), float(eta), float(cs), float(dt),
-                              float(cfl_adv), float(cfl_visc))
+                              float(cfl_adv), float(cfl_visc), int(integrator))
         self._h = lib.or_create(ctypes.byref(self.params))
         if not self._h:
             raise ValueError(f"oracle: cannot create instance (n={n} must be a power of two >= 4)")

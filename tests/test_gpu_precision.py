@@ -101,3 +101,23 @@ def test_taylor_green_512_mixed_vs_fp64(lib):
     errs = [rel_l2(g, e) for g, e in zip(got, ref)]
     print("512^3 mixed vs fp64 rel L2 (rho, m, B):", errs)
     assert all(e <= 1e-5 for e in errs)
+
+
+def test_plain_cufft_baseline_matches_oracle(lib, oracle_mod):
+    """The cuFFT-based plain build computes the same step (it is only a timing baseline)."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "baseline"))
+    from cufft_plain import PlainMHD
+    ic = inputs.orszag_tang(32, seed=0)
+    p = PlainMHD(32, ic.nu, ic.eta, ic.cs)
+    p.set_state(ic.rho, ic.u, ic.b)
+    p.step(20)
+    o = oracle_mod.Oracle(32, ic.nu, ic.eta, ic.cs)
+    o.set_state(ic.rho, ic.u, ic.b)
+    o.step(20)
+    r, m, b = o.get_state()
+    got = p.get_state()
+    assert rel_l2(got[0], r) <= 1e-10
+    assert rel_l2(np.stack(got[1:4]), m) <= 1e-10
+    assert rel_l2(np.stack(got[4:7]), b) <= 1e-10

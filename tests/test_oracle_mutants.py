@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import sympy as sp
 
+import test_oracle_integrators as integ
 import test_oracle_invariants as inv
 import test_oracle_linear_waves as lw
 import test_oracle_rhs_closed_form as rc
@@ -17,7 +18,7 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 
 # (name, text in the source, replacement)
 MUTANTS = [
-    ("continuity sign", "c->rhs[F_RHO][i] = -I *", "c->rhs[F_RHO][i] = I *"),
+    ("continuity sign", "out[F_RHO][i] = -I *", "out[F_RHO][i] = I *"),
     ("pressure sign", "- I * k[a] * cs2 * rho", "+ I * k[a] * cs2 * rho"),
     ("magnetic pressure dropped", "m[0] * u[0] + 0.5 * b2 - B[0] * B[0]", "m[0] * u[0] - B[0] * B[0]"),
     ("magnetic tension sign", "m[0] * u[1] - B[0] * B[1]", "m[0] * u[1] + B[0] * B[1]"),
@@ -32,6 +33,9 @@ MUTANTS = [
     ("forward normalisation", "const double s = 1.0 / (double)n3;", "const double s = 1.0 / (double)(n3 / n);"),
     ("twiddle sign", "return cos(ang) + (double)sign * sin(ang) * I;", "return cos(ang) - (double)sign * sin(ang) * I;"),
     ("CFL uses c_s only", "const double cf = sqrt(cs2 + b2 / rho);", "const double cf = sqrt(cs2);"),
+    ("RK4 stage weights", "st < 2 ? 2.0 : 1.0", "st < 2 ? 1.0 : 2.0"),
+    ("RK4 stage point", "const double cstage[3] = {0.5, 0.5, 1.0};", "const double cstage[3] = {0.5, 1.0, 1.0};"),
+    ("PC corrector weight", "y[i] + 0.5 * dt * (fn[i] + fs[i])", "y[i] + dt * (fn[i] + fs[i])"),
 ]
 
 
@@ -92,6 +96,15 @@ def _battery(om, lib):
     expect = 0.2 * (2 * np.pi / n) / np.sqrt(0.25 + 4.0)
     if abs(o.diagnostics()["dt"] - expect) > 1e-12 * expect:
         failed.append("cfl")
+    # RK4 and predictor-corrector on the sound wave
+    for method in (integ.RK4, integ.PC):
+        o = om.Oracle(n, nu, 0.01, cs, dt=0.01, lib=lib, integrator=method)
+        o.set_state(1.0 + lw.EPS * np.cos(k * X), np.zeros((3, n, n, n)), np.zeros((3, n, n, n)))
+        o.step(30)
+        y = integ.linear_run(A, [lw.EPS / 2, 0.0], [0.01] * 30, method)
+        gotm = np.array([o.spectrum(0)[i], o.spectrum(1)[i]])
+        if not np.all(np.isfinite(gotm)) or np.max(np.abs(gotm - y)) > 1e-5 * np.max(np.abs(y)):
+            failed.append(f"integrator {method}")
     # variable-step Adams-Bashforth against the integral of its interpolant
     if not check_variable_step(om, lib):
         failed.append("variable step")
