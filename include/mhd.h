@@ -62,13 +62,21 @@ typedef enum {
                          in FP64 */
 } mhd_precision;
 
+/* Explicit time solvers (paper, section "Code G-MHD3D", Table I; its results use
+ * Adams-Bashforth).  Each step takes dt from the CFL condition at the step's start state. */
+typedef enum {
+  MHD_AB2 = 0, /* Adams-Bashforth 2, variable step, forward Euler on the first step; 1 RHS/step */
+  MHD_RK4 = 1, /* classical Runge-Kutta 4; 4 RHS/step */
+  MHD_PC = 2   /* AB2 predictor + one trapezoidal (Adams-Moulton 2) corrector; 2 RHS/step */
+} mhd_integrator;
+
 typedef struct mhd_ctx mhd_ctx;
 
 typedef struct {
   int32_t n;          /* grid points per axis: a power of two, 16 <= n <= 1024 */
   int32_t batch;      /* independent instances sharing n, >= 1 */
   int32_t precision;  /* mhd_precision */
-  int32_t reserved0;  /* must be 0 */
+  int32_t integrator; /* mhd_integrator */
   double dt;          /* > 0: fixed step; <= 0: CFL step */
   double cfl_adv;     /* advective Courant number (default 0.2 when <= 0) */
   double cfl_visc;    /* diffusive number (default 0.5 when <= 0) */

@@ -17,10 +17,10 @@ namespace mhd {
 // FC: element type of the product spectra (FP64, or FP32 in the mixed mode); everything else,
 // the state, the history and the arithmetic, is FP64.
 template <typename FC>
-__global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict__ state,
-                                cplx64 *__restrict__ hist, cplx64 *__restrict__ rhs_out,
+__global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in, cplx64 *state,
+                                cplx64 *__restrict__ hist, cplx64 *ystage, cplx64 *__restrict__ rhs_out,
                                 const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
-                                int mode, int K, int batch, double inv_n3) {
+                                int op, int stage, int K, int batch, double inv_n3) {
   const int NX = K + 1, NK = 2 * K + 1;
   const size_t spec = (size_t)NK * NK * NX;
   const size_t total = spec * batch;
@@ -28,7 +28,7 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict_
        idx += (size_t)gridDim.x * blockDim.x) {
     const int inst = (int)(idx / spec);
     const size_t m = idx - (size_t)inst * spec;
-    if (mode == 1 && coef[inst].skip) continue;
+    if (op != ASM_RHS && coef[inst].skip) continue;
     const int kxi = (int)(m % NX);
     const size_t t = m / NX;
     const int jy = (int)(t % NK), jz = (int)(t / NK);
@@ -36,7 +36,7 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict_
     const double k2 = kx * kx + ky * ky + kz * kz;
     const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
 
-    const cplx64 *S = state + (size_t)inst * 7 * spec + m;
+    const cplx64 *S = y_in + (size_t)inst * 7 * spec + m;
     const FC *F = flux + (size_t)inst * 12 * spec + m;
     cplx64 y[7], f[12];
 #pragma unroll
@@ -75,24 +75,40 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, cplx64 *__restrict_
         r[4 + a] = cplx64{-c[a].im - eta * k2 * y[4 + a].re, c[a].re - eta * k2 * y[4 + a].im};
     }
 
-    if (mode == 0) {
-      cplx64 *R = rhs_out + (size_t)inst * 7 * spec + m;
+    const size_t o7 = (size_t)inst * 7 * spec + m;
+    if (op == ASM_RHS) {
 #pragma unroll
-      for (int q = 0; q < 7; ++q) R[q * spec] = r[q];
-    } else {
-      const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
-      cplx64 *Sw = state + (size_t)inst * 7 * spec + m;
-      cplx64 *H = hist + (size_t)inst * 7 * spec + m;
+      for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = r[q];
+      continue;
+    }
+    const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
 #pragma unroll
-      for (int q = 0; q < 7; ++q) {
-        cplx64 inc = {a1 * r[q].re, a1 * r[q].im};
+    for (int q = 0; q < 7; ++q) {
+      const size_t i = o7 + q * spec;
+      const cplx64 rq = r[q];
+      if (op == ASM_AB2 || op == ASM_PC_PRED) {
+        cplx64 inc = {a1 * rq.re, a1 * rq.im};
         if (a0 != 0.0) {
-          const cplx64 h = H[q * spec];
+          const cplx64 h = hist[i];
           inc.re += a0 * h.re;
           inc.im += a0 * h.im;
         }
-        Sw[q * spec] = cplx64{y[q].re + dt * inc.re, y[q].im + dt * inc.im};
-        H[q * spec] = r[q];
+        const cplx64 y0 = state[i];
+        const cplx64 yn = {y0.re + dt * inc.re, y0.im + dt * inc.im};
+        if (op == ASM_AB2) state[i] = yn;
+        else ystage[i] = yn;
+        hist[i] = rq;
+      } else if (op == ASM_RK_STAGE) {
+        const cplx64 acc = stage == 1 ? rq : cplx64{hist[i].re + 2.0 * rq.re, hist[i].im + 2.0 * rq.im};
+        hist[i] = acc;
+        const double w = (stage < 3 ? 0.5 : 1.0) * dt;
+        const cplx64 y0 = state[i];
+        ystage[i] = cplx64{y0.re + w * rq.re, y0.im + w * rq.im};
+      } else {  // ASM_RK_FINAL, ASM_PC_CORR
+        const double w = op == ASM_RK_FINAL ? dt / 6.0 : 0.5 * dt;
+        const cplx64 h = hist[i], y0 = state[i];
+        const cplx64 acc = {h.re + rq.re, h.im + rq.im};
+        state[i] = cplx64{y0.re + w * acc.re, y0.im + w * acc.im};
       }
     }
   }
@@ -108,10 +124,11 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
   lo = e - (hi - s);
 }
 
-__global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, cplx32 *__restrict__ s_hi,
-                                   cplx32 *__restrict__ s_lo, cplx32 *__restrict__ hist,
+__global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32 *y_in, cplx32 *s_hi,
+                                   cplx32 *__restrict__ s_lo, cplx32 *__restrict__ hist, cplx32 *ystage,
                                    cplx64 *__restrict__ rhs_out, const PhysDev *__restrict__ phys,
-                                   const StepCoef *__restrict__ coef, int mode, int K, int batch, float inv_n3) {
+                                   const StepCoef *__restrict__ coef, int op, int stage, int K, int batch,
+                                   float inv_n3) {
   const int NX = K + 1, NK = 2 * K + 1;
   const size_t spec = (size_t)NK * NK * NX;
   const size_t total = spec * batch;
@@ -119,7 +136,7 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, cplx32 *__re
        idx += (size_t)gridDim.x * blockDim.x) {
     const int inst = (int)(idx / spec);
     const size_t m = idx - (size_t)inst * spec;
-    if (mode == 1 && coef[inst].skip) continue;
+    if (op != ASM_RHS && coef[inst].skip) continue;
     const int kxi = (int)(m % NX);
     const size_t t = m / NX;
     const float kx = (float)kxi, ky = (float)kept_wave((int)(t % NK), K), kz = (float)kept_wave((int)(t / NK), K);
@@ -131,7 +148,7 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, cplx32 *__re
     const cplx32 *F = flux + (size_t)inst * 12 * spec + m;
     cplx32 y[7], f[12];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) y[q] = s_hi[base7 + q * spec];
+    for (int q = 0; q < 7; ++q) y[q] = y_in[base7 + q * spec];
 #pragma unroll
     for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
     const cplx32 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
@@ -160,27 +177,48 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, cplx32 *__re
       for (int a = 0; a < 3; ++a)
         r[4 + a] = cplx32{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
     }
-    if (mode == 0) {
-      cplx64 *R = rhs_out + (size_t)inst * 7 * spec + m;
+    if (op == ASM_RHS) {
 #pragma unroll
-      for (int q = 0; q < 7; ++q) R[q * spec] = c_cvt<cplx64>(r[q]);
-    } else {
-      const StepCoef cf = coef[inst];
+      for (int q = 0; q < 7; ++q) rhs_out[base7 + q * spec] = c_cvt<cplx64>(r[q]);
+      continue;
+    }
+    const StepCoef cf = coef[inst];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) {
-        cplx32 inc = {cf.fa1 * r[q].re, cf.fa1 * r[q].im};
+    for (int q = 0; q < 7; ++q) {
+      const size_t i = base7 + q * spec;
+      const cplx32 rq = r[q];
+      if (op == ASM_AB2 || op == ASM_PC_PRED) {
+        cplx32 inc = {cf.fa1 * rq.re, cf.fa1 * rq.im};
         if (cf.fa0 != 0.f) {
-          const cplx32 h = hist[base7 + q * spec];
+          const cplx32 h = hist[i];
           inc.re += cf.fa0 * h.re;
           inc.im += cf.fa0 * h.im;
         }
-        cplx32 lo = s_lo[base7 + q * spec];
-        float hr = y[q].re, hi_ = y[q].im;
-        df_add(hr, lo.re, cf.fdt * inc.re);
-        df_add(hi_, lo.im, cf.fdt * inc.im);
-        s_hi[base7 + q * spec] = cplx32{hr, hi_};
-        s_lo[base7 + q * spec] = lo;
-        hist[base7 + q * spec] = r[q];
+        if (op == ASM_AB2) {
+          cplx32 hi = s_hi[i], lo = s_lo[i];
+          df_add(hi.re, lo.re, cf.fdt * inc.re);
+          df_add(hi.im, lo.im, cf.fdt * inc.im);
+          s_hi[i] = hi;
+          s_lo[i] = lo;
+        } else {
+          const cplx32 hi = s_hi[i], lo = s_lo[i];
+          ystage[i] = cplx32{hi.re + (lo.re + cf.fdt * inc.re), hi.im + (lo.im + cf.fdt * inc.im)};
+        }
+        hist[i] = rq;
+      } else if (op == ASM_RK_STAGE) {
+        const cplx32 acc = stage == 1 ? rq : cplx32{hist[i].re + 2.f * rq.re, hist[i].im + 2.f * rq.im};
+        hist[i] = acc;
+        const float w = (stage < 3 ? 0.5f : 1.f) * cf.fdt;
+        const cplx32 hi = s_hi[i], lo = s_lo[i];
+        ystage[i] = cplx32{hi.re + (lo.re + w * rq.re), hi.im + (lo.im + w * rq.im)};
+      } else {  // ASM_RK_FINAL, ASM_PC_CORR
+        const float w = op == ASM_RK_FINAL ? cf.fdt / 6.f : 0.5f * cf.fdt;
+        const cplx32 h = hist[i];
+        cplx32 hi = s_hi[i], lo = s_lo[i];
+        df_add(hi.re, lo.re, w * (h.re + rq.re));
+        df_add(hi.im, lo.im, w * (h.im + rq.im));
+        s_hi[i] = hi;
+        s_lo[i] = lo;
       }
     }
   }
@@ -339,36 +377,23 @@ static unsigned grid_for(size_t total, int threads) {
   return (unsigned)(b == 0 ? 1 : b);
 }
 
-template <typename FC>
-static cudaError_t assemble_any(const FC *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
-                                const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                                cudaStream_t s) {
+cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *state, cplx64 *hist, cplx64 *ystage,
+                            cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op, int stage,
+                            const Dims &d, cudaStream_t s) {
   const size_t total = d.spec * d.batch;
   const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
-  assemble_kernel<FC><<<grid_for(total, 256), 256, 0, s>>>(flux, state, hist, rhs_out, phys, coef, mode, d.k,
-                                                           d.batch, inv_n3);
+  assemble_kernel<cplx64><<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, state, hist, ystage, rhs_out, phys, coef,
+                                                               op, stage, d.k, d.batch, inv_n3);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
-                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                            cudaStream_t s) {
-  return assemble_any(flux, state, hist, rhs_out, phys, coef, mode, d, s);
-}
-
-cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
-                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                            cudaStream_t s) {
-  return assemble_any(flux, state, hist, rhs_out, phys, coef, mode, d, s);
-}
-
-cudaError_t launch_assemble_df(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, cplx64 *rhs_out,
-                               const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                               cudaStream_t s) {
+cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist,
+                               cplx32 *ystage, cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op,
+                               int stage, const Dims &d, cudaStream_t s) {
   const size_t total = d.spec * d.batch;
   const float inv_n3 = (float)(1.0 / ((double)d.n * d.n * d.n));
-  assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, s_hi, s_lo, hist, rhs_out, phys, coef, mode, d.k,
-                                                          d.batch, inv_n3);
+  assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, s_hi, s_lo, hist, ystage, rhs_out, phys, coef,
+                                                          op, stage, d.k, d.batch, inv_n3);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ struct mhd_ctx {
   cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
   cplx32 *tw32 = nullptr;
   cplx64 *S64 = nullptr;  // mixed precision: FP64 copy of one instance's state for set/get/diagnostics
+  int integrator = MHD_AB2;
+  void *Y = nullptr;      // stage state of RK4 / predictor-corrector ([b][7][spec], working precision)
   size_t w1_len = 0, w2_len = 0;  // bytes / 16
   double *part = nullptr;
   size_t part_len = 0;
@@ -138,6 +140,7 @@ Sizes sizes_for(const mhd::Dims &d, int precision) {
 size_t footprint(const mhd::Dims &d, int precision) {
   const Sizes s = sizes_for(d, precision);
   return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + d.n * sizeof(cplx32) + s.part * sizeof(double) +
+         (precision == MHD_FP64 ? 0 : 7 * d.spec * sizeof(cplx64)) +
          d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) + 64 * sizeof(double);
 }
 
@@ -289,7 +292,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (!out) return MHD_EINVAL;
   *out = nullptr;
   if (!p || !phys) return MHD_EINVAL;
-  if (!valid_n(p->n) || p->batch < 1 || p->reserved0 != 0) return MHD_EINVAL;
+  if (!valid_n(p->n) || p->batch < 1) return MHD_EINVAL;
+  if (p->integrator < MHD_AB2 || p->integrator > MHD_PC) return MHD_EINVAL;
   if (p->precision != MHD_FP64 && p->precision != MHD_FP32_MIXED) return MHD_EINVAL;
   if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return MHD_EINVAL;
   for (int i = 0; i < p->batch; ++i) {
@@ -303,6 +307,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   c->p = *p;
   c->d = mhd::make_dims(p->n, p->batch);
   c->precision = p->precision;
+  c->integrator = p->integrator;
   c->stream = (cudaStream_t)p->stream;
   c->dt_fixed = p->dt > 0.0 ? p->dt : 0.0;
   c->cfl_adv = p->cfl_adv > 0.0 ? p->cfl_adv : 0.2;
@@ -324,6 +329,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->tw = (cplx64 *)dalloc(c, (size_t)c->d.n * sizeof(cplx64))) != nullptr;
   ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
   if (c->precision != MHD_FP64) ok = ok && (c->S64 = (cplx64 *)dalloc(c, 7 * c->d.spec * sizeof(cplx64))) != nullptr;
+  if (c->integrator != MHD_AB2)
+    ok = ok && (c->Y = dalloc(c, s.S * (c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32)))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
@@ -449,7 +456,8 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 
 // Steps 1-6 of the pass order for the instances in `d` starting at state `S`; leaves the 12
 // product spectra in W1.
-// CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.
+// CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.  `advance`
+// runs the step-size kernel after the flux pass.
 template <typename CF, typename CS>
 static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, const mhd::PhysDev *phys,
                                  mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw) {
@@ -469,26 +477,54 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, co
   return MHD_OK;
 }
 
-// Steps 1-6, then step 7: assembly into `rhs_out` (mode 0) or the AB2 update (mode 1), for the
-// `d.batch` instances starting at `inst0`.
-static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 *rhs_out,
-                              const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, int mode) {
-  const bool advance = mode == 1;
-  const bool prof = advance && c->profiling;
+// One RHS evaluation (steps 1-6 of the pass order at the state `y_in`, dt on the first
+// evaluation of a step) and the assembly operation `op` for the `d.batch` instances from `inst0`.
+static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, const void *y_in, cplx64 *rhs_out,
+                                    const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, bool first,
+                                    int op, int stage) {
+  const bool prof = op != mhd::ASM_RHS && c->profiling;
   mhd_status st;
+  const size_t off = (size_t)inst0 * 7 * d.spec;
   if (c->precision == MHD_FP64) {
-    cplx64 *S = state64(c, inst0);
-    cplx64 *H = mode == 1 ? c->H + (size_t)inst0 * 7 * d.spec : nullptr;
-    if ((st = flux_spectra_t<cplx64>(c, d, (const cplx64 *)S, phys, ts, coef, advance, c->tw))) return st;
-    LAUNCH(6, mhd::launch_assemble(c->W1, S, H, rhs_out, phys, coef, mode, d, c->stream));
+    const cplx64 *yi = static_cast<const cplx64 *>(y_in);
+    if ((st = flux_spectra_t<cplx64>(c, d, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw))) return st;
+    cplx64 *Y = c->Y ? static_cast<cplx64 *>(c->Y) + off : nullptr;
+    LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
+                                   c->stream));
   } else {
-    cplx32 *hi = state_hi(c, inst0), *lo = state_lo(c, inst0);
-    cplx32 *H = mode == 1 ? hist32(c, inst0) : nullptr;
-    if ((st = flux_spectra_t<cplx32>(c, d, (const cplx32 *)hi, phys, ts, coef, advance, c->tw32))) return st;
-    LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), hi, lo, H, rhs_out, phys, coef, mode,
-                                      d, c->stream));
+    const cplx32 *yi = static_cast<const cplx32 *>(y_in);
+    if ((st = flux_spectra_t<cplx32>(c, d, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32))) return st;
+    cplx32 *Y = c->Y ? static_cast<cplx32 *>(c->Y) + off : nullptr;
+    LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), yi, state_hi(c, inst0),
+                                      state_lo(c, inst0), hist32(c, inst0), Y, rhs_out, phys, coef, op, stage, d,
+                                      c->stream));
   }
   return MHD_OK;
+}
+
+// The RHS of instances [inst0, inst0 + d.batch) into `rhs_out` (mode 0), or one time step of the
+// context's solver (mode 1).
+static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 *rhs_out,
+                              const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, int mode) {
+  const size_t off = (size_t)inst0 * 7 * d.spec;
+  const void *y = c->precision == MHD_FP64 ? (const void *)state64(c, inst0) : (const void *)state_hi(c, inst0);
+  const void *Y = nullptr;
+  if (c->Y) Y = c->precision == MHD_FP64 ? (const void *)(static_cast<cplx64 *>(c->Y) + off)
+                                         : (const void *)(static_cast<cplx32 *>(c->Y) + off);
+  if (mode == 0) return eval_and_assemble(c, d, inst0, y, rhs_out, phys, ts, coef, true, mhd::ASM_RHS, 0);
+  mhd_status st;
+  switch (c->integrator) {
+    case MHD_RK4:
+      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_RK_STAGE, 1))) return st;
+      for (int sg = 2; sg <= 3; ++sg)
+        if ((st = eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_RK_STAGE, sg))) return st;
+      return eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_RK_FINAL, 0);
+    case MHD_PC:
+      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_PC_PRED, 0))) return st;
+      return eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_PC_CORR, 0);
+    default:
+      return eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_AB2, 0);
+  }
 }
 
 extern "C" {

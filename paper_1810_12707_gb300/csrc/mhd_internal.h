@@ -124,22 +124,30 @@ cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *p
                            TimeState *ts, StepCoef *coef, const Dims &d, double dt_fixed,
                            double cfl_adv, double cfl_visc, cudaStream_t s);
 
-// Spectral assembly of the RHS from the 12 product spectra (scaled by N^-3) and the state.
-// mode 0: write the RHS to `rhs_out`; mode 1: AB2 update of `state` and `hist` with `coef`.
-cudaError_t launch_assemble(const cplx64 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
-                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                            cudaStream_t s);
-cudaError_t launch_assemble(const cplx32 *flux, cplx64 *state, cplx64 *hist, cplx64 *rhs_out,
-                            const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                            cudaStream_t s);
+// What the assembly does with the RHS r it computes (f evaluated at the state `y_in`), with y the
+// instance's state, h its history buffer and Y the stage state:
+enum AsmOp {
+  ASM_RHS = 0,       // rhs_out = r
+  ASM_AB2 = 1,       // y += dt (a1 r + a0 h);  h = r
+  ASM_RK_STAGE = 2,  // h = r (stage 1) or h + 2 r (stages 2, 3);  Y = y + c dt r, c = 1/2, 1/2, 1
+  ASM_RK_FINAL = 3,  // y += dt/6 (h + r)
+  ASM_PC_PRED = 4,   // Y = y + dt (a1 r + a0 h);  h = r
+  ASM_PC_CORR = 5    // y += dt/2 (h + r)
+};
+
+// Spectral assembly of the RHS from the 12 product spectra (scaled by N^-3) and the state y_in,
+// followed by `op`; `stage` is the RK4 stage (1..3) for ASM_RK_STAGE.
+cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *state, cplx64 *hist, cplx64 *ystage,
+                            cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op, int stage,
+                            const Dims &d, cudaStream_t s);
 
 // Mixed precision keeps the state as double-float pairs: S_hi and S_lo ([inst][7][spec] FP32
-// complex each, hi + lo carrying a 48-bit significand) and the history in FP32.  The update
-// y <- y + dt (a1 f + a0 h) adds the FP32 increment to (hi, lo) with an error-free two-sum.
-// mode 0 writes the RHS (FP64) to `rhs_out`; mode 1 updates hi, lo and hist.
-cudaError_t launch_assemble_df(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, cplx64 *rhs_out,
-                               const PhysDev *phys, const StepCoef *coef, int mode, const Dims &d,
-                               cudaStream_t s);
+// complex each, hi + lo carrying a 48-bit significand), the history and the stage state in FP32.
+// Updates of y add the FP32 increment to (hi, lo) with an error-free two-sum; ASM_RHS writes the
+// RHS in FP64 to `rhs_out`.
+cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist,
+                               cplx32 *ystage, cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op,
+                               int stage, const Dims &d, cudaStream_t s);
 // FP64 spectra <-> (hi, lo) pairs of `count` complex values.
 cudaError_t launch_split_state(const cplx64 *in, cplx32 *hi, cplx32 *lo, size_t count, cudaStream_t s);
 cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out, size_t count, cudaStream_t s);

@@ -162,7 +162,7 @@ extern "C" MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, c
   NA_CK(mhd::launch_col_forward(W1, W2, n, 12 * n, d.nx, 1.0, tw, s));
   NA_CK(mhd::launch_col_forward(W2, W1, n, 12, d.nk * d.nx, 1.0, tw, s));
   // RHS spectra, then back to the grid
-  NA_CK(mhd::launch_assemble(W1, S, nullptr, R, pd, nullptr, 0, d, s));
+  NA_CK(mhd::launch_assemble(W1, S, S, nullptr, nullptr, R, pd, nullptr, mhd::ASM_RHS, 0, d, s));
   NA_CK(mhd::launch_col_inverse(R, W1, n, 7, d.nk * d.nx, tw, s));
   NA_CK(mhd::launch_col_inverse(W1, W2, n, 7 * n, d.nx, tw, s));
   double *real = reinterpret_cast<double *>(W1);

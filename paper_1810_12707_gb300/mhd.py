@@ -23,6 +23,7 @@ LIBRARY = os.path.join(_PKG, "libmhd_gb300.so")
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ESTATE, MHD_ENONFINITE, MHD_ETIMEOUT, MHD_EBUSY = range(8)
 MHD_FP64 = 0
 MHD_FP32_MIXED = 1
+MHD_AB2, MHD_RK4, MHD_PC = 0, 1, 2
 MHD_OPT_CUDA_GRAPH, MHD_OPT_TILE_INV_Z, MHD_OPT_TILE_INV_Y, MHD_OPT_TILE_FWD_Y, MHD_OPT_TILE_FWD_Z = range(5)
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_ESTATE",
                 5: "MHD_ENONFINITE", 6: "MHD_ETIMEOUT", 7: "MHD_EBUSY"}
@@ -47,7 +48,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 class MhdParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("batch", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("dt", ctypes.c_double), ("cfl_adv", ctypes.c_double),
+                ("integrator", ctypes.c_int32), ("dt", ctypes.c_double), ("cfl_adv", ctypes.c_double),
                 ("cfl_visc", ctypes.c_double), ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
@@ -219,7 +220,7 @@ def mhd_footprint_bytes(n: int, precision: int = MHD_FP64, batch: int = 1) -> in
 
 
 def mhd_init(n: int, phys, dt: float = 0.0, cfl_adv: float = 0.2, cfl_visc: float = 0.5,
-             precision: int = MHD_FP64, allocator: str = "torch", stream=None) -> Context:
+             precision: int = MHD_FP64, allocator: str = "torch", stream=None, integrator: int = MHD_AB2) -> Context:
     """Create a context; `phys` is a list of (nu, eta, cs), one per instance."""
     lib = load_library()
     phys = list(phys)
@@ -235,7 +236,7 @@ def mhd_init(n: int, phys, dt: float = 0.0, cfl_adv: float = 0.2, cfl_visc: floa
     if allocator == "torch":
         alloc, free = _torch_allocator()
         keep += [alloc, free]
-    p = MhdParams(int(n), len(phys), int(precision), 0, float(dt), float(cfl_adv), float(cfl_visc),
+    p = MhdParams(int(n), len(phys), int(precision), int(integrator), float(dt), float(cfl_adv), float(cfl_visc),
                   ctypes.c_void_p(stream) if stream else None,
                   alloc if alloc else ALLOC_FN(), free if free else FREE_FN(), None)
     h = ctypes.c_void_p()
@@ -389,7 +390,8 @@ def _pcheck(pool, status: int):
 
 
 def mhd_pool_create(n: int, slots: int, dt: float = 0.0, cfl_adv: float = 0.2, cfl_visc: float = 0.5,
-                    precision: int = MHD_FP32_MIXED, allocator: str = "torch", stream=None) -> Pool:
+                    precision: int = MHD_FP32_MIXED, allocator: str = "torch", stream=None,
+                    integrator: int = MHD_AB2) -> Pool:
     lib = load_library()
     keep = []
     alloc = free = None
@@ -402,7 +404,7 @@ def mhd_pool_create(n: int, slots: int, dt: float = 0.0, cfl_adv: float = 0.2, c
     if allocator == "torch":
         alloc, free = _torch_allocator()
         keep += [alloc, free]
-    p = MhdParams(int(n), int(slots), int(precision), 0, float(dt), float(cfl_adv), float(cfl_visc),
+    p = MhdParams(int(n), int(slots), int(precision), int(integrator), float(dt), float(cfl_adv), float(cfl_visc),
                   ctypes.c_void_p(stream) if stream else None,
                   alloc if alloc else ALLOC_FN(), free if free else FREE_FN(), None)
     h = ctypes.c_void_p()

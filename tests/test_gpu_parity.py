@@ -232,3 +232,23 @@ def test_instance_result_is_the_same_alone_and_in_a_batch(lib, precision):
         lib.mhd_step(alone, 15)
         for g, e in zip(lib.mhd_get_state(mix, i), lib.mhd_get_state(alone, 0)):
             assert np.array_equal(g, e)
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rk4_and_predictor_corrector_match_oracle(lib, oracle_mod, integrator, precision):
+    """The paper's other two time solvers, through the same kernels: FP64 to 1e-10, the mixed mode
+    to 1e-5 (relative L2 per field after 30 CFL steps)."""
+    ic = random_state(32, 40 + integrator)
+    ctx = lib.mhd_init(32, [(ic.nu, ic.eta, ic.cs)], integrator=integrator, precision=precision)
+    lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+    lib.mhd_step(ctx, 30)
+    assert lib.mhd_synchronize(ctx) == lib.MHD_OK
+    o = oracle_mod.Oracle(32, ic.nu, ic.eta, ic.cs, integrator=integrator)
+    o.set_state(ic.rho, ic.u, ic.b)
+    o.step(30)
+    tol = 1e-10 if precision == 0 else 1e-5
+    for g, e in zip(lib.mhd_get_state(ctx, 0), o.get_state()):
+        assert rel_l2(g, e) <= tol
+    dg, do = lib.mhd_diagnostics(ctx, 0), o.diagnostics()
+    assert dg["step"] == 30 and abs(dg["t"] - do["t"]) <= (1e-12 if precision == 0 else 1e-6) * do["t"]
