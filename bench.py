@@ -167,6 +167,16 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest value of `x` over all ranks (the slowest rank's time); `x` itself alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_oracle(cfg, steps: int, budget_s: float = 30.0):
     """Time the CPU oracle on the same workload: `steps` AB2 steps of the first instance after one
     untimed set_state.  Returns grid-point-steps/s."""
@@ -272,12 +282,8 @@ def run_ours(args, name, cfg):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     st = mhd.mhd_synchronize(ctx)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     pts = batch * n ** 3
     value = world * pts * K / (ms / 1e3)
     diag = mhd.mhd_diagnostics(ctx, 0)
@@ -313,11 +319,7 @@ def run_ours(args, name, cfg):
     t0 = time.perf_counter()
     for _ in range(E):
         e2e_step()
-    te = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": world * pts * E / te, "unit": UNIT, "h2d_bytes_per_step": 7 * pts * 8,
            "d2h_bytes_per_step": 7 * pts * 8, "steps": E}
     mhd.mhd_destroy(ectx)
