@@ -182,13 +182,18 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *                          Profiling (mhd_profile) always uses direct launches.
  *   MHD_OPT_TILE_INV_Z ... MHD_OPT_TILE_FWD_Z: columns per block of the four column FFT passes
  *                          (inverse z, inverse y, forward y, forward z); 0 (default) = chosen by
- *                          the library; otherwise 1..64 (an autotuner sets these). */
+ *                          the library; otherwise 1..64 (an autotuner sets these).
+ *   MHD_OPT_FLUX_PIPELINE  1: the fused x pass of the mixed mode at N >= 128 runs as a persistent
+ *                          kernel that prefetches the next rows with bulk copies (TMA); 0
+ *                          (default): one block per row pair, which measured faster on GB300.
+ *                          Results are identical. */
 enum {
   MHD_OPT_CUDA_GRAPH = 0,
   MHD_OPT_TILE_INV_Z = 1,
   MHD_OPT_TILE_INV_Y = 2,
   MHD_OPT_TILE_FWD_Y = 3,
-  MHD_OPT_TILE_FWD_Z = 4
+  MHD_OPT_TILE_FWD_Z = 4,
+  MHD_OPT_FLUX_PIPELINE = 5
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
 

@@ -95,6 +95,27 @@ __device__ __forceinline__ void dft_small(C *v) {
   else dft2<DIR>(v);
 }
 
+// Twiddle load that the compiler may not hoist out of loops: kernels that transform many pencils
+// in a loop would otherwise keep every stage's twiddles live in registers across the loop.
+__device__ __forceinline__ cplx64 tw_load(const cplx64 *p) {
+  cplx64 v;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.re), "=d"(v.im) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ cplx32 tw_load(const cplx32 *p) {
+  cplx32 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.re), "=f"(v.im) : "l"(p));
+  return v;
+}
+
+// The value of x, opaque to the optimiser: index arithmetic derived from it cannot be hoisted out
+// of a persistent loop and kept live (in registers or spilled) across iterations.
+__device__ __forceinline__ int launder(int x) {
+  int y;
+  asm volatile("mov.b32 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+
 // ---- shared-memory pencil layout ----
 // A pencil element e lives at sm_idx<C>(e) = e + e / (128 / sizeof(C)): one pad element per 128
 // bytes.  The first Stockham stage writes with a stride of 8 elements; without the pad every lane
@@ -104,6 +125,29 @@ template <typename C>
 __host__ __device__ constexpr int sm_idx(int e) { return e + e / (int)(128 / sizeof(C)); }
 template <typename C>
 __host__ __device__ constexpr int pencil_pitch(int n) { return sm_idx<C>(n) | 1; }
+
+// ---- barrier of one pencil's thread group ----
+// A pencil is transformed by the TPP = N/8 consecutive threads of its group and nobody else
+// touches it meanwhile, so the stages only need that group to synchronise: within a warp
+// (TPP <= 32) a warp barrier over the lanes that exist, otherwise a named barrier per group
+// (ids 1..15; id 0 is __syncthreads), falling back to the block barrier when there are more groups.
+__device__ __forceinline__ unsigned existing_lanes() {
+  const int left = (int)blockDim.x - (int)(threadIdx.x & ~31u);
+  return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
+template <int TPP>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (TPP <= 32) {
+    __syncwarp(existing_lanes());
+  } else {
+    if (blockDim.x / TPP <= 15) {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / TPP)), "r"(TPP) : "memory");
+    } else {
+      __syncthreads();
+    }
+  }
+}
 
 // ---- Stockham pencil FFT ----
 //
@@ -116,8 +160,9 @@ __host__ __device__ constexpr int pencil_pitch(int n) { return sm_idx<C>(n) | 1;
 // group owns 8 / R butterflies per stage, so it always holds 8 values.  `tw[m]` = W_N^m =
 // exp(-2 pi i m / N); the inverse uses its conjugate.
 //
-// Every thread of the block must call this (it contains __syncthreads); threads with
-// `active == false` only take part in the barriers.
+// Every thread of the block must call this (it contains group barriers); threads with
+// `active == false` only take part in the barriers.  The caller separates the transform from the
+// preceding writes and the following reads of the pencil with a block barrier.
 template <int N, int DIR, int NS, typename C>
 __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
@@ -135,14 +180,14 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         for (int r = 0; r < R; ++r) {
           C x = buf[sm_idx<C>(j + r * (N / R))];
           if (NS > 1 && r > 0) {
-            const C w = tw[r * k * TWSTEP];
+            const C w = tw_load(tw + r * k * TWSTEP);
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
           }
           v[b * R + r] = x;
         }
       }
     }
-    __syncthreads();
+    group_sync<TPP>();
     if (active) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -154,7 +199,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         for (int r = 0; r < R; ++r) buf[sm_idx<C>(base + r * NS)] = v[b * R + r];
       }
     }
-    __syncthreads();
+    group_sync<TPP>();
     stockham_stages<N, DIR, NS * R, C>(buf, t, active, tw);
   }
 }

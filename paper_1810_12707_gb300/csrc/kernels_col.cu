@@ -53,6 +53,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   const int t = threadIdx.x - pencil * TPP;
   const bool active = pencil < tc && c0 + pencil < cols;
   pencil_fft<N, DIR, CC>(sm + (active ? pencil : 0) * P, t, active, tw);
+  __syncthreads();  // the store loop reads every pencil
 
   CO *dst = out + slab * (size_t)lout * cols;
   for (int q = threadIdx.x; q < lout * tc; q += nthr) {

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "fft_device.cuh"
+#include "tma_util.cuh"
 
 namespace mhd {
 
@@ -242,18 +243,15 @@ __global__ void combine_state_kernel(const cplx32 *__restrict__ hi, const cplx32
   }
 }
 
-// One block per instance: maximum of the CFL partials, the step size, the Adams-Bashforth
+// One thread per instance: the CFL maximum of the flux pass, the step size, the Adams-Bashforth
 // coefficients of this step, and the advance of the time state.
-__global__ void step_dt_kernel(const double *__restrict__ part, int nparts,
-                               const PhysDev *__restrict__ phys, TimeState *__restrict__ ts,
-                               StepCoef *__restrict__ coef, int n, int K, double dt_fixed,
-                               double cfl_adv, double cfl_visc) {
-  __shared__ double red[32];
-  const int inst = blockIdx.x;
-  double m = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) m = nan_max(m, part[(size_t)inst * nparts + i]);
-  m = block_nan_max(m, red);
-  if (threadIdx.x != 0) return;
+__global__ void step_dt_kernel(unsigned long long *__restrict__ smax_bits, const PhysDev *__restrict__ phys,
+                               TimeState *__restrict__ ts, StepCoef *__restrict__ coef, int batch, int n, int K,
+                               double dt_fixed, double cfl_adv, double cfl_visc) {
+  const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+  if (inst >= batch) return;
+  const double m = __longlong_as_double((long long)smax_bits[inst]);
+  smax_bits[inst] = 0ull;
   TimeState s = ts[inst];
   StepCoef c = {0.0, 0.0, 0.0, 0.f, 0.f, 0.f, 1};
   if (s.status == 0 && (s.step_limit == 0 || s.step < s.step_limit)) {
@@ -407,11 +405,10 @@ cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys, TimeState *ts,
-                           StepCoef *coef, const Dims &d, double dt_fixed, double cfl_adv,
-                           double cfl_visc, cudaStream_t s) {
-  step_dt_kernel<<<d.batch, 256, 0, s>>>(smax_part, nparts, phys, ts, coef, d.n, d.k, dt_fixed, cfl_adv,
-                                         cfl_visc);
+cudaError_t launch_step_dt(unsigned long long *smax_bits, const PhysDev *phys, TimeState *ts, StepCoef *coef,
+                           const Dims &d, double dt_fixed, double cfl_adv, double cfl_visc, cudaStream_t s) {
+  step_dt_kernel<<<(d.batch + 127) / 128, 128, 0, s>>>(smax_bits, phys, ts, coef, d.batch, d.n, d.k, dt_fixed, cfl_adv,
+                                                       cfl_visc);
   return cudaGetLastError();
 }
 

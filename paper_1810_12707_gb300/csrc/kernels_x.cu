@@ -14,6 +14,7 @@
 // spectra.  Rows are indexed r = z*N + y; a block owns PAIRS consecutive row pairs.
 #include "fft_device.cuh"
 #include "launch_util.cuh"
+#include "tma_util.cuh"
 
 namespace mhd {
 
@@ -33,7 +34,8 @@ constexpr int threads_for(int n, int pencils) {
 }
 
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
-// N/8 threads of the block taking one pencil at a time.
+// N/8 threads of the block taking one pencil at a time.  Each pencil is touched by its group only,
+// so the stages synchronise per group; one block barrier closes the whole transform.
 template <int N, int DIR, typename Ptr, typename C>
 __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
   constexpr int TPP = N / 8;
@@ -44,6 +46,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
     const bool active = g < G && id < np;
     pencil_fft<N, DIR, C>(ptr(active ? id : 0), t, active, tw);
   }
+  __syncthreads();  // the callers' next phase reads every pencil
 }
 
 }  // namespace
@@ -55,7 +58,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // combined in FP64.
 template <int N, typename C>
 __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
-                              const PhysDev *__restrict__ phys, double *__restrict__ smax_part,
+                              const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
                               int K, int blocks_per_inst, const C *__restrict__ tw) {
   using R = typename C::value_type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,7 +158,161 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
   }
 
   const double m = block_nan_max((double)smax, red);
-  if (threadIdx.x == 0) smax_part[(size_t)inst * blocks_per_inst + bl] = m;
+  if (threadIdx.x == 0) atomicMax(smax_bits + inst, max_bits(m));
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused flux pass, persistent and pipelined (one row pair per iteration, N >= 128, FP32)
+// ------------------------------------------------------------------------------------------
+// Each block walks over row pairs (pair = blockIdx.x, + gridDim.x, ...).  The 7 state rows of
+// the next pair (one contiguous chunk of 2 * NX complex values per field) are fetched with bulk
+// asynchronous copies into the other of two staging buffers while the current pair is
+// transformed, so the copy engine keeps HBM busy during the FFT work.  The arithmetic, its order
+// and the results are those of flux_x_kernel.  A barrier wait that does not complete within its
+// poll limit sets *err and ends the block (after one more bounded wait for its own copies).
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+template <int N, typename C>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    flux_x_pipe_kernel(const C *__restrict__ in, C *__restrict__ out, const PhysDev *__restrict__ phys,
+                       unsigned long long *__restrict__ smax_bits, int K, long long total_pairs,
+                       const C *__restrict__ tw, int *err) {
+  using R = typename C::value_type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  constexpr int P = pencil_pitch<C>(N);
+  constexpr long long PPI = (long long)N * N / 2;  // row pairs per instance
+  constexpr size_t NN = (size_t)N * N;
+  const int NX = K + 1;
+  const int chunk = 2 * NX;  // complex values of one field's row pair
+  const uint32_t chunk_bytes = (uint32_t)(chunk * sizeof(C));
+  C *stage = reinterpret_cast<C *>(smem_raw);
+  C *sm = stage + ((2 * 7 * chunk * sizeof(C) + 127) / 128 * 128) / sizeof(C);
+  const int nthr = blockDim.x;
+
+  auto issue = [&](long long pr, int b) {
+    const int inst = (int)(pr / PPI);
+    const size_t row0 = (size_t)(pr - (long long)inst * PPI) * 2;
+    mbar_arrive_expect_tx(&mbar[b], 7 * chunk_bytes);
+    for (int f = 0; f < 7; ++f)
+      bulk_g2s(stage + (size_t)(b * 7 + f) * chunk, in + ((size_t)(inst * 7 + f) * NN + row0) * NX, chunk_bytes,
+               &mbar[b]);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  long long pair = blockIdx.x;
+  if (threadIdx.x == 0 && pair < total_pairs) issue(pair, 0);
+  int issued_next = 0;
+  for (int iter = 0; pair < total_pairs; pair += gridDim.x, ++iter) {
+    const int buf = iter & 1;
+    const long long nxt = pair + gridDim.x;
+    if (threadIdx.x == 0) {
+      issued_next = nxt < total_pairs;
+      if (issued_next) {
+        fence_proxy_async();
+        issue(nxt, buf ^ 1);
+      }
+    }
+    const bool ok = mbar_wait(&mbar[buf], (iter >> 1) & 1, kMaxPolls);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        if (issued_next) mbar_wait(&mbar[buf ^ 1], ((iter + 1) >> 1) & 1, kMaxPolls);
+      }
+      return;
+    }
+    const int inst = (int)(pair / PPI);
+    const size_t row0 = (size_t)(pair - (long long)inst * PPI) * 2;
+    const int tx = launder(threadIdx.x);
+
+    // 1. pack the 7 fields of this row pair from the staging buffer
+    const C *st = stage + (size_t)buf * 7 * chunk;
+    for (int q = tx; q < 7 * NX; q += nthr) {
+      const int k = q % NX, f = q / NX;
+      const C x0 = st[f * chunk + k], x1 = st[f * chunk + NX + k];
+      C *pen = sm + f * P;
+      if (k == 0) {
+        pen[0] = C{x0.re, x1.re};
+      } else {
+        pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
+        pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
+      }
+    }
+    for (int q = tx; q < 7 * (N - 2 * K - 1); q += nthr) {
+      const int z = q % (N - 2 * K - 1), f = q / (N - 2 * K - 1);
+      sm[f * P + sm_idx<C>(K + 1 + z)] = C{0, 0};
+    }
+    __syncthreads();
+
+    // 2. inverse transforms of the 7 fields
+    fft_pencils<N, +1>(7, [&](int id) { return sm + id * P; }, tw);
+
+    // 3. products on the grid
+    const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
+    R smax = 0;
+    for (int j = tx; j < N; j += nthr) {
+      C *b = sm + sm_idx<C>(j);
+      R v[2][7];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        const C c = b[f * P];
+        v[0][f] = c.re;
+        v[1][f] = c.im;
+      }
+      R *bd = reinterpret_cast<R *>(b);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const R rho = v[h][0];
+        const R mx = v[h][1], my = v[h][2], mz = v[h][3];
+        const R bx = v[h][4], by = v[h][5], bz = v[h][6];
+        const R ir = (R)1 / rho;
+        const R ux = mx * ir, uy = my * ir, uz = mz * ir;
+        const R b2 = bx * bx + by * by + bz * bz;
+        const R hb = (R)0.5 * b2;
+        bd[2 * 0 * P + h] = mx * ux + hb - bx * bx;
+        bd[2 * 1 * P + h] = my * uy + hb - by * by;
+        bd[2 * 2 * P + h] = mz * uz + hb - bz * bz;
+        bd[2 * 3 * P + h] = mx * uy - bx * by;
+        bd[2 * 4 * P + h] = mx * uz - bx * bz;
+        bd[2 * 5 * P + h] = my * uz - by * bz;
+        bd[2 * 6 * P + h] = uy * bz - uz * by;
+        bd[2 * 7 * P + h] = uz * bx - ux * bz;
+        bd[2 * 8 * P + h] = ux * by - uy * bx;
+        bd[2 * 9 * P + h] = ux;
+        bd[2 * 10 * P + h] = uy;
+        bd[2 * 11 * P + h] = uz;
+        const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 * ir);
+        smax = (s != s || s > smax) ? s : smax;
+      }
+    }
+    __syncthreads();
+
+    // 4. forward transforms of the 12 products
+    fft_pencils<N, -1>(12, [&](int id) { return sm + id * P; }, tw);
+
+    // 5. unpack and store
+    const R half = (R)0.5;
+    for (int q = tx; q < 12 * NX; q += nthr) {
+      const int k = q % NX, f = q / NX;
+      const C *pen = sm + f * P;
+      const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
+      C *dst = out + ((size_t)(inst * 12 + f) * NN + row0) * NX;
+      dst[k] = C{half * (z.re + zc.re), half * (z.im - zc.im)};
+      dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
+    }
+
+    // CFL maximum of this pair: warp maximum, one atomic per warp
+    double m = (double)smax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = nan_max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(smax_bits + inst, max_bits(m));
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -331,9 +488,29 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
 namespace {
 
 template <int N, typename C>
-cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, double *part, const Dims &d, const C *tw,
-                   cudaStream_t s) {
+cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
+                   cudaStream_t s, int *err) {
   constexpr int PAIRS = pairs_for(N);
+  if constexpr (PAIRS == 1 && sizeof(C) == 8) {
+    const int chunk = 2 * (d.k + 1);
+    const size_t stage_bytes = (2 * 7 * chunk * sizeof(C) + 127) / 128 * 128;
+    const size_t smem = stage_bytes + (size_t)12 * pencil_pitch<C>(N) * sizeof(C);
+    if (err != nullptr && smem <= 200 * 1024) {
+      cudaError_t e = ensure_smem<flux_x_pipe_kernel<N, C>>((int)smem);
+      if (e != cudaSuccess) return e;
+      const int threads = threads_for(N, 12);
+      int per_sm = 0, dev = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flux_x_pipe_kernel<N, C>, threads, smem);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      const long long total = (long long)d.batch * N * N / 2;
+      long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+      if (blocks > total) blocks = total;
+      flux_x_pipe_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, total, tw, err);
+      return cudaGetLastError();
+    }
+  }
   const int bpi = N * N / (2 * PAIRS);
   const int threads = threads_for(N, 12 * PAIRS);
   const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
@@ -407,14 +584,14 @@ cudaError_t diag_n(const cplx64 *in, const PhysDev *phys, double *part, const Di
 int flux_x_blocks_per_instance(int n) { return n * n / (2 * pairs_for(n)); }
 int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
 
-cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
-                          const Dims &d, const cplx64 *tw, cudaStream_t s) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_part, d, tw, s)));
+cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
+                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err)));
 }
 
-cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, double *smax_part,
-                          const Dims &d, const cplx32 *tw, cudaStream_t s) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_part, d, tw, s)));
+cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
+                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err)));
 }
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,

@@ -44,6 +44,10 @@ struct mhd_ctx {
   size_t w1_len = 0, w2_len = 0;  // bytes / 16
   double *part = nullptr;
   size_t part_len = 0;
+  // CFL maxima as bits for atomic maxima: [0, batch) feed the step size, [batch, 2 batch) take the
+  // maxima of evaluations whose step size is not needed (RK stages, mhd_rhs)
+  unsigned long long *smax_bits = nullptr;
+  int *d_err = nullptr;  // set by a device-side wait that gave up
   mhd::TimeState *ts = nullptr;
   mhd::StepCoef *coef = nullptr;
   double *diag_out = nullptr;
@@ -52,6 +56,7 @@ struct mhd_ctx {
   std::string err;
   // options and the captured step
   bool use_graph = true;
+  bool flux_pipeline = false;
   int tile[4] = {0, 0, 0, 0};
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -332,6 +337,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (c->integrator != MHD_AB2)
     ok = ok && (c->Y = dalloc(c, s.S * (c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32)))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
+  ok = ok && (c->smax_bits = (unsigned long long *)dalloc(c, 2 * p->batch * sizeof(unsigned long long))) != nullptr;
+  ok = ok && (c->d_err = (int *)dalloc(c, 4 * sizeof(int))) != nullptr;
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
   ok = ok && (c->phys = (mhd::PhysDev *)dalloc(c, p->batch * sizeof(mhd::PhysDev))) != nullptr;
@@ -353,6 +360,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->smax_bits, 0, 2 * p->batch * sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_all(c);
@@ -393,6 +402,7 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
     CK(cudaMemsetAsync(hist32(c, inst), 0, 7 * d.spec * sizeof(cplx32), c->stream));
   }
   CK(cudaMemsetAsync(c->ts + inst, 0, sizeof(mhd::TimeState), c->stream));
+  CK(cudaMemsetAsync(c->smax_bits + inst, 0, sizeof(unsigned long long), c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->is_set[inst] = 1;
   return MHD_OK;
@@ -459,7 +469,7 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 // CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.  `advance`
 // runs the step-size kernel after the flux pass.
 template <typename CF, typename CS>
-static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, const mhd::PhysDev *phys,
+static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, const CS *S, const mhd::PhysDev *phys,
                                  mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
@@ -467,10 +477,10 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, const CS *S, co
   CF *w2 = reinterpret_cast<CF *>(c->W2);
   LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0]));
   LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1]));
-  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, c->part, d, tw, c->stream));
+  unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
+  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr));
   if (advance) {
-    LAUNCH(3, mhd::launch_step_dt(c->part, mhd::flux_x_blocks_per_instance(d.n), phys, ts, coef, d, c->dt_fixed,
-                                  c->cfl_adv, c->cfl_visc, c->stream));
+    LAUNCH(3, mhd::launch_step_dt(bits, phys, ts, coef, d, c->dt_fixed, c->cfl_adv, c->cfl_visc, c->stream));
   }
   LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2]));
   LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3]));
@@ -487,13 +497,13 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
   const size_t off = (size_t)inst0 * 7 * d.spec;
   if (c->precision == MHD_FP64) {
     const cplx64 *yi = static_cast<const cplx64 *>(y_in);
-    if ((st = flux_spectra_t<cplx64>(c, d, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw))) return st;
+    if ((st = flux_spectra_t<cplx64>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw))) return st;
     cplx64 *Y = c->Y ? static_cast<cplx64 *>(c->Y) + off : nullptr;
     LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
                                    c->stream));
   } else {
     const cplx32 *yi = static_cast<const cplx32 *>(y_in);
-    if ((st = flux_spectra_t<cplx32>(c, d, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32))) return st;
+    if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32))) return st;
     cplx32 *Y = c->Y ? static_cast<cplx32 *>(c->Y) + off : nullptr;
     LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), yi, state_hi(c, inst0),
                                       state_lo(c, inst0), hist32(c, inst0), Y, rhs_out, phys, coef, op, stage, d,
@@ -651,6 +661,9 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   if (option == MHD_OPT_CUDA_GRAPH) {
     if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "graph option must be 0 or 1");
     c->use_graph = value != 0;
+  } else if (option == MHD_OPT_FLUX_PIPELINE) {
+    if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "pipeline option must be 0 or 1");
+    c->flux_pipeline = value != 0;
   } else if (option >= MHD_OPT_TILE_INV_Z && option <= MHD_OPT_TILE_FWD_Z) {
     if (value < 0 || value > 64) return fail(c, MHD_EINVAL, "tile must be 0..64");
     c->tile[option - MHD_OPT_TILE_INV_Z] = (int)value;
@@ -665,10 +678,12 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
 mhd_status mhd_synchronize(mhd_ctx *c) {
   if (!c) return MHD_EINVAL;
   DeviceGuard g(c->device);
-  int32_t any = 0;
+  int32_t any = 0, err = 0;
   CK(mhd::launch_status_any(c->ts, c->d.batch, c->flag, c->stream));
   CK(cudaMemcpyAsync(&any, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (err) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up");
   return any ? MHD_ENONFINITE : MHD_OK;
 }
 

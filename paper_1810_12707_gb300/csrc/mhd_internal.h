@@ -96,12 +96,14 @@ cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, 
                                double scale, const cplx32 *tw, cudaStream_t s, int tile = 0);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
-// grid, forward real transforms of the 12 product fields (kx <= K kept), and per-block maxima of
-// |u| + c_f into `smax_part` ([batch][x_blocks(n)]).
-cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, double *smax_part,
-                          const Dims &d, const cplx64 *tw, cudaStream_t s);
-cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, double *smax_part,
-                          const Dims &d, const cplx32 *tw, cudaStream_t s);
+// grid, forward real transforms of the 12 product fields (kx <= K kept), and the maximum of
+// |u| + c_f per instance, accumulated as an atomic maximum on the bits into smax_bits[batch]
+// (which must start at 0).  With `err` non-null, FP32 and N >= 128 the persistent, bulk-copy
+// pipelined variant runs; a bounded wait that gives up sets *err = 1.
+cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
+                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err = nullptr);
+cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
+                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
@@ -118,11 +120,10 @@ cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, c
                           const cplx64 *tw, cudaStream_t s);
 int diag_x_blocks(int n);
 
-// dt of every instance from the CFL partials (or the fixed dt), the AB2 coefficients of this
-// step, and the advance of the per-instance time state.
-cudaError_t launch_step_dt(const double *smax_part, int nparts, const PhysDev *phys,
-                           TimeState *ts, StepCoef *coef, const Dims &d, double dt_fixed,
-                           double cfl_adv, double cfl_visc, cudaStream_t s);
+// dt of every instance from its CFL maximum (or the fixed dt), the AB2 coefficients of this
+// step, and the advance of the per-instance time state; resets smax_bits to 0 for the next pass.
+cudaError_t launch_step_dt(unsigned long long *smax_bits, const PhysDev *phys, TimeState *ts, StepCoef *coef,
+                           const Dims &d, double dt_fixed, double cfl_adv, double cfl_visc, cudaStream_t s);
 
 // What the assembly does with the RHS r it computes (f evaluated at the state `y_in`), with y the
 // instance's state, h its history buffer and Y the stage state:

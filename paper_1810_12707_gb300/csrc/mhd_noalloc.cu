@@ -158,7 +158,8 @@ extern "C" MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, c
   // products on the grid and their truncated spectra
   NA_CK(mhd::launch_col_inverse(S, W1, n, 7, d.nk * d.nx, tw, s));
   NA_CK(mhd::launch_col_inverse(W1, W2, n, 7 * n, d.nx, tw, s));
-  NA_CK(mhd::launch_flux_x(W2, W1, pd, part, d, tw, s));
+  // the CFL maximum is not needed here; the partials region takes the atomic maxima
+  NA_CK(mhd::launch_flux_x(W2, W1, pd, reinterpret_cast<unsigned long long *>(part), d, tw, s));
   NA_CK(mhd::launch_col_forward(W1, W2, n, 12 * n, d.nx, 1.0, tw, s));
   NA_CK(mhd::launch_col_forward(W2, W1, n, 12, d.nk * d.nx, 1.0, tw, s));
   // RHS spectra, then back to the grid

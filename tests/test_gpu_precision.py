@@ -121,3 +121,22 @@ def test_plain_cufft_baseline_matches_oracle(lib, oracle_mod):
     assert rel_l2(got[0], r) <= 1e-10
     assert rel_l2(np.stack(got[1:4]), m) <= 1e-10
     assert rel_l2(np.stack(got[4:7]), b) <= 1e-10
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_pipelined_flux_pass_equals_block_per_row_pair(lib, n):
+    """The persistent bulk-copy pipelined flux kernel (mixed mode, N >= 128) computes exactly what
+    the one-block-per-row-pair kernel computes."""
+    ic = inputs.abc_dynamo(n, seed=3, b_energy=1e-2)
+    out = []
+    for pipe in (0, 1):
+        ctx = lib.mhd_init(n, [(ic.nu, ic.eta, ic.cs)], precision=lib.MHD_FP32_MIXED)
+        lib.mhd_set_option(ctx, lib.MHD_OPT_FLUX_PIPELINE, pipe)
+        lib.mhd_set_state(ctx, 0, ic.rho, ic.u, ic.b)
+        lib.mhd_step(ctx, 4)
+        assert lib.mhd_synchronize(ctx) == lib.MHD_OK
+        out.append((lib.mhd_get_state(ctx, 0), lib.mhd_diagnostics(ctx, 0)["dt"]))
+        lib.mhd_destroy(ctx)
+    for g, e in zip(out[0][0], out[1][0]):
+        assert np.array_equal(g, e)
+    assert out[0][1] == out[1][1]
