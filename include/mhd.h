@@ -162,6 +162,11 @@ MHD_API mhd_status mhd_get_spectrum(mhd_ctx *ctx, int32_t inst, int32_t field, d
  * MHD_ENONFINITE in its diagnostics and from mhd_synchronize. */
 MHD_API mhd_status mhd_step(mhd_ctx *ctx, int32_t nsteps);
 
+/* ABC body force rho f on instance `inst` (paper, section "for magnetohydrodynamic flow"):
+ * f = amp (A sin kf z + C cos kf y, B sin kf x + A cos kf z, C sin kf y + B cos kf x), added to the
+ * momentum equation.  amp = 0 switches it off (the default).  1 <= kf <= k_max.  Synchronises. */
+MHD_API mhd_status mhd_set_forcing(mhd_ctx *ctx, int32_t inst, double amp, double A, double B, double C, int32_t kf);
+
 /* Wait for queued work; MHD_ENONFINITE if any instance stopped advancing. */
 MHD_API mhd_status mhd_synchronize(mhd_ctx *ctx);
 

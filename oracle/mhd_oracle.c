@@ -215,6 +215,11 @@ typedef struct {
   double dt_fixed;      /* > 0: fixed step; <= 0: CFL step */
   double cfl_adv, cfl_visc;
   int integrator;       /* 0 Adams-Bashforth 2, 1 Runge-Kutta 4, 2 predictor-corrector */
+  /* ABC body force rho f (paper, section "for magnetohydrodynamic flow"): f = famp *
+   * (A sin(kf z) + C cos(kf y), B sin(kf x) + A cos(kf z), C sin(kf y) + B cos(kf x));
+   * off when famp == 0 */
+  double famp, fa, fb, fc;
+  int fkf;
 } or_params;
 
 typedef struct {
@@ -226,6 +231,7 @@ typedef struct {
   cplx *ystage[NSTATE]; /* intermediate states of the multi-stage methods */
   cplx *kacc[NSTATE];   /* RK4 weighted sum of the stage derivatives */
   cplx *flux[NFLUX];
+  cplx *force[3];       /* spectra of rho f */
   double *real[NSTATE];
   double *rflux[NFLUX];
   cplx *tmp;
@@ -247,6 +253,7 @@ static void ctx_free(or_ctx *c) {
     free(c->flux[f]);
     free(c->rflux[f]);
   }
+  for (int d = 0; d < 3; ++d) free(c->force[d]);
   free(c->tmp);
   free(c);
 }
@@ -270,6 +277,7 @@ or_ctx *or_create(const or_params *p) {
     ok &= (c->flux[f] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
     ok &= (c->rflux[f] = (double *)calloc(c->n3, sizeof(double))) != NULL;
   }
+  for (int d = 0; d < 3; ++d) ok &= (c->force[d] = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
   ok &= (c->tmp = (cplx *)calloc(c->n3, sizeof(cplx))) != NULL;
   if (!ok) {
     ctx_free(c);
@@ -405,6 +413,25 @@ static int compute_rhs_of(or_ctx *c, cplx *const *y, cplx *const *out, double *s
   /* 3. */
   for (int f = 0; f < NFLUX; ++f) or_forward(c->rflux[f], c->flux[f], n);
 
+  /* body force: rho f on the grid, transformed (reuses the first three flux grids) */
+  const int forced = c->p.famp != 0.0;
+  if (forced) {
+    const double kf = (double)c->p.fkf, A = c->p.fa, B = c->p.fb, C = c->p.fc, F = c->p.famp;
+    for (int z = 0; z < n; ++z) {
+      for (int y = 0; y < n; ++y) {
+        for (int x = 0; x < n; ++x) {
+          const size_t i = ((size_t)z * n + y) * n + x;
+          const double X = 2.0 * M_PI * x / n, Y = 2.0 * M_PI * y / n, Z = 2.0 * M_PI * z / n;
+          const double rho = c->real[F_RHO][i];
+          c->rflux[0][i] = rho * F * (A * sin(kf * Z) + C * cos(kf * Y));
+          c->rflux[1][i] = rho * F * (B * sin(kf * X) + A * cos(kf * Z));
+          c->rflux[2][i] = rho * F * (C * sin(kf * Y) + B * cos(kf * X));
+        }
+      }
+    }
+    for (int d = 0; d < 3; ++d) or_forward(c->rflux[d], c->force[d], n);
+  }
+
   /* 4. and 5. */
   const double nu = c->p.nu, eta = c->p.eta;
   cplx *const *yv = y;
@@ -434,7 +461,7 @@ static int compute_rhs_of(or_ctx *c, cplx *const *y, cplx *const *out, double *s
         /* momentum */
         for (int a = 0; a < 3; ++a) {
           cplx divT = k[0] * T[a][0] + k[1] * T[a][1] + k[2] * T[a][2];
-          out[F_MX + a][i] = -I * divT - I * k[a] * cs2 * rho - nu * k2 * uh[a];
+          out[F_MX + a][i] = -I * divT - I * k[a] * cs2 * rho - nu * k2 * uh[a] + (forced ? c->force[a][i] : 0.0);
         }
         /* induction: curl E with E = u x B */
         const cplx curlE[3] = {I * (k[1] * Eh[2] - k[2] * Eh[1]), I * (k[2] * Eh[0] - k[0] * Eh[2]),

@@ -43,7 +43,9 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("eta", ctypes.c_double),
                 ("cs", ctypes.c_double), ("dt_fixed", ctypes.c_double),
-                ("cfl_adv", ctypes.c_double), ("cfl_visc", ctypes.c_double), ("integrator", ctypes.c_int)]
+                ("cfl_adv", ctypes.c_double), ("cfl_visc", ctypes.c_double), ("integrator", ctypes.c_int),
+                ("famp", ctypes.c_double), ("fa", ctypes.c_double), ("fb", ctypes.c_double), ("fc", ctypes.c_double),
+                ("fkf", ctypes.c_int)]
 
 
 def _declare(lib):
@@ -152,11 +154,15 @@ class Oracle:
     AB2, RK4, PC = 0, 1, 2
 
     def __init__(self, n: int, nu: float, eta: float, cs: float, dt: float = 0.0,
-                 cfl_adv: float = 0.2, cfl_visc: float = 0.5, lib=None, integrator: int = 0):
+                 cfl_adv: float = 0.2, cfl_visc: float = 0.5, lib=None, integrator: int = 0,
+                 forcing=None):
+        """`forcing` = (amplitude, A, B, C, k_f) of the ABC body force, or None."""
         lib = lib if lib is not None else _load()
         self.n = int(n)
+        famp, fa, fb, fc, fkf = forcing if forcing is not None else (0.0, 0.0, 0.0, 0.0, 1)
         self.params = _Params(self.n, float(nu), float(eta), float(cs), float(dt),
-                              float(cfl_adv), float(cfl_visc), int(integrator))
+                              float(cfl_adv), float(cfl_visc), int(integrator),
+                              float(famp), float(fa), float(fb), float(fc), int(fkf))
         self._h = lib.or_create(ctypes.byref(self.params))
         if not self._h:
             raise ValueError(f"oracle: cannot create instance (n={n} must be a power of two >= 4)")

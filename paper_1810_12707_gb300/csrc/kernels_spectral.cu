@@ -15,13 +15,53 @@
 
 namespace mhd {
 
+// rho_hat at wavevector (kx, ky, kz) of one instance's truncated density spectrum (zero outside
+// the kept set; kx < 0 through Hermitian symmetry).
+template <typename CT>
+__device__ __forceinline__ CT rho_at(const CT *rho, int kx, int ky, int kz, int K) {
+  if (kx < -K || kx > K || ky < -K || ky > K || kz < -K || kz > K) return CT{0, 0};
+  const int NX = K + 1, NK = 2 * K + 1;
+  const bool cj = kx < 0;
+  if (cj) {
+    kx = -kx;
+    ky = -ky;
+    kz = -kz;
+  }
+  const CT v = rho[((size_t)(kz >= 0 ? kz : kz + NK) * NK + (ky >= 0 ? ky : ky + NK)) * NX + kx];
+  return cj ? CT{v.re, -v.im} : v;
+}
+
+// Spectrum of rho f_ABC at (kx, ky, kz): the product with sin(kf s) and cos(kf s) shifts the
+// density spectrum by +-kf along s, (rho sin)^(k) = [rho(k - kf s) - rho(k + kf s)] / 2i and
+// (rho cos)^(k) = [rho(k - kf s) + rho(k + kf s)] / 2.  The product is band-limited (no aliasing),
+// so this equals the transform of the product on the grid.
+template <typename CT>
+__device__ __forceinline__ void abc_force(const CT *rho, int kx, int ky, int kz, int K, const PhysDev &ph, CT f[3]) {
+  using R = typename CT::value_type;
+  const int q = ph.fkf;
+  const R a = (R)ph.fa, b = (R)ph.fb, c = (R)ph.fc, amp = (R)ph.famp, h = (R)0.5;
+  CT S[3], Co[3];  // (rho sin(q s)), (rho cos(q s)) for s = x, y, z
+  const int d[3][3] = {{q, 0, 0}, {0, q, 0}, {0, 0, q}};
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const CT m = rho_at(rho, kx - d[s][0], ky - d[s][1], kz - d[s][2], K);
+    const CT p = rho_at(rho, kx + d[s][0], ky + d[s][1], kz + d[s][2], K);
+    S[s] = CT{h * (m.im - p.im), -h * (m.re - p.re)};  // (m - p) / 2i
+    Co[s] = CT{h * (m.re + p.re), h * (m.im + p.im)};
+  }
+  f[0] = CT{amp * (a * S[2].re + c * Co[1].re), amp * (a * S[2].im + c * Co[1].im)};
+  f[1] = CT{amp * (b * S[0].re + a * Co[2].re), amp * (b * S[0].im + a * Co[2].im)};
+  f[2] = CT{amp * (c * S[1].re + b * Co[0].re), amp * (c * S[1].im + b * Co[0].im)};
+}
+
 // FC: element type of the product spectra (FP64, or FP32 in the mixed mode); everything else,
 // the state, the history and the arithmetic, is FP64.
 template <typename FC>
 __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in, cplx64 *state,
                                 cplx64 *__restrict__ hist, cplx64 *ystage, cplx64 *__restrict__ rhs_out,
                                 const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
-                                int op, int stage, int K, int batch, double inv_n3) {
+                                const cplx64 *__restrict__ force, int op, int stage, int K, int batch,
+                                double inv_n3) {
   const int NX = K + 1, NK = 2 * K + 1;
   const size_t spec = (size_t)NK * NK * NX;
   const size_t total = spec * batch;
@@ -64,6 +104,13 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
         const cplx64 g = {divT.re + kk[a] * cs2 * y[0].re, divT.im + kk[a] * cs2 * y[0].im};
         const cplx64 u = f[9 + a];
         r[1 + a] = cplx64{g.im - nu * k2 * u.re, -g.re - nu * k2 * u.im};
+      }
+      if (force != nullptr && phys[inst].famp != 0.0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const cplx64 fo = force[((size_t)inst * 3 + a) * spec + m];
+          r[1 + a] = cplx64{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+        }
       }
     }
     // induction: i k x E - eta k^2 B
@@ -128,8 +175,8 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
 __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32 *y_in, cplx32 *s_hi,
                                    cplx32 *__restrict__ s_lo, cplx32 *__restrict__ hist, cplx32 *ystage,
                                    cplx64 *__restrict__ rhs_out, const PhysDev *__restrict__ phys,
-                                   const StepCoef *__restrict__ coef, int op, int stage, int K, int batch,
-                                   float inv_n3) {
+                                   const StepCoef *__restrict__ coef, const cplx32 *__restrict__ force, int op,
+                                   int stage, int K, int batch, float inv_n3) {
   const int NX = K + 1, NK = 2 * K + 1;
   const size_t spec = (size_t)NK * NK * NX;
   const size_t total = spec * batch;
@@ -168,6 +215,13 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32
                           kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im + kk[a] * cs2 * y[0].im};
         const cplx32 u = f[9 + a];
         r[1 + a] = cplx32{g.im - nuk2 * u.re, -g.re - nuk2 * u.im};
+      }
+      if (force != nullptr && ph.famp != 0.0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const cplx32 fo = force[((size_t)inst * 3 + a) * spec + m];
+          r[1 + a] = cplx32{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+        }
       }
     }
     {
@@ -222,6 +276,31 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32
         s_lo[i] = lo;
       }
     }
+  }
+}
+
+// rho f_ABC of every kept mode into force[inst][3][spec], from the density spectrum of `y_in`.
+// A pass of its own: the assembly updates the state in place, so it must not read neighbouring
+// modes of it.
+template <typename CT>
+__global__ void force_kernel(const CT *__restrict__ y_in, CT *__restrict__ force, const PhysDev *__restrict__ phys,
+                             int K, int batch) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const size_t total = spec * batch;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(idx / spec);
+    const size_t m = idx - (size_t)inst * spec;
+    const PhysDev ph = phys[inst];
+    if (ph.famp == 0.0) continue;
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    CT fo[3];
+    abc_force(y_in + (size_t)inst * 7 * spec, kxi, kept_wave((int)(t % NK), K), kept_wave((int)(t / NK), K), K, ph,
+              fo);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) force[((size_t)inst * 3 + a) * spec + m] = fo[a];
   }
 }
 
@@ -377,21 +456,31 @@ static unsigned grid_for(size_t total, int threads) {
 
 cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *state, cplx64 *hist, cplx64 *ystage,
                             cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op, int stage,
-                            const Dims &d, cudaStream_t s) {
+                            const Dims &d, cudaStream_t s, const cplx64 *force) {
   const size_t total = d.spec * d.batch;
   const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
   assemble_kernel<cplx64><<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, state, hist, ystage, rhs_out, phys, coef,
-                                                               op, stage, d.k, d.batch, inv_n3);
+                                                               force, op, stage, d.k, d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force(const cplx64 *y_in, cplx64 *force, const PhysDev *phys, const Dims &d, cudaStream_t s) {
+  force_kernel<cplx64><<<grid_for(d.spec * d.batch, 256), 256, 0, s>>>(y_in, force, phys, d.k, d.batch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force(const cplx32 *y_in, cplx32 *force, const PhysDev *phys, const Dims &d, cudaStream_t s) {
+  force_kernel<cplx32><<<grid_for(d.spec * d.batch, 256), 256, 0, s>>>(y_in, force, phys, d.k, d.batch);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist,
                                cplx32 *ystage, cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op,
-                               int stage, const Dims &d, cudaStream_t s) {
+                               int stage, const Dims &d, cudaStream_t s, const cplx32 *force) {
   const size_t total = d.spec * d.batch;
   const float inv_n3 = (float)(1.0 / ((double)d.n * d.n * d.n));
   assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, s_hi, s_lo, hist, ystage, rhs_out, phys, coef,
-                                                          op, stage, d.k, d.batch, inv_n3);
+                                                          force, op, stage, d.k, d.batch, inv_n3);
   return cudaGetLastError();
 }
 

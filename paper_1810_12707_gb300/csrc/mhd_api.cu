@@ -57,6 +57,7 @@ struct mhd_ctx {
   // options and the captured step
   bool use_graph = true;
   bool flux_pipeline = false;
+  bool forced = false;  // some instance has the ABC body force on
   int tile[4] = {0, 0, 0, 0};
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -350,7 +351,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
     return MHD_ENOMEM;
   }
   std::vector<mhd::PhysDev> pd(p->batch);
-  for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs};
+  for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
   const std::vector<cplx64> w = twiddles(c->d.n);
   std::vector<cplx32> w32(w.size());
   for (size_t i = 0; i < w.size(); ++i) w32[i] = cplx32{(float)w[i].re, (float)w[i].im};
@@ -499,15 +500,19 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
     const cplx64 *yi = static_cast<const cplx64 *>(y_in);
     if ((st = flux_spectra_t<cplx64>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw))) return st;
     cplx64 *Y = c->Y ? static_cast<cplx64 *>(c->Y) + off : nullptr;
+    cplx64 *force = c->forced ? c->W2 : nullptr;  // W2 is free after the forward z pass
+    if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
     LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
-                                   c->stream));
+                                   c->stream, force));
   } else {
     const cplx32 *yi = static_cast<const cplx32 *>(y_in);
     if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32))) return st;
     cplx32 *Y = c->Y ? static_cast<cplx32 *>(c->Y) + off : nullptr;
+    cplx32 *force = c->forced ? reinterpret_cast<cplx32 *>(c->W2) : nullptr;  // free after forward z
+    if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
     LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), yi, state_hi(c, inst0),
                                       state_lo(c, inst0), hist32(c, inst0), Y, rhs_out, phys, coef, op, stage, d,
-                                      c->stream));
+                                      c->stream, force));
   }
   return MHD_OK;
 }
@@ -672,6 +677,22 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   }
   CK(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
+  return MHD_OK;
+}
+
+mhd_status mhd_set_forcing(mhd_ctx *c, int32_t inst, double amp, double a, double b, double cc, int32_t kf) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!isfinite(amp) || !isfinite(a) || !isfinite(b) || !isfinite(cc)) return fail(c, MHD_EINVAL, "non-finite forcing");
+  if (kf < 1 || kf > c->d.k) return fail(c, MHD_EINVAL, "forcing wavenumber %d outside 1..%d", kf, c->d.k);
+  DeviceGuard g(c->device);
+  const mhd::PhysDev pd{c->phys_host[inst].nu, c->phys_host[inst].eta, c->phys_host[inst].cs, amp, a, b, cc, kf, 0};
+  CK(cudaMemcpyAsync(c->phys + inst, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (amp != 0.0 && !c->forced) {
+    c->forced = true;  // the step gains the force pass: recapture
+    drop_graphs(c);
+  }
   return MHD_OK;
 }
 
@@ -862,7 +883,7 @@ mhd_status mhd_pool_admit(mhd_pool *p, const mhd_phys *phys, const double *rho, 
   if (handle < 0) return MHD_EBUSY;
   DeviceGuard g(c->device);
   const int pos = c->live;
-  const mhd::PhysDev pd{phys->nu, phys->eta, phys->cs};
+  const mhd::PhysDev pd{phys->nu, phys->eta, phys->cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
   CK(cudaMemcpyAsync(c->phys + pos, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
   c->phys_host[pos] = *phys;
   mhd_status st = mhd_set_state(c, pos, rho, u, b, on_device);

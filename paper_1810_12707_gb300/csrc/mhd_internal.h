@@ -49,9 +49,12 @@ struct StepCoef {
   int32_t skip;
 };
 
-// Per-instance physical parameters in device memory.
+// Per-instance physical parameters in device memory; famp != 0 switches on the ABC body force
+// rho f, f = famp (fa sin kf z + fc cos kf y, fb sin kf x + fa cos kf z, fc sin kf y + fb cos kf x).
 struct PhysDev {
   double nu, eta, cs;
+  double famp, fa, fb, fc;
+  int fkf, pad;
 };
 
 struct Dims {
@@ -138,9 +141,15 @@ enum AsmOp {
 
 // Spectral assembly of the RHS from the 12 product spectra (scaled by N^-3) and the state y_in,
 // followed by `op`; `stage` is the RK4 stage (1..3) for ASM_RK_STAGE.
+// `force` (nullable): rho f spectra [inst][3][spec] from launch_force, added to the momentum RHS
+// of the instances whose famp is non-zero.
 cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *state, cplx64 *hist, cplx64 *ystage,
                             cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op, int stage,
-                            const Dims &d, cudaStream_t s);
+                            const Dims &d, cudaStream_t s, const cplx64 *force = nullptr);
+// Spectra of the ABC body force rho f at the state y_in: force[inst][3][spec] (instances with
+// famp == 0 are skipped).  Must run before an assembly that updates y_in in place.
+cudaError_t launch_force(const cplx64 *y_in, cplx64 *force, const PhysDev *phys, const Dims &d, cudaStream_t s);
+cudaError_t launch_force(const cplx32 *y_in, cplx32 *force, const PhysDev *phys, const Dims &d, cudaStream_t s);
 
 // Mixed precision keeps the state as double-float pairs: S_hi and S_lo ([inst][7][spec] FP32
 // complex each, hi + lo carrying a 48-bit significand), the history and the stage state in FP32.
@@ -148,7 +157,7 @@ cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *stat
 // RHS in FP64 to `rhs_out`.
 cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist,
                                cplx32 *ystage, cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op,
-                               int stage, const Dims &d, cudaStream_t s);
+                               int stage, const Dims &d, cudaStream_t s, const cplx32 *force = nullptr);
 // FP64 spectra <-> (hi, lo) pairs of `count` complex values.
 cudaError_t launch_split_state(const cplx64 *in, cplx32 *hi, cplx32 *lo, size_t count, cudaStream_t s);
 cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out, size_t count, cudaStream_t s);

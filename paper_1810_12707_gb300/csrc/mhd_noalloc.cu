@@ -147,7 +147,7 @@ extern "C" MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, c
   double *part = reinterpret_cast<double *>(base + kOffPart);
   const cplx64 *tw = reinterpret_cast<const cplx64 *>(base + (n == 16 ? kOffTw16 : kOffTw32));
   mhd::PhysDev *pd = reinterpret_cast<mhd::PhysDev *>(base + kOffPhys);
-  const mhd::PhysDev hp{phys->nu, phys->eta, phys->cs};
+  const mhd::PhysDev hp{phys->nu, phys->eta, phys->cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
   NA_CK(cudaMemcpyAsync(pd, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
 
   // state spectra from the real-space fields (m = rho u), truncated and normalised

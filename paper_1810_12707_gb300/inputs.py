@@ -130,3 +130,41 @@ def ensemble_params(count: int, seed: int = 4):
     eta = 10.0 ** rng.uniform(-3.0, -2.0, count)
     mach = rng.uniform(0.05, 0.5, count)
     return nu, eta, mach
+
+
+def paper_flow(n: int, kind: str, A: float = 1.0, B: float = 1.0, C: float = 1.0, k0: int = 1,
+               u0: float = 1.0) -> np.ndarray:
+    """The unforced initial flows of the paper's energy-exchange runs, as printed
+    (section "for magnetohydrodynamic flow"):
+      "abc"          (A sin k0 z + C cos k0 y, B sin k0 x + A cos k0 z, C sin k0 y + B cos k0 x)
+      "abc_single"   U0 (A sin k0 z, B sin k0 x, C sin k0 y)
+      "tg_paper"     A U0 (cos k0 x sin k0 y cos k0 z, -sin k0 x cos k0 y cos k0 z, 0)
+      "cats_eye"     U0 (B sin k0 y, A sin k0 x, A cos k0 x - B cos k0 y)"""
+    X, Y, Z = grid(n)
+    k = float(k0)
+    if kind == "abc":
+        u = [A * np.sin(k * Z) + C * np.cos(k * Y), B * np.sin(k * X) + A * np.cos(k * Z),
+             C * np.sin(k * Y) + B * np.cos(k * X)]
+    elif kind == "abc_single":
+        u = [u0 * A * np.sin(k * Z), u0 * B * np.sin(k * X), u0 * C * np.sin(k * Y)]
+    elif kind == "tg_paper":
+        u = [A * u0 * np.cos(k * X) * np.sin(k * Y) * np.cos(k * Z),
+             -A * u0 * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z), np.zeros_like(X)]
+    elif kind == "cats_eye":
+        u = [u0 * B * np.sin(k * Y), u0 * A * np.sin(k * X), u0 * (A * np.cos(k * X) - B * np.cos(k * Y))]
+    else:
+        raise ValueError(f"unknown flow {kind!r}")
+    return np.ascontiguousarray(np.stack(u))
+
+
+def energy_exchange(n: int, kind: str, seed: int = 0, mach: float = 0.1, re: float = 450.0,
+                    rm: float = 450.0) -> InitialCondition:
+    """Energy-exchange run: one of the paper's flows with a seeded random |k| <= 4 solenoidal
+    magnetic field of the same energy as the flow (Alfven Mach number 1: equal initial kinetic and
+    magnetic energies), rho = 1, Cs = 1 / mach, nu = 1 / Re, eta = 1 / Rm."""
+    u = paper_flow(n, kind)
+    rng = np.random.default_rng(seed)
+    b = random_solenoidal(n, rng)
+    b *= rms(u) / rms(b)
+    return InitialCondition(np.ones((n, n, n)), u, np.ascontiguousarray(b), 1.0 / re, 1.0 / rm, 1.0 / mach,
+                            f"energy_exchange_{kind}", {"seed": seed, "mach": mach})

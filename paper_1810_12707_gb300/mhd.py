@@ -34,7 +34,7 @@ EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "
            "mhd_diagnostics", "mhd_checkpoint_doubles", "mhd_checkpoint", "mhd_restore", "mhd_profile",
            "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
            "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
-           "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info")
+           "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing")
 
 
 class MhdError(RuntimeError):
@@ -133,6 +133,8 @@ def load_library(path: str = LIBRARY):
     lib.mhd_pool_retire.argtypes = [P, I32, P, P, P, I32]
     lib.mhd_pool_info.restype = I32
     lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.mhd_set_forcing.restype = I32
+    lib.mhd_set_forcing.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, I32]
     lib.mhd_set_option.restype = I32
     lib.mhd_set_option.argtypes = [P, I32, ctypes.c_int64]
     lib.mhd_rhs_noalloc.restype = I32
@@ -296,6 +298,11 @@ def mhd_step(ctx: Context, nsteps: int = 1) -> None:
 
 def mhd_set_option(ctx: Context, option: int, value: int) -> None:
     _check(ctx, load_library().mhd_set_option(ctx.handle, int(option), int(value)))
+
+
+def mhd_set_forcing(ctx: Context, inst: int, amp: float, A: float = 1.0, B: float = 1.0, C: float = 1.0,
+                    kf: int = 1) -> None:
+    _check(ctx, load_library().mhd_set_forcing(ctx.handle, int(inst), float(amp), float(A), float(B), float(C), int(kf)))
 
 
 def mhd_synchronize(ctx: Context) -> int:

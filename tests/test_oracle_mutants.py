@@ -36,6 +36,8 @@ MUTANTS = [
     ("RK4 stage weights", "st < 2 ? 2.0 : 1.0", "st < 2 ? 1.0 : 2.0"),
     ("RK4 stage point", "const double cstage[3] = {0.5, 0.5, 1.0};", "const double cstage[3] = {0.5, 1.0, 1.0};"),
     ("PC corrector weight", "y[i] + 0.5 * dt * (fn[i] + fs[i])", "y[i] + dt * (fn[i] + fs[i])"),
+    ("force component swapped", "rho * F * (A * sin(kf * Z) + C * cos(kf * Y))", "rho * F * (C * sin(kf * Z) + A * cos(kf * Y))"),
+    ("force without density", "c->rflux[1][i] = rho * F *", "c->rflux[1][i] = F *"),
 ]
 
 
@@ -108,6 +110,17 @@ def _battery(om, lib):
     # variable-step Adams-Bashforth against the integral of its interpolant
     if not check_variable_step(om, lib):
         failed.append("variable step")
+    # ABC body force on a non-uniform density
+    rho_e, u_e, B_e = rc.STATES["mixed"]
+    f = rc.abc_force(0.7, 1.0, 0.6, 0.3, 1)
+    ex = rc.continuum_rhs(rho_e, u_e, B_e, 1.7, 0.03, 0.05)
+    ex = [rc.on_grid(e, 32) for e in [ex[0]] + [ex[1 + a] + rho_e * f[a] for a in range(3)] + ex[4:]]
+    o = om.Oracle(32, 0.03, 0.05, 1.7, dt=1e-3, lib=lib, forcing=(0.7, 1.0, 0.6, 0.3, 1))
+    o.set_state(rc.on_grid(rho_e, 32), np.stack([rc.on_grid(e, 32) for e in u_e]),
+                np.stack([rc.on_grid(e, 32) for e in B_e]))
+    drho, dm, db = o.rhs()
+    if any(np.max(np.abs(g - e)) > 1e-11 * 10 for g, e in zip([drho, *dm, *db], ex)):
+        failed.append("forcing")
     # the z-axis mask on aliased indices
     Z = grid(n)[2]
     o = om.Oracle(n, 0.01, 0.02, 1.1, dt=1e-3, lib=lib)

@@ -134,3 +134,30 @@ def test_mask_boundary_keeps_kmax_and_drops_kmax_plus_one(oracle_mod):
             else:
                 assert np.max(np.abs(bb)) <= 1e-13  # only rounding leaks
     assert oracle_mod.kmax(32) == 10 and oracle_mod.kmax(16) == 5 and oracle_mod.kmax(256) == 85
+
+
+def abc_force(amp, A, B, C, kf):
+    """The ABC body force as printed (section "for magnetohydrodynamic flow"), times `amp`."""
+    return [amp * (A * sp.sin(kf * z) + C * sp.cos(kf * y)),
+            amp * (B * sp.sin(kf * x) + A * sp.cos(kf * z)),
+            amp * (C * sp.sin(kf * y) + B * sp.cos(kf * x))]
+
+
+@pytest.mark.parametrize("kf", [1, 2])
+def test_forced_rhs_adds_rho_times_abc_force(oracle_mod, kf):
+    """Eq. velocity with its body-force term rho f: the momentum RHS gains rho f_ABC."""
+    n = 32
+    cs, nu, eta = 1.7, 0.03, 0.05
+    amp, A, B, C = 0.7, 1.0, 0.6, 0.3
+    rho_e, u_e, B_e = STATES["mixed"]
+    exact = continuum_rhs(rho_e, u_e, B_e, cs, nu, eta)
+    f = abc_force(amp, A, B, C, kf)
+    exact = [exact[0]] + [exact[1 + a] + rho_e * f[a] for a in range(3)] + exact[4:]
+    exact = [on_grid(e, n) for e in exact]
+    o = oracle_mod.Oracle(n, nu, eta, cs, dt=1e-3, forcing=(amp, A, B, C, kf))
+    o.set_state(on_grid(rho_e, n), np.stack([on_grid(e, n) for e in u_e]),
+                np.stack([on_grid(e, n) for e in B_e]))
+    got = [o.rhs()[0], *o.rhs()[1], *o.rhs()[2]]
+    scale = max(np.max(np.abs(e)) for e in exact)
+    for g, e in zip(got, exact):
+        assert np.max(np.abs(g - e)) <= 1e-12 * scale
