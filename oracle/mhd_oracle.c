@@ -13,7 +13,10 @@
  *   d(rho u)/dt = -div[ rho u(x)u + (P + |B|^2/2) I - B(x)B ] + mu lap(u),   P = Cs^2 rho
  *   dB/dt      = -div( u(x)B - B(x)u ) + eta lap(B)
  * in the component form the paper writes out for the momentum and induction equations
- * (section "Governing equations"), with no forcing and no energy equation (isothermal closure).
+ * (section "Governing equations"), with no energy equation (isothermal closure), plus the
+ * optional ABC body force rho f of section "for magnetohydrodynamic flow" in the momentum
+ * equation.  Diagnostics: grid energies and means, and the shell spectra, theta' and S_3 of the
+ * hydrodynamic-flow section (or_spectra).
  *
  * Spatial discretisation (paper, section "Code G-MHD3D"; Table I): pseudo-spectral.  Derivatives
  * are products with i k in Fourier space, nonlinear products are formed in real space.  Products
@@ -664,6 +667,101 @@ int or_diagnostics(or_ctx *c, double *out) {
   out[15] = c->t;
   out[16] = c->dt_last;
   out[17] = (double)c->step;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Spectra and velocity-derivative statistics                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Number of spectral shells of an n^3 grid: shells 0 .. round(sqrt(3) k_max). */
+int or_num_shells(int n) {
+  const int k = or_kmax(n);
+  return (int)floor(sqrt(3.0 * k * k) + 0.5) + 1;
+}
+
+/*
+ * Shell-summed spectra and the velocity-derivative statistics of the hydrodynamic-flow section
+ * (theta' and the skewness S_3 of du_1/dx_1).  Readings: the velocity is u = m / rho on the grid,
+ * transformed and cut to the dealiased modes (the spectra and derivatives of the truncated
+ * field); a mode k belongs to shell s = round(|k|); the shell sums run over the whole spectrum,
+ * so that sum_s ek[s] = <|u_D|^2>/2 and sum_s em[s] = <|B|^2>/2 (Parseval, with this oracle's
+ * forward normalisation).
+ *   ek[s], em[s]  sum over the dealiased k with round(|k|) = s of |u_hat(k)|^2/2, |B_hat(k)|^2/2
+ *   stats[0]      theta' = sqrt(<(div u_D)^2>), div u_D formed on the grid
+ *   stats[1]      S_3 = <d^3> / <d^2>^{3/2},  d = du_x/dx of u_D, on the grid
+ *   stats[2..3]   <d^2>, <d^3>
+ * `nshell` must equal or_num_shells(n).
+ */
+int or_spectra(or_ctx *c, int nshell, double *ek, double *em, double *stats) {
+  const int n = c->p.n;
+  const size_t n3 = c->n3;
+  if (nshell != or_num_shells(n)) return -1;
+  cplx *uh[3];
+  double *g = (double *)malloc(sizeof(double) * n3);
+  int ok = g != NULL;
+  for (int a = 0; a < 3; ++a) ok &= (uh[a] = (cplx *)malloc(sizeof(cplx) * n3)) != NULL;
+  if (!ok) {
+    free(g);
+    for (int a = 0; a < 3; ++a) free(uh[a]);
+    return -2;
+  }
+  /* u = m / rho on the grid, then its dealiased spectrum */
+  or_inverse_tmp(c->state[F_RHO], c->real[F_RHO], n, c->tmp);
+  for (int a = 0; a < 3; ++a) {
+    or_inverse_tmp(c->state[F_MX + a], c->real[F_MX + a], n, c->tmp);
+    for (size_t i = 0; i < n3; ++i) g[i] = c->real[F_MX + a][i] / c->real[F_RHO][i];
+    or_forward(g, uh[a], n);
+    apply_mask(uh[a], n);
+  }
+  for (int s = 0; s < nshell; ++s) ek[s] = em[s] = 0.0;
+  for (int z = 0; z < n; ++z) {
+    for (int y = 0; y < n; ++y) {
+      for (int x = 0; x < n; ++x) {
+        if (!mask23(x, y, z, n)) continue;
+        const double kx = wavenumber(x, n), ky = wavenumber(y, n), kz = wavenumber(z, n);
+        const int sh = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
+        const size_t i = ((size_t)z * n + y) * n + x;
+        for (int a = 0; a < 3; ++a) {
+          const cplx v = uh[a][i], b = c->state[F_BX + a][i];
+          ek[sh] += 0.5 * (creal(v) * creal(v) + cimag(v) * cimag(v));
+          em[sh] += 0.5 * (creal(b) * creal(b) + cimag(b) * cimag(b));
+        }
+      }
+    }
+  }
+  /* div u_D on the grid */
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const size_t i = ((size_t)z * n + y) * n + x;
+        c->tmp[i] = I * (wavenumber(x, n) * uh[0][i] + wavenumber(y, n) * uh[1][i] + wavenumber(z, n) * uh[2][i]);
+      }
+  or_fft3d(c->tmp, n, +1);
+  double th = 0.0;
+  for (size_t i = 0; i < n3; ++i) th += creal(c->tmp[i]) * creal(c->tmp[i]);
+  /* d = du_x/dx on the grid */
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const size_t i = ((size_t)z * n + y) * n + x;
+        c->tmp[i] = I * wavenumber(x, n) * uh[0][i];
+      }
+  or_fft3d(c->tmp, n, +1);
+  double m2 = 0.0, m3 = 0.0;
+  for (size_t i = 0; i < n3; ++i) {
+    const double d = creal(c->tmp[i]);
+    m2 += d * d;
+    m3 += d * d * d;
+  }
+  m2 /= (double)n3;
+  m3 /= (double)n3;
+  stats[0] = sqrt(th / (double)n3);
+  stats[1] = m3 / pow(m2, 1.5);
+  stats[2] = m2;
+  stats[3] = m3;
+  free(g);
+  for (int a = 0; a < 3; ++a) free(uh[a]);
   return 0;
 }
 

@@ -68,6 +68,8 @@ def _declare(lib):
     lib.or_forward.argtypes = [D, D, ctypes.c_int]
     lib.or_inverse.argtypes = [D, D, ctypes.c_int]
     lib.or_kmax.argtypes = [ctypes.c_int]
+    lib.or_num_shells.argtypes = [ctypes.c_int]
+    lib.or_spectra.argtypes = [P, ctypes.c_int, D, D, D]
     return lib
 
 
@@ -242,3 +244,12 @@ class Oracle:
         d["step"] = int(d["step"])
         d["etot"] = d["ke"] + d["me"] + d["eint"]
         return d
+
+    def spectra(self) -> dict:
+        """Shell spectra ek, em (index = shell) and theta', S3, <d^2>, <d^3> of d = du_x/dx."""
+        ns = int(self._lib.or_num_shells(self.n))
+        ek, em, st = np.zeros(ns), np.zeros(ns), np.zeros(4)
+        rc = self._lib.or_spectra(self._h, ns, _dp(ek), _dp(em), _dp(st))
+        if rc != 0:
+            raise RuntimeError(f"or_spectra failed ({rc})")
+        return {"ek": ek, "em": em, "theta": st[0], "s3": st[1], "d2": st[2], "d3": st[3]}

@@ -168,3 +168,39 @@ def energy_exchange(n: int, kind: str, seed: int = 0, mach: float = 0.1, re: flo
     b *= rms(u) / rms(b)
     return InitialCondition(np.ones((n, n, n)), u, np.ascontiguousarray(b), 1.0 / re, 1.0 / rm, 1.0 / mach,
                             f"energy_exchange_{kind}", {"seed": seed, "mach": mach})
+
+
+def decaying_turbulence(n: int, k0: float, seed: int, u_rms: float = 1.0, mach: float = 0.1,
+                        nu: float = 5e-3) -> InitialCondition:
+    """Decaying compressible turbulence of the hydrodynamic-flow section: a seeded random
+    solenoidal velocity whose shell spectrum is E(k) = A k^4 exp(-2 k^2 / k0^2) on the shells
+    k = 1 .. k_max (a mode k belongs to shell round(|k|)), A fixed by the RMS speed `u_rms`;
+    rho = 1, B = 0 (the induction equation then stays at B = 0), Cs = u_rms / mach, eta = nu.
+
+    Recipe: complex Gaussian vectors on every dealiased wavevector with round(|k|) <= k_max,
+    projected normal to k; the real part of their inverse transform; each shell of that field's
+    spectrum rescaled to the target energy; the field rescaled to `u_rms`."""
+    kmax = (n - 1) // 3
+    k1 = np.fft.fftfreq(n, 1.0 / n)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    k2 = KX * KX + KY * KY + KZ * KZ
+    shell = np.floor(np.sqrt(k2) + 0.5).astype(np.int64)
+    keep = ((3 * np.abs(KX) < n) & (3 * np.abs(KY) < n) & (3 * np.abs(KZ) < n) & (shell >= 1) & (shell <= kmax))
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((3, n, n, n)) + 1j * rng.standard_normal((3, n, n, n))
+    kv = np.stack([KX, KY, KZ])
+    safe = np.where(k2 > 0, k2, 1.0)
+    a = (a - kv * (np.sum(kv * a, axis=0) / safe)) * keep
+    u = np.real(np.fft.ifftn(a, axes=(1, 2, 3)))
+    uh = np.fft.fftn(u, axes=(1, 2, 3))
+    e_now = np.bincount(shell.ravel(), weights=np.sum(np.abs(uh) ** 2, axis=0).ravel(), minlength=kmax + 2)
+    s = np.arange(len(e_now), dtype=np.float64)
+    target = s ** 4 * np.exp(-2.0 * s * s / (k0 * k0))
+    gain = np.zeros_like(e_now)
+    ok = (s >= 1) & (s <= kmax) & (e_now > 0)
+    gain[ok] = np.sqrt(target[ok] / e_now[ok])
+    uh *= gain[np.minimum(shell, len(gain) - 1)] * keep
+    u = np.real(np.fft.ifftn(uh, axes=(1, 2, 3)))
+    u *= u_rms / rms(u)
+    return InitialCondition(np.ones((n, n, n)), np.ascontiguousarray(u), np.zeros((3, n, n, n)), nu, nu,
+                            u_rms / mach, "decaying_turbulence", {"seed": seed, "k0": k0, "mach": mach})

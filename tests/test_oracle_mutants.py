@@ -12,6 +12,7 @@ import test_oracle_integrators as integ
 import test_oracle_invariants as inv
 import test_oracle_linear_waves as lw
 import test_oracle_rhs_closed_form as rc
+import test_oracle_spectra as spec
 from paper_1810_12707_gb300.inputs import grid
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "mhd_oracle.c")
@@ -38,6 +39,11 @@ MUTANTS = [
     ("PC corrector weight", "y[i] + 0.5 * dt * (fn[i] + fs[i])", "y[i] + dt * (fn[i] + fs[i])"),
     ("force component swapped", "rho * F * (A * sin(kf * Z) + C * cos(kf * Y))", "rho * F * (C * sin(kf * Z) + A * cos(kf * Y))"),
     ("force without density", "c->rflux[1][i] = rho * F *", "c->rflux[1][i] = F *"),
+    ("shell by floor not round", "sqrt(kx * kx + ky * ky + kz * kz) + 0.5)", "sqrt(kx * kx + ky * ky + kz * kz))"),
+    ("spectrum of m not u", "g[i] = c->real[F_MX + a][i] / c->real[F_RHO][i];", "g[i] = c->real[F_MX + a][i];"),
+    ("magnetic spectrum without 1/2", "em[sh] += 0.5 *", "em[sh] += 1.0 *"),
+    ("divergence drops z", "wavenumber(y, n) * uh[1][i] + wavenumber(z, n) * uh[2][i]", "wavenumber(y, n) * uh[1][i]"),
+    ("skewness exponent", "m3 / pow(m2, 1.5)", "m3 / pow(m2, 1.0)"),
 ]
 
 
@@ -130,6 +136,9 @@ def _battery(om, lib):
     _, dm, _ = o.rhs()
     if np.max(np.abs(dm[2] - (np.sin(Z) - 0.01 * (16 * np.cos(4 * Z) + 25 * np.cos(5 * Z))))) > 1e-11:
         failed.append("mask z")
+    # spectra, theta' and S_3
+    failed += spec.closed_form_failures(om, lib)
+    failed += spec.brute_force_failures(om, lib)
     return failed
 
 
