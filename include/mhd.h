@@ -173,6 +173,31 @@ MHD_API mhd_status mhd_synchronize(mhd_ctx *ctx);
 /* Diagnostics of instance `inst` at its current state.  Synchronises. */
 MHD_API mhd_status mhd_diagnostics(mhd_ctx *ctx, int32_t inst, mhd_diag *out);
 
+/* Velocity-derivative statistics of the hydrodynamic-flow section, all of the dealiased velocity
+ * u = m / rho (its spectrum cut to the kept modes): */
+typedef struct {
+  double theta; /* theta' = <(div u)^2>^(1/2) */
+  double s3;    /* S_3 = <d^3> / <d^2>^(3/2), d = du_x/dx */
+  double d2;    /* <d^2> */
+  double d3;    /* <d^3> */
+} mhd_flow_stats;
+
+/* Number of spectral shells of an n^3 grid, round(sqrt(3) k_max) + 1 with k_max = floor((n-1)/3);
+ * 0 for an unsupported n. */
+MHD_API int32_t mhd_num_shells(int32_t n);
+
+/* Shell spectra of instance `inst` (paper, section "for hydrodynamic flow": kinetic and magnetic
+ * energy spectra, theta' and S_3).  Mode k belongs to shell round(|k|); per shell s,
+ *   ek[s] = sum |u_hat(k)|^2 / 2,   em[s] = sum |B_hat(k)|^2 / 2
+ * over the kept modes of the full spectrum (both k and -k), with f_hat(k) = N^-3 sum f e^{-ik.x},
+ * so sum_s em[s] = <|B|^2>/2 and, when rho = 1, sum_s ek[s] = <|u|^2>/2.
+ * ek, em: HOST arrays of `nshells` doubles (= mhd_num_shells(n)), or NULL to skip; stats: HOST,
+ * or NULL.  Computed on the GPU in FP64 (after combining the mixed-precision state), with a fixed
+ * summation order: repeated calls give identical bits.  Uses the context's scratch buffers; do
+ * not overlap with a step of the same context.  Synchronises.  MHD_EINVAL for a wrong nshells. */
+MHD_API mhd_status mhd_spectra(mhd_ctx *ctx, int32_t inst, double *ek, double *em, int32_t nshells,
+                               mhd_flow_stats *stats);
+
 /* Checkpoint support.  The restartable state of an instance is its state spectra, its history
  * (the previous step's RHS spectra), and (t, dt_prev, step).  Both calls move
  * mhd_checkpoint_doubles(ctx) doubles through `buf` (host or device), in a layout private to the

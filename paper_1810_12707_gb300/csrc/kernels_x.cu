@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                        unsigned long long *__restrict__ smax_bits, int K, long long total_pairs,
                        const C *__restrict__ tw, int *err) {
   using R = typename C::value_type;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_pipe[];
   __shared__ __align__(8) uint64_t mbar[2];
   constexpr int P = pencil_pitch<C>(N);
   constexpr long long PPI = (long long)N * N / 2;  // row pairs per instance
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   const int NX = K + 1;
   const int chunk = 2 * NX;  // complex values of one field's row pair
   const uint32_t chunk_bytes = (uint32_t)(chunk * sizeof(C));
-  C *stage = reinterpret_cast<C *>(smem_raw);
+  C *stage = reinterpret_cast<C *>(smem_pipe);
   C *sm = stage + ((2 * 7 * chunk * sizeof(C) + 127) / 128 * 128) / sizeof(C);
   const int nthr = blockDim.x;
 

@@ -708,6 +708,61 @@ mhd_status mhd_synchronize(mhd_ctx *c) {
   return any ? MHD_ENONFINITE : MHD_OK;
 }
 
+int32_t mhd_num_shells(int32_t n) { return valid_n(n) ? mhd::num_shells((n - 1) / 3) : 0; }
+
+mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t nshells, mhd_flow_stats *stats) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  const mhd::Dims d = one(c);
+  const int ns = mhd::num_shells(d.k);
+  if ((ek || em) && nshells != ns) return fail(c, MHD_EINVAL, "nshells must equal mhd_num_shells(n)");
+  DeviceGuard g(c->device);
+  const size_t n3 = (size_t)d.n * d.n * d.n;
+  const size_t part_len = sizes_for(c->d, c->precision).part;
+  const int mblocks = (int)std::min<size_t>(2 * 152, part_len / 2);
+  if ((size_t)3 * ns > part_len || mblocks < 1) return fail(c, MHD_EINVAL, "scratch too small for the spectra");
+  const cplx64 *Si = nullptr;
+  if ((st = state_fp64(c, inst, &Si))) return st;
+  // u_hat: inverse z, y of the state; u = m / rho with the x passes; forward y, z
+  if ((st = inverse_zy(c, Si))) return st;
+  CK(mhd::launch_velocity_x(c->W2, c->W1, d, c->tw, c->stream));
+  CK(mhd::launch_col_forward(c->W1, c->W2, d.n, 3 * d.n, d.nx, 1.0, c->tw, c->stream));
+  CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 3, d.nk * d.nx, 1.0 / (double)n3, c->tw, c->stream));
+  // shells, and the spectrum of du_x/dx into W2
+  CK(mhd::launch_shells(c->W1, Si + 4 * d.spec, c->W2, c->part, d, c->stream));
+  std::vector<double> sh((size_t)3 * ns);
+  CK(cudaMemcpyAsync(sh.data(), c->part, sh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // du_x/dx on the grid, then its moments
+  CK(mhd::launch_col_inverse(c->W2, c->W1, d.n, 1, d.nk * d.nx, c->tw, c->stream));
+  CK(mhd::launch_col_inverse(c->W1, c->W2, d.n, d.n, d.nx, c->tw, c->stream));
+  double *real = reinterpret_cast<double *>(c->W1);
+  CK(mhd::launch_get_x(c->W2, real, 1, d, c->tw, c->stream));
+  CK(mhd::launch_moments(real, n3, c->part, mblocks, c->stream));
+  std::vector<double> mp((size_t)2 * mblocks);
+  CK(cudaMemcpyAsync(mp.data(), c->part, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double th = 0.0, m2 = 0.0, m3 = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    if (ek) ek[s] = sh[3 * s];
+    if (em) em[s] = sh[3 * s + 1];
+    th += sh[3 * s + 2];
+  }
+  for (int b = 0; b < mblocks; ++b) {
+    m2 += mp[2 * b];
+    m3 += mp[2 * b + 1];
+  }
+  m2 /= (double)n3;
+  m3 /= (double)n3;
+  if (stats) {
+    stats->theta = sqrt(th);
+    stats->d2 = m2;
+    stats->d3 = m3;
+    stats->s3 = m3 / pow(m2, 1.5);
+  }
+  return MHD_OK;
+}
+
 mhd_status mhd_diagnostics(mhd_ctx *c, int32_t inst, mhd_diag *out) {
   mhd_status st = check_inst(c, inst);
   if (st) return st;

@@ -164,6 +164,16 @@ cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out
 
 // Final reduction of the diagnostic partials of one instance plus the spectral terms; writes
 // 24 doubles to `out` (see mhd_api.cu for the order).
+// Shell spectra (kernels_spectra.cu).  launch_velocity_x: rho, m (fields 0..3 of [7][z][y][kx],
+// one instance) -> u = m / rho -> forward x -> [3][z][y][kx].  launch_shells: one block per shell,
+// out[s][3] = (E_u, E_B, sum |k.u_hat|^2) of shell s, dh = i k_x u_hat_x on every kept mode.
+// launch_moments: part[b][2] = (sum v^2, sum v^3) of a fixed share of v.
+int num_shells(int k);
+cudaError_t launch_velocity_x(const cplx64 *in, cplx64 *out, const Dims &d, const cplx64 *tw, cudaStream_t s);
+cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, double *out, const Dims &d,
+                          cudaStream_t s);
+cudaError_t launch_moments(const double *v, size_t n, double *part, int blocks, cudaStream_t s);
+
 cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state,
                                const PhysDev *phys, const TimeState *ts, double *out,
                                const Dims &d, cudaStream_t s);

@@ -34,7 +34,8 @@ EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "
            "mhd_diagnostics", "mhd_checkpoint_doubles", "mhd_checkpoint", "mhd_restore", "mhd_profile",
            "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
            "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
-           "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing")
+           "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing", "mhd_num_shells",
+           "mhd_spectra")
 
 
 class MhdError(RuntimeError):
@@ -56,6 +57,11 @@ class MhdParams(ctypes.Structure):
 
 class MhdPhys(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("eta", ctypes.c_double), ("cs", ctypes.c_double)]
+
+
+class MhdFlowStats(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("s3", ctypes.c_double), ("d2", ctypes.c_double),
+                ("d3", ctypes.c_double)]
 
 
 class MhdDiag(ctypes.Structure):
@@ -133,6 +139,11 @@ def load_library(path: str = LIBRARY):
     lib.mhd_pool_retire.argtypes = [P, I32, P, P, P, I32]
     lib.mhd_pool_info.restype = I32
     lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.mhd_num_shells.restype = I32
+    lib.mhd_num_shells.argtypes = [I32]
+    lib.mhd_spectra.restype = I32
+    lib.mhd_spectra.argtypes = [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), I32,
+                                ctypes.POINTER(MhdFlowStats)]
     lib.mhd_set_forcing.restype = I32
     lib.mhd_set_forcing.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, I32]
     lib.mhd_set_option.restype = I32
@@ -298,6 +309,21 @@ def mhd_step(ctx: Context, nsteps: int = 1) -> None:
 
 def mhd_set_option(ctx: Context, option: int, value: int) -> None:
     _check(ctx, load_library().mhd_set_option(ctx.handle, int(option), int(value)))
+
+
+def mhd_num_shells(n: int) -> int:
+    return int(load_library().mhd_num_shells(int(n)))
+
+
+def mhd_spectra(ctx: Context, inst: int = 0) -> dict:
+    """Shell spectra ek, em (index = shell round(|k|)) and theta', S3, <d^2>, <d^3> of d = du_x/dx."""
+    ns = mhd_num_shells(ctx.n)
+    ek, em = np.zeros(ns), np.zeros(ns)
+    st = MhdFlowStats()
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, load_library().mhd_spectra(ctx.handle, int(inst), ek.ctypes.data_as(dp), em.ctypes.data_as(dp), ns,
+                                           ctypes.byref(st)))
+    return {"ek": ek, "em": em, "theta": st.theta, "s3": st.s3, "d2": st.d2, "d3": st.d3}
 
 
 def mhd_set_forcing(ctx: Context, inst: int, amp: float, A: float = 1.0, B: float = 1.0, C: float = 1.0,
