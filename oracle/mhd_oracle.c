@@ -240,6 +240,11 @@ typedef struct {
   cplx *tmp;
   double t, dt_prev, dt_last;
   int64_t step;
+  /* tracer particles (section "Tracer Particles"): ntr particles, tr[m][6] = x y z vx vy vz;
+   * bgrid: the grid magnetic field they are pushed with (3 N^3) */
+  int64_t ntr;
+  double *tr;
+  double *bgrid;
 } or_ctx;
 
 static void ctx_free(or_ctx *c) {
@@ -258,6 +263,8 @@ static void ctx_free(or_ctx *c) {
   }
   for (int d = 0; d < 3; ++d) free(c->force[d]);
   free(c->tmp);
+  free(c->tr);
+  free(c->bgrid);
   free(c);
 }
 
@@ -522,6 +529,129 @@ static void axpy7(cplx *const *dst, cplx *const *a, double w, cplx *const *b, si
   }
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Tracer particles (section "Tracer Particles": CIC interpolation, Eq. tracer_eq; Boris push,   */
+/* Eq. boris; position update, Eq. euler)                                                       */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Position wrapped into the periodic box [0, 2 pi). */
+static double wrap_2pi(double x) {
+  const double L = 2.0 * M_PI;
+  double w = x - L * floor(x / L);
+  if (w >= L) w -= L; /* x just below a multiple of L can round up to L */
+  return w;
+}
+
+/*
+ * Cloud-in-cell value of the periodic grid field g (N^3, index (z*N + y)*N + x) at (x, y, z), as
+ * Eq. tracer_eq: the particle's cell has its bottom-left-front corner at grid index (i, j, k);
+ * each of the 8 corners is weighted by the volume of the sub-cell opposite to it.  Reading: the
+ * volumes are divided by the cell volume h^3 (weights summing to 1) and the printed factor dt is
+ * not applied.  Periodic: index N is index 0.
+ */
+static double cic(const double *g, int n, double x, double y, double z) {
+  const double h = 2.0 * M_PI / (double)n;
+  const int i = (int)floor(x / h), j = (int)floor(y / h), k = (int)floor(z / h);
+  /* distances from the lower faces (p - x_g^i) and to the upper faces (x_g^{i+1} - p), in cells */
+  const double lx = x / h - i, ly = y / h - j, lz = z / h - k;
+  const double ux = 1.0 - lx, uy = 1.0 - ly, uz = 1.0 - lz;
+  const int i0 = ((i % n) + n) % n, j0 = ((j % n) + n) % n, k0 = ((k % n) + n) % n;
+  const int i1 = (i0 + 1) % n, j1 = (j0 + 1) % n, k1 = (k0 + 1) % n;
+#define G(a, b, c) g[((size_t)(c) * n + (b)) * n + (a)]
+  return G(i0, j0, k0) * ux * uy * uz + G(i1, j0, k0) * lx * uy * uz + G(i0, j1, k0) * ux * ly * uz +
+         G(i1, j1, k0) * lx * ly * uz + G(i0, j0, k1) * ux * uy * lz + G(i1, j0, k1) * lx * uy * lz +
+         G(i0, j1, k1) * ux * ly * lz + G(i1, j1, k1) * lx * ly * lz;
+#undef G
+}
+
+/* Grid u = m / rho (which = 1) or B (which = 0) of the current state into out[3][N^3]. */
+static void grid_field(or_ctx *c, int which, double *out) {
+  const int n = c->p.n;
+  const size_t n3 = c->n3;
+  if (which == 0) {
+    for (int a = 0; a < 3; ++a) or_inverse_tmp(c->state[F_BX + a], out + a * n3, n, c->tmp);
+    return;
+  }
+  or_inverse_tmp(c->state[F_RHO], c->real[F_RHO], n, c->tmp);
+  for (int a = 0; a < 3; ++a) {
+    or_inverse_tmp(c->state[F_MX + a], out + a * n3, n, c->tmp);
+    for (size_t i = 0; i < n3; ++i) out[a * n3 + i] /= c->real[F_RHO][i];
+  }
+}
+
+/* CIC value of B (which = 0) or u (which = 1) at `count` positions pos[m][3] into out[m][3]. */
+int or_tracer_field(or_ctx *c, int which, int64_t count, const double *pos, double *out) {
+  double *g = (double *)malloc(sizeof(double) * 3 * c->n3);
+  if (!g) return -2;
+  grid_field(c, which, g);
+  for (int64_t m = 0; m < count; ++m) {
+    const double x = wrap_2pi(pos[3 * m]), y = wrap_2pi(pos[3 * m + 1]), z = wrap_2pi(pos[3 * m + 2]);
+    for (int a = 0; a < 3; ++a) out[3 * m + a] = cic(g + a * c->n3, c->p.n, x, y, z);
+  }
+  free(g);
+  return 0;
+}
+
+/* Place `count` tracers at pos[m][3] (wrapped into the box) with the CIC-interpolated grid
+ * velocity as their initial velocity; count = 0 removes them. */
+int or_tracers_set(or_ctx *c, int64_t count, const double *pos) {
+  free(c->tr);
+  c->tr = NULL;
+  c->ntr = 0;
+  if (count <= 0) return 0;
+  c->tr = (double *)malloc(sizeof(double) * 6 * (size_t)count);
+  if (!c->bgrid) c->bgrid = (double *)malloc(sizeof(double) * 3 * c->n3);
+  if (!c->tr || !c->bgrid) return -2;
+  double *v = (double *)malloc(sizeof(double) * 3 * (size_t)count);
+  if (!v) return -2;
+  or_tracer_field(c, 1, count, pos, v);
+  for (int64_t m = 0; m < count; ++m)
+    for (int a = 0; a < 3; ++a) {
+      c->tr[6 * m + a] = wrap_2pi(pos[3 * m + a]);
+      c->tr[6 * m + 3 + a] = v[3 * m + a];
+    }
+  free(v);
+  c->ntr = count;
+  return 0;
+}
+
+/* Positions and velocities of the tracers, [m][3] each (either may be NULL). */
+int or_tracers_get(or_ctx *c, double *pos, double *vel) {
+  for (int64_t m = 0; m < c->ntr; ++m)
+    for (int a = 0; a < 3; ++a) {
+      if (pos) pos[3 * m + a] = c->tr[6 * m + a];
+      if (vel) vel[3 * m + a] = c->tr[6 * m + 3 + a];
+    }
+  return 0;
+}
+
+/* One push of every tracer over dt in the grid magnetic field of the current state, in the
+ * paper's order: (1) the cell, (2) B at the particle by CIC, (3) the Boris velocity update with
+ * q = M = 1 and no electric field, (4) the position update with the new velocity, wrapped. */
+static void push_tracers(or_ctx *c, double dt) {
+  grid_field(c, 0, c->bgrid);
+  const size_t n3 = c->n3;
+#pragma omp parallel for schedule(static)
+  for (long m = 0; m < (long)c->ntr; ++m) {
+    double *p = c->tr + 6 * m, *v = p + 3;
+    double B[3];
+    for (int a = 0; a < 3; ++a) B[a] = cic(c->bgrid + a * n3, c->p.n, p[0], p[1], p[2]);
+    double t[3], s[3], vd[3];
+    for (int a = 0; a < 3; ++a) t[a] = B[a] * dt / 2.0;
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + t2);
+    vd[0] = v[0] + (v[1] * t[2] - v[2] * t[1]);
+    vd[1] = v[1] + (v[2] * t[0] - v[0] * t[2]);
+    vd[2] = v[2] + (v[0] * t[1] - v[1] * t[0]);
+    const double vn[3] = {v[0] + (vd[1] * s[2] - vd[2] * s[1]), v[1] + (vd[2] * s[0] - vd[0] * s[2]),
+                          v[2] + (vd[0] * s[1] - vd[1] * s[0])};
+    for (int a = 0; a < 3; ++a) {
+      v[a] = vn[a];
+      p[a] = wrap_2pi(p[a] + vn[a] * dt);
+    }
+  }
+}
+
 /*
  * Advance `nsteps` steps of the configured method.  Returns 0, or 1 if a non-finite value
  * appeared in max(|u| + c_f) or dt at the start of a step (the state is then left at the last
@@ -538,6 +668,8 @@ int or_step(or_ctx *c, int nsteps) {
     compute_rhs(c, &smax); /* f^n = f(y^n) in c->rhs */
     const double dt = c->p.dt_fixed > 0.0 ? c->p.dt_fixed : cfl_dt(c, smax);
     if (!isfinite(smax) || !isfinite(dt) || dt <= 0.0) return 1;
+    /* tracers move over [t_n, t_n + dt] in the magnetic field of y^n */
+    if (c->ntr > 0) push_tracers(c, dt);
     double a1 = 1.0, a0 = 0.0; /* AB2 coefficients of f^n and f^{n-1} */
     if (c->step > 0) {
       const double r = dt / c->dt_prev;

@@ -69,6 +69,9 @@ def _declare(lib):
     lib.or_inverse.argtypes = [D, D, ctypes.c_int]
     lib.or_kmax.argtypes = [ctypes.c_int]
     lib.or_num_shells.argtypes = [ctypes.c_int]
+    lib.or_tracer_field.argtypes = [P, ctypes.c_int, ctypes.c_int64, D, D]
+    lib.or_tracers_set.argtypes = [P, ctypes.c_int64, D]
+    lib.or_tracers_get.argtypes = [P, D, D]
     lib.or_spectra.argtypes = [P, ctypes.c_int, D, D, D]
     return lib
 
@@ -244,6 +247,26 @@ class Oracle:
         d["step"] = int(d["step"])
         d["etot"] = d["ke"] + d["me"] + d["eint"]
         return d
+
+    def tracer_field(self, which: str, pos) -> np.ndarray:
+        """CIC value of "B" or "u" at positions pos (count, 3)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        out = np.zeros_like(pos)
+        self._lib.or_tracer_field(self._h, 0 if which == "B" else 1, len(pos), _dp(pos), _dp(out))
+        return out
+
+    def tracers_set(self, pos) -> None:
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        self._ntr = len(pos)
+        if self._lib.or_tracers_set(self._h, len(pos), _dp(pos)) != 0:
+            raise RuntimeError("or_tracers_set failed")
+
+    def tracers_get(self):
+        """(positions, velocities), each (count, 3)."""
+        n = getattr(self, "_ntr", 0)
+        pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+        self._lib.or_tracers_get(self._h, _dp(pos), _dp(vel))
+        return pos, vel
 
     def spectra(self) -> dict:
         """Shell spectra ek, em (index = shell) and theta', S3, <d^2>, <d^3> of d = du_x/dx."""

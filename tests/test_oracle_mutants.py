@@ -13,6 +13,7 @@ import test_oracle_invariants as inv
 import test_oracle_linear_waves as lw
 import test_oracle_rhs_closed_form as rc
 import test_oracle_spectra as spec
+import test_oracle_tracers as trc
 from paper_1810_12707_gb300.inputs import grid
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "mhd_oracle.c")
@@ -44,6 +45,13 @@ MUTANTS = [
     ("magnetic spectrum without 1/2", "em[sh] += 0.5 *", "em[sh] += 1.0 *"),
     ("divergence drops z", "wavenumber(y, n) * uh[1][i] + wavenumber(z, n) * uh[2][i]", "wavenumber(y, n) * uh[1][i]"),
     ("skewness exponent", "m3 / pow(m2, 1.5)", "m3 / pow(m2, 1.0)"),
+    ("CIC corner weight", "G(i0, j1, k1) * ux * ly * lz", "G(i0, j1, k1) * lx * ly * uz"),
+    ("CIC cell from rounding", "const int i = (int)floor(x / h)", "const int i = (int)floor(x / h + 0.5)"),
+    ("Boris half step", "t[a] = B[a] * dt / 2.0;", "t[a] = B[a] * dt;"),
+    ("Boris s factor", "s[a] = 2.0 * t[a] / (1.0 + t2);", "s[a] = t[a];"),
+    ("Boris cross sign", "vd[1] = v[1] + (v[2] * t[0] - v[0] * t[2]);", "vd[1] = v[1] - (v[2] * t[0] - v[0] * t[2]);"),
+    ("position with old velocity", "v[a] = vn[a];\n      p[a] = wrap_2pi(p[a] + vn[a] * dt);",
+     "p[a] = wrap_2pi(p[a] + v[a] * dt);\n      v[a] = vn[a];"),
 ]
 
 
@@ -139,6 +147,9 @@ def _battery(om, lib):
     # spectra, theta' and S_3
     failed += spec.closed_form_failures(om, lib)
     failed += spec.brute_force_failures(om, lib)
+    # tracer particles
+    failed += trc.interpolation_failures(om, lib)
+    failed += trc.push_failures(om, lib)
     return failed
 
 
