@@ -173,6 +173,23 @@ MHD_API mhd_status mhd_synchronize(mhd_ctx *ctx);
 /* Diagnostics of instance `inst` at its current state.  Synchronises. */
 MHD_API mhd_status mhd_diagnostics(mhd_ctx *ctx, int32_t inst, mhd_diag *out);
 
+/* Tracer particles of instance `inst` (paper, section "Tracer Particles").  `count` particles are
+ * placed at pos[m][3] (HOST, x y z of particle m; wrapped into [0, 2 pi)); their initial velocity is
+ * the grid velocity u = m / rho interpolated by cloud-in-cell weights (Eq. tracer_eq, weights
+ * normalised by the cell volume).  Every later mhd_step moves them once per step: the grid
+ * magnetic field of the step's start state is interpolated to each particle the same way, the
+ * velocity is turned by the Boris rotation with q = M = 1 and no electric field (Eq. boris), and
+ * the position advances by the new velocity times the step's dt (Eq. euler), wrapped into the box.
+ * Tracers are passive: they do not change the flow.  count = 0 removes them.  Positions and
+ * velocities are kept in FP64 in device memory; the interpolated field has the context's
+ * precision.  Not part of checkpoints; not available on pool contexts (MHD_ESTATE).  Needs a state
+ * (MHD_ESTATE otherwise); MHD_EINVAL for a negative count or a non-finite position.  Synchronises. */
+MHD_API mhd_status mhd_tracers_set(mhd_ctx *ctx, int32_t inst, int64_t count, const double *pos);
+/* Current positions and velocities, HOST arrays [count][3] (either may be NULL).  Synchronises. */
+MHD_API mhd_status mhd_tracers_get(mhd_ctx *ctx, int32_t inst, double *pos, double *vel);
+/* Number of tracers of instance `inst`, or -1 for a bad context or index. */
+MHD_API int64_t mhd_tracers_count(mhd_ctx *ctx, int32_t inst);
+
 /* Velocity-derivative statistics of the hydrodynamic-flow section, all of the dealiased velocity
  * u = m / rho (its spectrum cut to the kept modes): */
 typedef struct {

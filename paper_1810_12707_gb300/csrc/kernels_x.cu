@@ -56,10 +56,13 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // ------------------------------------------------------------------------------------------
 // C: complex type of the data and of all arithmetic (cplx64 or cplx32); the CFL maxima are
 // combined in FP64.
+// bgrid (nullable): the grid magnetic field is also written out, [inst][3][N^3] in the data's
+// precision, for the tracer push.
 template <int N, typename C>
 __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
-                              int K, int blocks_per_inst, const C *__restrict__ tw) {
+                              int K, int blocks_per_inst, const C *__restrict__ tw,
+                              typename C::value_type *__restrict__ bgrid) {
   using R = typename C::value_type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = reinterpret_cast<C *>(smem_raw);
@@ -111,6 +114,15 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
       const C c = b[f * P];
       v[0][f] = c.re;
       v[1][f] = c.im;
+    }
+    if (bgrid != nullptr) {
+      constexpr size_t N3 = NN * N;
+      R *g = bgrid + (size_t)inst * 3 * N3 + (row0 + 2 * p) * N + j;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        g[c * N3] = v[0][4 + c];
+        g[c * N3 + N] = v[1][4 + c];
+      }
     }
     R *bd = reinterpret_cast<R *>(b);
 #pragma unroll
@@ -489,9 +501,10 @@ namespace {
 
 template <int N, typename C>
 cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
-                   cudaStream_t s, int *err) {
+                   cudaStream_t s, int *err, typename C::value_type *bgrid) {
   constexpr int PAIRS = pairs_for(N);
   if constexpr (PAIRS == 1 && sizeof(C) == 8) {
+    if (bgrid != nullptr) err = nullptr;  // the pipelined variant does not write the grid field
     const int chunk = 2 * (d.k + 1);
     const size_t stage_bytes = (2 * 7 * chunk * sizeof(C) + 127) / 128 * 128;
     const size_t smem = stage_bytes + (size_t)12 * pencil_pitch<C>(N) * sizeof(C);
@@ -519,7 +532,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (long long)bpi * d.batch;
-  flux_x_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw);
+  flux_x_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw, bgrid);
   return cudaGetLastError();
 }
 
@@ -585,13 +598,13 @@ int flux_x_blocks_per_instance(int n) { return n * n / (2 * pairs_for(n)); }
 int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
 
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err)));
+                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err, double *bgrid) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid)));
 }
 
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err)));
+                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err, float *bgrid) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid)));
 }
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,

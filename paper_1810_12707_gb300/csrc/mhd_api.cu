@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -58,6 +59,11 @@ struct mhd_ctx {
   bool use_graph = true;
   bool flux_pipeline = false;
   bool forced = false;  // some instance has the ABC body force on
+  // tracer particles: per instance a count and device data tr[6][count]; the grid magnetic field
+  // the step's flux pass writes for them ([batch][3][N^3], working precision)
+  std::vector<int64_t> ntr;
+  std::vector<double *> tr;
+  void *bgrid = nullptr;
   int tile[4] = {0, 0, 0, 0};
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -74,8 +80,8 @@ struct mhd_ctx {
 };
 
 namespace {
-const char *const kKernelNames[7] = {"inverse_z", "inverse_y", "flux_x", "step_dt", "forward_y", "forward_z",
-                                     "assemble_ab2"};
+const char *const kKernelNames[8] = {"inverse_z", "inverse_y", "flux_x", "step_dt", "forward_y", "forward_z",
+                                     "assemble_ab2", "tracer_push"};
 }
 
 namespace {
@@ -160,6 +166,17 @@ void *dalloc(mhd_ctx *c, size_t bytes) {
   }
   if (p) c->allocs.push_back(p);
   return p;
+}
+
+void dfree(mhd_ctx *c, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  if (c->p.dev_free) c->p.dev_free(p, c->p.alloc_user);
+  else cudaFree(p);
 }
 
 void free_all(mhd_ctx *c) {
@@ -320,6 +337,8 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   c->cfl_visc = p->cfl_visc > 0.0 ? p->cfl_visc : 0.5;
   c->phys_host.assign(phys, phys + p->batch);
   c->is_set.assign(p->batch, 0);
+  c->ntr.assign(p->batch, 0);
+  c->tr.assign(p->batch, nullptr);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return MHD_ECUDA;
@@ -469,9 +488,11 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 // product spectra in W1.
 // CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.  `advance`
 // runs the step-size kernel after the flux pass.
+// `bgrid` (nullable) receives the grid magnetic field for the tracers.
 template <typename CF, typename CS>
 static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, const CS *S, const mhd::PhysDev *phys,
-                                 mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw) {
+                                 mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw,
+                                 typename CF::value_type *bgrid) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
@@ -479,7 +500,7 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0]));
   LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1]));
   unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
-  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr));
+  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(bits, phys, ts, coef, d, c->dt_fixed, c->cfl_adv, c->cfl_visc, c->stream));
   }
@@ -492,13 +513,15 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
 // evaluation of a step) and the assembly operation `op` for the `d.batch` instances from `inst0`.
 static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, const void *y_in, cplx64 *rhs_out,
                                     const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, bool first,
-                                    int op, int stage) {
+                                    int op, int stage, void *bgrid = nullptr) {
   const bool prof = op != mhd::ASM_RHS && c->profiling;
   mhd_status st;
   const size_t off = (size_t)inst0 * 7 * d.spec;
   if (c->precision == MHD_FP64) {
     const cplx64 *yi = static_cast<const cplx64 *>(y_in);
-    if ((st = flux_spectra_t<cplx64>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw))) return st;
+    if ((st = flux_spectra_t<cplx64>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw,
+                                     static_cast<double *>(bgrid))))
+      return st;
     cplx64 *Y = c->Y ? static_cast<cplx64 *>(c->Y) + off : nullptr;
     cplx64 *force = c->forced ? c->W2 : nullptr;  // W2 is free after the forward z pass
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
@@ -506,7 +529,9 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
                                    c->stream, force));
   } else {
     const cplx32 *yi = static_cast<const cplx32 *>(y_in);
-    if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32))) return st;
+    if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32,
+                                     static_cast<float *>(bgrid))))
+      return st;
     cplx32 *Y = c->Y ? static_cast<cplx32 *>(c->Y) + off : nullptr;
     cplx32 *force = c->forced ? reinterpret_cast<cplx32 *>(c->W2) : nullptr;  // free after forward z
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
@@ -527,19 +552,39 @@ static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 
   if (c->Y) Y = c->precision == MHD_FP64 ? (const void *)(static_cast<cplx64 *>(c->Y) + off)
                                          : (const void *)(static_cast<cplx32 *>(c->Y) + off);
   if (mode == 0) return eval_and_assemble(c, d, inst0, y, rhs_out, phys, ts, coef, true, mhd::ASM_RHS, 0);
+  // tracers: the first evaluation (at y^n) also writes the grid field; the push follows the step
+  void *bg = nullptr;
+  for (int i = inst0; i < inst0 + d.batch && !bg; ++i)
+    if (c->ntr[i] > 0) bg = c->bgrid;
   mhd_status st;
   switch (c->integrator) {
     case MHD_RK4:
-      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_RK_STAGE, 1))) return st;
+      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_RK_STAGE, 1, bg))) return st;
       for (int sg = 2; sg <= 3; ++sg)
         if ((st = eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_RK_STAGE, sg))) return st;
-      return eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_RK_FINAL, 0);
+      st = eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_RK_FINAL, 0);
+      break;
     case MHD_PC:
-      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_PC_PRED, 0))) return st;
-      return eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_PC_CORR, 0);
+      if ((st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_PC_PRED, 0, bg))) return st;
+      st = eval_and_assemble(c, d, inst0, Y, nullptr, phys, ts, coef, false, mhd::ASM_PC_CORR, 0);
+      break;
     default:
-      return eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_AB2, 0);
+      st = eval_and_assemble(c, d, inst0, y, nullptr, phys, ts, coef, true, mhd::ASM_AB2, 0, bg);
   }
+  if (st || !bg) return st;
+  const bool prof = c->profiling;
+  const size_t n3 = (size_t)d.n * d.n * d.n;
+  for (int i = inst0; i < inst0 + d.batch; ++i) {
+    if (c->ntr[i] == 0) continue;
+    const size_t goff = (size_t)(i - inst0) * 3 * n3;
+    if (c->precision == MHD_FP64)
+      LAUNCH(7, mhd::launch_tracer_push(static_cast<const double *>(c->bgrid) + goff, c->tr[i], c->ntr[i], coef + i,
+                                        d.n, c->stream));
+    else
+      LAUNCH(7, mhd::launch_tracer_push(static_cast<const float *>(c->bgrid) + goff, c->tr[i], c->ntr[i], coef + i,
+                                        d.n, c->stream));
+  }
+  return MHD_OK;
 }
 
 extern "C" {
@@ -655,7 +700,7 @@ mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32
   mhd_status st = prof_resolve(c);
   if (st) return st;
   int k = 0;
-  for (int i = 0; i < 7 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
+  for (int i = 0; i < 8 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
   *count = k;
   return MHD_OK;
 }
@@ -706,6 +751,77 @@ mhd_status mhd_synchronize(mhd_ctx *c) {
   CK(cudaStreamSynchronize(c->stream));
   if (err) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up");
   return any ? MHD_ENONFINITE : MHD_OK;
+}
+
+mhd_status mhd_tracers_set(mhd_ctx *c, int32_t inst, int64_t count, const double *pos) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (count < 0 || (count > 0 && !pos)) return fail(c, MHD_EINVAL, "bad tracer count or null positions");
+  if (c->live >= 0) return fail(c, MHD_ESTATE, "tracers are not available on pool contexts");
+  if (count > 0 && !c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
+  DeviceGuard g(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);  // the step gains or loses launches
+  dfree(c, c->tr[inst]);
+  c->tr[inst] = nullptr;
+  c->ntr[inst] = 0;
+  if (count == 0) return MHD_OK;
+  const mhd::Dims d = one(c);
+  const size_t n3 = (size_t)d.n * d.n * d.n;
+  if (!c->bgrid) {
+    const size_t elem = c->precision == MHD_FP64 ? sizeof(double) : sizeof(float);
+    if (!(c->bgrid = dalloc(c, (size_t)c->d.batch * 3 * n3 * elem))) return fail(c, MHD_ENOMEM, "tracer grid buffer");
+  }
+  double *t = static_cast<double *>(dalloc(c, (size_t)count * 6 * sizeof(double)));
+  if (!t) return fail(c, MHD_ENOMEM, "tracer arrays (%lld particles)", (long long)count);
+  // positions, wrapped into [0, 2 pi), stored by component
+  const double L = 2.0 * M_PI;
+  std::vector<double> h((size_t)count * 3);
+  for (int64_t m = 0; m < count; ++m)
+    for (int a = 0; a < 3; ++a) {
+      const double x = pos[3 * m + a];
+      if (!std::isfinite(x)) {
+        dfree(c, t);
+        return fail(c, MHD_EINVAL, "tracer %lld has a non-finite position", (long long)m);
+      }
+      double w = x - L * floor(x / L);
+      if (w >= L) w -= L;
+      h[(size_t)a * count + m] = w;
+    }
+  CK(cudaMemcpyAsync(t, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // initial velocities: the grid velocity at the particles
+  const cplx64 *Si = nullptr;
+  if ((st = state_fp64(c, inst, &Si))) return st;
+  if ((st = inverse_zy(c, Si))) return st;
+  double *real = reinterpret_cast<double *>(c->W1);
+  CK(mhd::launch_get_x(c->W2, real, 7, d, c->tw, c->stream));
+  CK(mhd::launch_tracer_init(real, t, count, d.n, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->tr[inst] = t;
+  c->ntr[inst] = count;
+  return MHD_OK;
+}
+
+mhd_status mhd_tracers_get(mhd_ctx *c, int32_t inst, double *pos, double *vel) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  const int64_t count = c->ntr[inst];
+  if (count == 0) return MHD_OK;
+  DeviceGuard g(c->device);
+  std::vector<double> h((size_t)count * 6);
+  CK(cudaMemcpyAsync(h.data(), c->tr[inst], h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int64_t m = 0; m < count; ++m)
+    for (int a = 0; a < 3; ++a) {
+      if (pos) pos[3 * m + a] = h[(size_t)a * count + m];
+      if (vel) vel[3 * m + a] = h[(size_t)(3 + a) * count + m];
+    }
+  return MHD_OK;
+}
+
+int64_t mhd_tracers_count(mhd_ctx *c, int32_t inst) {
+  if (!c || inst < 0 || inst >= c->d.batch) return -1;
+  return c->ntr[inst];
 }
 
 int32_t mhd_num_shells(int32_t n) { return valid_n(n) ? mhd::num_shells((n - 1) / 3) : 0; }

@@ -102,11 +102,14 @@ cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, 
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and the maximum of
 // |u| + c_f per instance, accumulated as an atomic maximum on the bits into smax_bits[batch]
 // (which must start at 0).  With `err` non-null, FP32 and N >= 128 the persistent, bulk-copy
-// pipelined variant runs; a bounded wait that gives up sets *err = 1.
+// pipelined variant runs; a bounded wait that gives up sets *err = 1.  With `bgrid` non-null the
+// grid magnetic field is written to bgrid[inst][3][N^3] as well (the plain variant runs).
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err = nullptr);
+                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err = nullptr,
+                          double *bgrid = nullptr);
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr);
+                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr,
+                          float *bgrid = nullptr);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
@@ -173,6 +176,16 @@ cudaError_t launch_velocity_x(const cplx64 *in, cplx64 *out, const Dims &d, cons
 cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, double *out, const Dims &d,
                           cudaStream_t s);
 cudaError_t launch_moments(const double *v, size_t n, double *part, int blocks, cudaStream_t s);
+
+// Tracer particles (kernels_tracers.cu).  Particle data: tr[6][count] = x, y, z, vx, vy, vz (FP64,
+// positions in [0, 2 pi)).  launch_tracer_init: velocities = CIC of u = m / rho from the real
+// state fields real[7][N^3] (rho, m, B) at the stored positions.  launch_tracer_push: one Boris
+// push over coef->dt in the grid field bgrid[3][N^3] (skipped when coef->skip is set).
+cudaError_t launch_tracer_init(const double *real, double *tr, long long count, int n, cudaStream_t s);
+cudaError_t launch_tracer_push(const double *bgrid, double *tr, long long count, const StepCoef *coef, int n,
+                               cudaStream_t s);
+cudaError_t launch_tracer_push(const float *bgrid, double *tr, long long count, const StepCoef *coef, int n,
+                               cudaStream_t s);
 
 cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state,
                                const PhysDev *phys, const TimeState *ts, double *out,

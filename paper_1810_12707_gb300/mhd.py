@@ -35,7 +35,7 @@ EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "
            "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
            "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
            "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing", "mhd_num_shells",
-           "mhd_spectra")
+           "mhd_spectra", "mhd_tracers_set", "mhd_tracers_get", "mhd_tracers_count")
 
 
 class MhdError(RuntimeError):
@@ -139,6 +139,12 @@ def load_library(path: str = LIBRARY):
     lib.mhd_pool_retire.argtypes = [P, I32, P, P, P, I32]
     lib.mhd_pool_info.restype = I32
     lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.mhd_tracers_set.restype = I32
+    lib.mhd_tracers_set.argtypes = [P, I32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_tracers_get.restype = I32
+    lib.mhd_tracers_get.argtypes = [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_tracers_count.restype = ctypes.c_int64
+    lib.mhd_tracers_count.argtypes = [P, I32]
     lib.mhd_num_shells.restype = I32
     lib.mhd_num_shells.argtypes = [I32]
     lib.mhd_spectra.restype = I32
@@ -309,6 +315,24 @@ def mhd_step(ctx: Context, nsteps: int = 1) -> None:
 
 def mhd_set_option(ctx: Context, option: int, value: int) -> None:
     _check(ctx, load_library().mhd_set_option(ctx.handle, int(option), int(value)))
+
+
+def mhd_tracers_set(ctx: Context, inst: int, pos) -> None:
+    """Place tracers at pos (count, 3); their velocity starts as the interpolated grid velocity."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, load_library().mhd_tracers_set(ctx.handle, int(inst), len(pos), pos.ctypes.data_as(dp)))
+
+
+def mhd_tracers_get(ctx: Context, inst: int = 0):
+    """(positions, velocities) of the tracers, each (count, 3)."""
+    n = int(load_library().mhd_tracers_count(ctx.handle, int(inst)))
+    if n < 0:
+        raise MhdError(MHD_EINVAL, "bad context or instance")
+    pos, vel = np.zeros((n, 3)), np.zeros((n, 3))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, load_library().mhd_tracers_get(ctx.handle, int(inst), pos.ctypes.data_as(dp), vel.ctypes.data_as(dp)))
+    return pos, vel
 
 
 def mhd_num_shells(n: int) -> int:
