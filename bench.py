@@ -254,6 +254,8 @@ def run_ours(args, name, cfg):
     for i, ic in enumerate(ics):
         mhd.mhd_set_state(ctx, i, ic.rho, ic.u, ic.b)
     stream = torch.cuda.current_stream()
+    # tile widths of the column FFT passes from the library's autotuner (before any timing)
+    tiles = None if args.no_autotune else mhd.mhd_autotune(ctx, reps=3)["tiles"]
 
     # per-kernel device times from a profiled run (direct launches, events on the library's
     # stream) of K steps, after the warm-up
@@ -302,6 +304,10 @@ def run_ours(args, name, cfg):
         hs.append(h)
     outs = [(pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))) for _ in range(len(hs))]
     ectx = mhd.mhd_init(n, phys, dt=cfg["dt"], precision=prec)
+    if tiles:
+        for opt, t in zip((mhd.MHD_OPT_TILE_INV_Z, mhd.MHD_OPT_TILE_INV_Y, mhd.MHD_OPT_TILE_FWD_Y,
+                           mhd.MHD_OPT_TILE_FWD_Z), tiles):
+            mhd.mhd_set_option(ectx, opt, t)
 
     def e2e_step():
         for i in range(batch):
@@ -365,7 +371,8 @@ def run_ours(args, name, cfg):
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / (world * PAPER_256_V100) if (n == 256 and batch == 1) else None,
             "dtype": "f64" if prec == mhd.MHD_FP64 else "f32 (double-float state)", "data": "synthetic",
-            "config": config_block(name, cfg, world),
+            "config": dict(config_block(name, cfg, world),
+                           col_tiles=tiles if tiles else "library default (autotuner off)"),
             "roofline": roof,
             "kernels": per,
             "cpu_baseline": cpu,
@@ -478,6 +485,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference", "cufft"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default FFT tile widths")
     ap.add_argument("--serve", action="store_true", help="run the serving configuration instead")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--serve-k", type=int, default=10)

@@ -229,7 +229,8 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *                          Profiling (mhd_profile) always uses direct launches.
  *   MHD_OPT_TILE_INV_Z ... MHD_OPT_TILE_FWD_Z: columns per block of the four column FFT passes
  *                          (inverse z, inverse y, forward y, forward z); 0 (default) = chosen by
- *                          the library; otherwise 1..64 (an autotuner sets these).
+ *                          the library; otherwise 1..64, rounded down to a power of two
+ *                          (mhd_autotune sets these).
  *   MHD_OPT_FLUX_PIPELINE  1: the fused x pass of the mixed mode at N >= 128 runs as a persistent
  *                          kernel that prefetches the next rows with bulk copies (TMA); 0
  *                          (default): one block per row pair, which measured faster on GB300.
@@ -243,6 +244,17 @@ enum {
   MHD_OPT_FLUX_PIPELINE = 5
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
+
+/* Autotuner of the column FFT passes (the paper has no counterpart: its FFTs are library calls).
+ * For each of the four passes (inverse z, inverse y, forward y, forward z), every power-of-two
+ * tile width from 1 to 64 columns that fits the thread and shared-memory limits is launched
+ * `reps` times (1..100) on the context's own buffers, with the step's shapes (all instances, the
+ * working precision), and timed with CUDA events on the context's stream; the fastest width is
+ * set with the MHD_OPT_TILE_* options.  The chosen widths go to tiles[4] (HOST, may be NULL) and
+ * the mean milliseconds per launch of each chosen width to ms[4] (HOST, may be NULL).  Tile width
+ * does not change any result: each column's transform is the same.  The scratch buffers are
+ * overwritten; the state is only read.  Synchronises. */
+MHD_API mhd_status mhd_autotune(mhd_ctx *ctx, int32_t reps, int32_t *tiles, double *ms);
 
 /* Per-kernel device time of mhd_step, for measurement.  While profiling is on, every kernel that
  * mhd_step launches is bracketed by CUDA events on the context's stream.  mhd_profile(ctx, 1)

@@ -231,6 +231,31 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;
 }
 
+// The same in the data's precision: FP32 kernels keep the reduction off the FP64 pipe, which on
+// GB300 runs at 1/64 of the FP32 rate (widening the result is exact and monotonic, so the maximum
+// is the one an FP64 reduction of the widened values would give).
+__device__ __forceinline__ float nan_max(float a, float b) {
+  if (a != a) return a;
+  if (b != b) return b;
+  return a > b ? a : b;
+}
+
+__device__ __forceinline__ float block_nan_max(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = red[0];
+    for (int i = 1; i < nw; ++i) s = nan_max(s, red[i]);
+  }
+  return s;
+}
+
 __device__ __forceinline__ double block_nan_max(double v, double *red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_down_sync(0xffffffffu, v, o));

@@ -13,57 +13,67 @@
 #include "fft_device.cuh"
 #include "launch_util.cuh"
 
+#include <type_traits>
+
 namespace mhd {
 
 // CI, CO: element types in and out; CC: type of the transform arithmetic (= the output's).
+// A block has TC = 2^tsh columns and TC * N/8 threads: thread (l0, c) = (tid >> tsh, tid & (TC-1))
+// moves rows l0, l0 + N/8, ... of column c, so consecutive threads touch consecutive columns of a
+// row (coalesced) and no index needs a division.
 template <int N, int DIR, typename CI, typename CO, typename CC>
-__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tc,
-                               int cols, int K, double scale, const CC *__restrict__ tw) {
+__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
+                               int cols, typename CC::value_type scale, const CC *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CC *sm = reinterpret_cast<CC *>(smem_raw);
   constexpr int TPP = N / 8;
   constexpr int P = pencil_pitch<CC>(N);
-  const int NK = 2 * K + 1;
-  const int lin = DIR > 0 ? NK : N;
-  const int lout = DIR > 0 ? N : NK;
+  constexpr int K = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
+  constexpr int NK = 2 * K + 1;
+  constexpr int LIN = DIR > 0 ? NK : N;
+  constexpr int LOUT = DIR > 0 ? N : NK;
+  const int tc = 1 << tsh;
   const int tile = blockIdx.x % ntiles;
   const size_t slab = blockIdx.x / ntiles;
-  const int c0 = tile * tc;
-  const int nthr = blockDim.x;
+  const int c = threadIdx.x & (tc - 1);
+  const int l0 = threadIdx.x >> tsh;  // 0 .. TPP-1
+  const int col = tile * tc + c;
+  const bool col_ok = col < cols;
 
-  const CI *src = in + slab * (size_t)lin * cols;
-  for (int q = threadIdx.x; q < lin * tc; q += nthr) {
-    const int l = q / tc, c = q - l * tc;
-    const int col = c0 + c;
-    CC v = {0, 0};
-    if (col < cols) v = c_cvt<CC>(src[(size_t)l * cols + col]);
-    const int f = DIR > 0 ? kept_to_fft(l, K, N) : l;
-    sm[c * P + sm_idx<CC>(f)] = v;
+  const CI *src = in + slab * (size_t)LIN * cols + col;
+  CC *pen = sm + c * P;
+  // fully unrolled (the trip count is a constant), so all of a thread's loads are in flight at once
+  constexpr int NLD = (LIN + TPP - 1) / TPP;
+  CC v[NLD];
+#pragma unroll
+  for (int i = 0; i < NLD; ++i) {
+    const int l = l0 + i * TPP;
+    v[i] = CC{0, 0};
+    if (col_ok && l < LIN) v[i] = c_cvt<CC>(src[(size_t)l * cols]);
+  }
+#pragma unroll
+  for (int i = 0; i < NLD; ++i) {
+    const int l = l0 + i * TPP;
+    if (l < LIN) pen[sm_idx<CC>(DIR > 0 ? kept_to_fft(l, K, N) : l)] = v[i];
   }
   if (DIR > 0) {
-    const int nz = N - NK;  // FFT indices K+1 .. N-K-1 are outside the kept set
-    for (int q = threadIdx.x; q < nz * tc; q += nthr) {
-      const int l = q / tc, c = q - l * tc;
-      sm[c * P + sm_idx<CC>(K + 1 + l)] = CC{0, 0};
-    }
+    // FFT indices K+1 .. N-K-1 are outside the kept set
+    for (int l = l0; l < N - NK; l += TPP) pen[sm_idx<CC>(K + 1 + l)] = CC{0, 0};
   }
   __syncthreads();
 
   const int pencil = threadIdx.x / TPP;
   const int t = threadIdx.x - pencil * TPP;
-  const bool active = pencil < tc && c0 + pencil < cols;
+  const bool active = pencil < tc && tile * tc + pencil < cols;
   pencil_fft<N, DIR, CC>(sm + (active ? pencil : 0) * P, t, active, tw);
   __syncthreads();  // the store loop reads every pencil
 
-  CO *dst = out + slab * (size_t)lout * cols;
-  for (int q = threadIdx.x; q < lout * tc; q += nthr) {
-    const int l = q / tc, c = q - l * tc;
-    const int col = c0 + c;
-    if (col < cols) {
-      const int f = DIR > 0 ? l : kept_to_fft(l, K, N);
-      CC v = sm[c * P + sm_idx<CC>(f)];
-      if (DIR < 0) v = c_scale(v, (typename CC::value_type)scale);
-      dst[(size_t)l * cols + col] = c_cvt<CO>(v);
+  if (col_ok) {
+    CO *dst = out + slab * (size_t)LOUT * cols + col;
+    for (int l = l0; l < LOUT; l += TPP) {
+      CC v = pen[sm_idx<CC>(DIR > 0 ? l : kept_to_fft(l, K, N))];
+      if (DIR < 0) v = c_scale(v, scale);
+      dst[(size_t)l * cols] = c_cvt<CO>(v);
     }
   }
 }
@@ -77,18 +87,37 @@ int pick_tc(int n, int cols) {
   int tc = 8;
   while (tc * tpp < 128 && tc < 64) tc *= 2;
   while (tc * tpp > 1024) tc /= 2;
-  if (tc > cols) tc = cols;
-  return tc < 1 ? 1 : tc;
+  while (tc > 1 && tc / 2 >= cols) tc /= 2;  // no more than one power of two above `cols`
+  return tc;
+}
+
+// log2 of the largest power of two <= v (v >= 1)
+int floor_log2(int v) {
+  int s = 0;
+  while ((2 << s) <= v) ++s;
+  return s;
+}
+
+// Largest thread count a launch of this instantiation may use (its registers bound it below 1024).
+template <int N, int DIR, typename CI, typename CO>
+int col_max_threads() {
+  static int cached = 0;
+  if (cached == 0) {
+    cudaFuncAttributes a;
+    cached = cudaFuncGetAttributes(&a, col_fft_kernel<N, DIR, CI, CO, CO>) == cudaSuccess ? a.maxThreadsPerBlock : 256;
+  }
+  return cached;
 }
 
 template <int N, int DIR, typename CI, typename CO>
 cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
                          cudaStream_t s, int tile) {
-  const int K = (N - 1) / 3;
   int tc = tile > 0 ? tile : pick_tc(N, cols);
-  while (tc * (N / 8) > 1024) tc /= 2;
-  if (tc > cols) tc = cols;
+  const int max_threads = col_max_threads<N, DIR, CI, CO>();
+  while (tc > 1 && tc * (N / 8) > max_threads) tc /= 2;
   if (tc < 1) tc = 1;
+  const int tsh = floor_log2(tc);  // a requested width that is not a power of two is rounded down
+  tc = 1 << tsh;
   const int ntiles = (cols + tc - 1) / tc;
   const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
   if (smem > 48 * 1024) {
@@ -98,8 +127,8 @@ cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scal
   const long long blocks = (long long)nslab * ntiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  col_fft_kernel<N, DIR, CI, CO, CO><<<(unsigned)blocks, tc * (N / 8), smem, s>>>(in, out, ntiles, tc, cols, K,
-                                                                                 scale, tw);
+  col_fft_kernel<N, DIR, CI, CO, CO><<<(unsigned)blocks, tc * (N / 8), smem, s>>>(
+      in, out, ntiles, tsh, cols, (typename CO::value_type)scale, tw);
   return cudaGetLastError();
 }
 
@@ -119,6 +148,29 @@ cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double
 }
 
 }  // namespace
+
+int col_max_tile(int n, int dir, bool fp64, bool mixed_in) {
+  auto pick = [&](auto tag_n) -> int {
+    constexpr int N = decltype(tag_n)::value;
+    int t;
+    if (fp64) t = dir > 0 ? col_max_threads<N, +1, cplx64, cplx64>() : col_max_threads<N, -1, cplx64, cplx64>();
+    else if (dir > 0) t = mixed_in ? col_max_threads<N, +1, cplx64, cplx32>() : col_max_threads<N, +1, cplx32, cplx32>();
+    else t = col_max_threads<N, -1, cplx32, cplx32>();
+    int tc = 1;
+    while (tc * 2 * (N / 8) <= t && tc < 64) tc *= 2;
+    return tc;
+  };
+  switch (n) {
+    case 16: return pick(std::integral_constant<int, 16>());
+    case 32: return pick(std::integral_constant<int, 32>());
+    case 64: return pick(std::integral_constant<int, 64>());
+    case 128: return pick(std::integral_constant<int, 128>());
+    case 256: return pick(std::integral_constant<int, 256>());
+    case 512: return pick(std::integral_constant<int, 512>());
+    case 1024: return pick(std::integral_constant<int, 1024>());
+    default: return 1;
+  }
+}
 
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                const cplx64 *tw, cudaStream_t s, int tile) {

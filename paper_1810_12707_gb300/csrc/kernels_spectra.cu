@@ -49,12 +49,13 @@ template <int N>
 __global__ void __launch_bounds__(kMaxThreads) velocity_x_kernel(const cplx64 *__restrict__ in,
                                                                   cplx64 *__restrict__ out, int K,
                                                                   const cplx64 *__restrict__ tw) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
@@ -72,10 +73,10 @@ __global__ void __launch_bounds__(kMaxThreads) velocity_x_kernel(const cplx64 *_
       pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
     }
   }
-  for (int q = threadIdx.x; q < 4 * PAIRS * (N - 2 * K - 1); q += nthr) {
-    const int z = q % (N - 2 * K - 1);
-    const int r = q / (N - 2 * K - 1);
-    sm[r * P + sm_idx<cplx64>(K + 1 + z)] = cplx64{0.0, 0.0};
+  for (int q = threadIdx.x; q < 4 * PAIRS * (N - 2 * KT - 1); q += nthr) {
+    const int z = q % (N - 2 * KT - 1);
+    const int r = q / (N - 2 * KT - 1);
+    sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
   fft_pencils<N, +1>(4 * PAIRS, [&](int id) { return sm + id * P; }, tw);

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
                               int K, int blocks_per_inst, const C *__restrict__ tw,
                               typename C::value_type *__restrict__ bgrid) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = reinterpret_cast<C *>(smem_raw);
@@ -70,32 +71,39 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
   constexpr int P = pencil_pitch<C>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const int inst = blockIdx.x / blocks_per_inst;
   const int bl = blockIdx.x - inst * blocks_per_inst;
   const size_t row0 = (size_t)bl * PAIRS * 2;
-  const int nthr = blockDim.x;
+  // the launch uses exactly this many threads, so every loop below has a constant trip count
+  constexpr int nthr = threads_for(N, 12 * PAIRS);
 
-  // 1. load and pack the 7 state fields: pencil (p, f) at sm + (p * 12 + f) * P
-  for (int q = threadIdx.x; q < 7 * PAIRS * NX; q += nthr) {
-    const int k = q % NX;
-    const int r = q / NX;
-    const int f = r % 7, p = r / 7;
-    const C *src = in + ((size_t)(inst * 7 + f) * NN + row0 + 2 * p) * NX;
-    C *pen = sm + (p * 12 + f) * P;
-    const C x0 = src[k], x1 = src[NX + k];
-    if (k == 0) {
-      pen[0] = C{x0.re, x1.re};
-    } else {
-      pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
-      pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
+  // 1. load and pack the 7 state fields: pencil (p, f) at sm + (p * 12 + f) * P.  Unrolled: all
+  // of a thread's loads are issued before the first shared-memory store.
+  constexpr int NLD = 7 * PAIRS * NX;
+#pragma unroll
+  for (int q0 = 0; q0 < NLD; q0 += nthr) {
+    const int q = q0 + (int)threadIdx.x;
+    if (q < NLD) {
+      const int k = q % NX;
+      const int r = q / NX;
+      const int f = r % 7, p = r / 7;
+      const C *src = in + ((size_t)(inst * 7 + f) * NN + row0 + 2 * p) * NX;
+      C *pen = sm + (p * 12 + f) * P;
+      const C x0 = src[k], x1 = src[NX + k];
+      if (k == 0) {
+        pen[0] = C{x0.re, x1.re};
+      } else {
+        pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
+        pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
+      }
     }
   }
-  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
-    const int z = q % (N - 2 * K - 1);
-    const int r = q / (N - 2 * K - 1);
+  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * KT - 1); q += nthr) {
+    const int z = q % (N - 2 * KT - 1);
+    const int r = q / (N - 2 * KT - 1);
     const int f = r % 7, p = r / 7;
-    sm[(p * 12 + f) * P + sm_idx<C>(K + 1 + z)] = C{0, 0};
+    sm[(p * 12 + f) * P + sm_idx<C>(KT + 1 + z)] = C{0, 0};
   }
   __syncthreads();
 
@@ -169,8 +177,8 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
     dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
   }
 
-  const double m = block_nan_max((double)smax, red);
-  if (threadIdx.x == 0) atomicMax(smax_bits + inst, max_bits(m));
+  const R m = block_nan_max(smax, reinterpret_cast<R *>(red));
+  if (threadIdx.x == 0) atomicMax(smax_bits + inst, max_bits((double)m));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -189,13 +197,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     flux_x_pipe_kernel(const C *__restrict__ in, C *__restrict__ out, const PhysDev *__restrict__ phys,
                        unsigned long long *__restrict__ smax_bits, int K, long long total_pairs,
                        const C *__restrict__ tw, int *err) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
   extern __shared__ __align__(128) unsigned char smem_pipe[];
   __shared__ __align__(8) uint64_t mbar[2];
   constexpr int P = pencil_pitch<C>(N);
   constexpr long long PPI = (long long)N * N / 2;  // row pairs per instance
   constexpr size_t NN = (size_t)N * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const int chunk = 2 * NX;  // complex values of one field's row pair
   const uint32_t chunk_bytes = (uint32_t)(chunk * sizeof(C));
   C *stage = reinterpret_cast<C *>(smem_pipe);
@@ -255,9 +264,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
       }
     }
-    for (int q = tx; q < 7 * (N - 2 * K - 1); q += nthr) {
-      const int z = q % (N - 2 * K - 1), f = q / (N - 2 * K - 1);
-      sm[f * P + sm_idx<C>(K + 1 + z)] = C{0, 0};
+    for (int q = tx; q < 7 * (N - 2 * KT - 1); q += nthr) {
+      const int z = q % (N - 2 * KT - 1), f = q / (N - 2 * KT - 1);
+      sm[f * P + sm_idx<C>(KT + 1 + z)] = C{0, 0};
     }
     __syncthreads();
 
@@ -319,10 +328,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
 
     // CFL maximum of this pair: warp maximum, one atomic per warp
-    double m = (double)smax;
+    R m = smax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = nan_max(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(smax_bits + inst, max_bits(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(smax_bits + inst, max_bits((double)m));
     __syncthreads();
   }
 }
@@ -334,12 +343,13 @@ template <int N>
 __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__restrict__ rho, const double *__restrict__ u,
                              const double *__restrict__ b, cplx64 *__restrict__ out, int K,
                              const cplx64 *__restrict__ tw) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
@@ -375,12 +385,13 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
 template <int N>
 __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__restrict__ in, double *__restrict__ out, int nf, int K,
                              const cplx64 *__restrict__ tw) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N, N3 = NN * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
@@ -398,10 +409,10 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
       pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
     }
   }
-  for (int q = threadIdx.x; q < nf * PAIRS * (N - 2 * K - 1); q += nthr) {
-    const int z = q % (N - 2 * K - 1);
-    const int r = q / (N - 2 * K - 1);
-    sm[r * P + sm_idx<cplx64>(K + 1 + z)] = cplx64{0.0, 0.0};
+  for (int q = threadIdx.x; q < nf * PAIRS * (N - 2 * KT - 1); q += nthr) {
+    const int z = q % (N - 2 * KT - 1);
+    const int r = q / (N - 2 * KT - 1);
+    sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
   fft_pencils<N, +1>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
@@ -422,13 +433,14 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
 template <int N>
 __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__restrict__ in, const PhysDev *__restrict__ phys,
                               double *__restrict__ part, int K, const cplx64 *__restrict__ tw) {
+  constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   __shared__ double red[32];
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
-  const int NX = K + 1;
+  constexpr int NX = KT + 1;
   const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
@@ -446,10 +458,10 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
       pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
     }
   }
-  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * K - 1); q += nthr) {
-    const int z = q % (N - 2 * K - 1);
-    const int r = q / (N - 2 * K - 1);
-    sm[r * P + sm_idx<cplx64>(K + 1 + z)] = cplx64{0.0, 0.0};
+  for (int q = threadIdx.x; q < 7 * PAIRS * (N - 2 * KT - 1); q += nthr) {
+    const int z = q % (N - 2 * KT - 1);
+    const int r = q / (N - 2 * KT - 1);
+    sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
   fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);

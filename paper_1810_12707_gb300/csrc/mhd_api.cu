@@ -705,6 +705,74 @@ mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32
   return MHD_OK;
 }
 
+mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, double *ms) {
+  if (!c) return MHD_EINVAL;
+  if (reps < 1 || reps > 100) return fail(c, MHD_EINVAL, "reps must be 1..100");
+  DeviceGuard g(c->device);
+  const mhd::Dims &d = c->d;
+  const int b = d.batch;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, MHD_ECUDA, "event creation failed");
+  }
+  // one launch of column pass `kind` with tile width `tile`, on the step's buffers and shapes
+  auto run = [&](int kind, int tile) -> cudaError_t {
+    if (c->precision == MHD_FP64) {
+      cplx64 *w1 = c->W1, *w2 = c->W2;
+      switch (kind) {
+        case 0: return mhd::launch_col_inverse(state64(c, 0), w1, d.n, b * 7, d.nk * d.nx, c->tw, c->stream, tile);
+        case 1: return mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, c->tw, c->stream, tile);
+        case 2: return mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw, c->stream, tile);
+        default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw, c->stream, tile);
+      }
+    }
+    cplx32 *w1 = reinterpret_cast<cplx32 *>(c->W1), *w2 = reinterpret_cast<cplx32 *>(c->W2);
+    switch (kind) {
+      case 0: return mhd::launch_col_inverse(state_hi(c, 0), w1, d.n, b * 7, d.nk * d.nx, c->tw32, c->stream, tile);
+      case 1: return mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, c->tw32, c->stream, tile);
+      case 2: return mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw32, c->stream, tile);
+      default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw32, c->stream, tile);
+    }
+  };
+  const size_t elem = c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32);
+  const size_t pitch = (size_t)(d.n + d.n / (128 / (int)elem)) | 1;  // pencil pitch, as the kernels lay it out
+  int best[4];
+  double best_ms[4];
+  cudaError_t err = cudaSuccess;
+  for (int kind = 0; kind < 4 && err == cudaSuccess; ++kind) {
+    best[kind] = 0;
+    best_ms[kind] = 1e300;
+    const int max_tc = mhd::col_max_tile(d.n, kind < 2 ? +1 : -1, c->precision == MHD_FP64);
+    for (int tc = 1; tc <= max_tc && err == cudaSuccess; tc *= 2) {
+      if (tc * pitch * elem > 227 * 1024) break;
+      if ((err = run(kind, tc)) != cudaSuccess) break;  // warm-up (raises the shared-memory limit)
+      if ((err = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
+      for (int r = 0; r < reps && err == cudaSuccess; ++r) err = run(kind, tc);
+      if (err != cudaSuccess || (err = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
+      if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float t = 0.0f;
+      if ((err = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+      const double per = (double)t / reps;
+      if (per < best_ms[kind]) {
+        best_ms[kind] = per;
+        best[kind] = tc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(c, MHD_ECUDA, "autotune: %s", cudaGetErrorString(err));
+  for (int k = 0; k < 4; ++k) {
+    c->tile[k] = best[k];
+    if (tiles) tiles[k] = best[k];
+    if (ms) ms[k] = best_ms[k];
+  }
+  drop_graphs(c);
+  return MHD_OK;
+}
+
 mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   if (!c) return MHD_EINVAL;
   DeviceGuard g(c->device);

@@ -93,6 +93,9 @@ cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, 
                                const cplx32 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
                                const cplx32 *tw, cudaStream_t s, int tile = 0);
+// Largest power-of-two tile width (columns per block, <= 64) a column pass can launch with:
+// dir +1 inverse, -1 forward; fp64 the transform type; mixed_in an FP64 input to an FP32 inverse.
+int col_max_tile(int n, int dir, bool fp64, bool mixed_in = false);
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                double scale, const cplx64 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,

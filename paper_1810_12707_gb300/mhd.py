@@ -35,7 +35,7 @@ EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "
            "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
            "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
            "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing", "mhd_num_shells",
-           "mhd_spectra", "mhd_tracers_set", "mhd_tracers_get", "mhd_tracers_count")
+           "mhd_spectra", "mhd_tracers_set", "mhd_tracers_get", "mhd_tracers_count", "mhd_autotune")
 
 
 class MhdError(RuntimeError):
@@ -139,6 +139,8 @@ def load_library(path: str = LIBRARY):
     lib.mhd_pool_retire.argtypes = [P, I32, P, P, P, I32]
     lib.mhd_pool_info.restype = I32
     lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.mhd_autotune.restype = I32
+    lib.mhd_autotune.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
     lib.mhd_tracers_set.restype = I32
     lib.mhd_tracers_set.argtypes = [P, I32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
     lib.mhd_tracers_get.restype = I32
@@ -315,6 +317,16 @@ def mhd_step(ctx: Context, nsteps: int = 1) -> None:
 
 def mhd_set_option(ctx: Context, option: int, value: int) -> None:
     _check(ctx, load_library().mhd_set_option(ctx.handle, int(option), int(value)))
+
+
+def mhd_autotune(ctx: Context, reps: int = 5) -> dict:
+    """Time every tile width of the four column FFT passes and keep the fastest; returns
+    {"tiles": [4 widths], "ms": [4 mean ms per launch]} for (inverse z, inverse y, forward y,
+    forward z)."""
+    tiles = (ctypes.c_int32 * 4)()
+    ms = (ctypes.c_double * 4)()
+    _check(ctx, load_library().mhd_autotune(ctx.handle, int(reps), tiles, ms))
+    return {"tiles": list(tiles), "ms": list(ms)}
 
 
 def mhd_tracers_set(ctx: Context, inst: int, pos) -> None:
