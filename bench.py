@@ -110,6 +110,42 @@ def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
     return {key: (b * batch, f * batch) for key, (b, f) in m.items()}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu capture
+# per entry (summarised under profiles/).  A figure stands only while the sources that build the
+# kernel are the ones it was taken on: the entry keeps a hash of those files and is dropped
+# (traffic reported as null) as soon as they change.
+KERNEL_SOURCES = {
+    "flux_x": ("kernels_x.cu", "fft_device.cuh"),
+    "col": ("kernels_col.cu", "fft_device.cuh"),
+}
+TRAFFIC = {
+    # (kernel, n, batch, precision): (bytes per launch, source hash, capture)
+    ("flux_x", 256, 1, "fp64"): (632_891_392 + 1_030_445_000, "f1a038060e49a439",
+                                 "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
+    ("flux_x", 256, 1, "fp32"): (315_954_944 + 491_257_344, "f1a038060e49a439",
+                                 "ncu --set full, profiles/ncu_abc256_fp32.md"),
+}
+
+
+def sources_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1810_12707_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, n: int, batch: int, precision: str):
+    entry = TRAFFIC.get((kernel, n, batch, precision))
+    if entry is None:
+        return None, "no capture for this kernel and workload"
+    nbytes, digest, capture = entry
+    if digest != sources_hash("col" if kernel.startswith(("inverse", "forward")) else kernel):
+        return None, "kernel sources changed since the capture"
+    return nbytes, capture
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -276,10 +312,12 @@ def run_ours(args, name, cfg):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select exactly the timed launches
     e0.record(stream)
     for _ in range(K):
         mhd.mhd_step(ctx, 1)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -344,17 +382,18 @@ def run_ours(args, name, cfg):
                           "gbs": b / (avg * 1e-3) / 1e9, "tflops": f / (avg * 1e-3) / 1e12}
     top = max(per, key=lambda k: per[k]["share"])
     tb, tf = model[top]
+    traffic, traffic_src = measured_traffic(top, n, batch, cfg["precision"])
     t_mem = tb / (hbm * 1e9)
     t_alu = tf / (alu_peak * 1e12)
     if t_alu >= t_mem:
         roof = {"bound": "alu", "achieved": per[top]["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": per[top]["tflops"] / alu_peak, "traffic": None,
+                "frac": per[top]["tflops"] / alu_peak, "traffic": traffic,
                 "peak_source": ("FP64 FMA units x clock (nominal 1.25 TFLOP/s; probe 1.19)" if prec == mhd.MHD_FP64
                                 else "FP32 FMA units x clock (probe 74.4 TFLOP/s)")}
     else:
         roof = {"bound": "hbm", "achieved": per[top]["gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": per[top]["gbs"] / hbm, "traffic": None, "peak_source": f"{hbm_src} copy"}
-    roof.update({"kernel": top, "algorithmic_bytes": tb, "algorithmic_flops": tf,
+                "frac": per[top]["gbs"] / hbm, "traffic": traffic, "peak_source": f"{hbm_src} copy"}
+    roof.update({"kernel": top, "traffic_source": traffic_src, "algorithmic_bytes": tb, "algorithmic_flops": tf,
                  "achieved_gbs": per[top]["gbs"], "frac_hbm_of_measured": per[top]["gbs"] / hbm,
                  "step_model_bytes": sum(v[0] for v in model.values()),
                  "step_frac_hbm": sum(v[0] for v in model.values()) / (ms / K * 1e-3) / 1e9 / hbm})
