@@ -24,13 +24,30 @@ constexpr int kMaxThreads = 384;
 
 constexpr int pairs_for(int n) { return (n / 8) >= 16 ? 1 : 16 / (n / 8); }
 
-constexpr int threads_for(int n, int pencils) {
-  // groups of N/8 threads, at most kMaxThreads threads, a multiple of 32
+constexpr int threads_for(int n, int pencils, int max_threads = kMaxThreads) {
+  // groups of N/8 threads, at most max_threads threads, a multiple of 32
   int tpp = n / 8;
-  int g = kMaxThreads / tpp;
+  int g = max_threads / tpp;
+  if (g < 1) g = 1;
   if (g > pencils) g = pencils;
   int t = g * tpp;
   return (t + 31) / 32 * 32;
+}
+
+// Block size of the flux pass.  At N = 256 and 512 several smaller blocks per SM let one block
+// transform while another waits at a barrier (measured on GB300 over 96..384 threads: 128 best at
+// 256^3 in both precisions, 192 at 512^3); below, the pencil count caps the block at 192 threads.
+constexpr int flux_max_threads(int n) { return n == 256 ? 128 : n == 512 ? 192 : kMaxThreads; }
+template <int N>
+constexpr int flux_threads() {
+  return threads_for(N, 12 * pairs_for(N), flux_max_threads(N));
+}
+// Blocks per SM the register allocation is sized for: about 170 registers a thread in FP64 and 85
+// in FP32.
+template <int N, typename C>
+constexpr int flux_min_blocks() {
+  const int b = (sizeof(C) == 8 ? 768 : 384) / flux_threads<N>();
+  return b < 1 ? 1 : b;
 }
 
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
@@ -59,7 +76,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // bgrid (nullable): the grid magnetic field is also written out, [inst][3][N^3] in the data's
 // precision, for the tracer push.
 template <int N, typename C>
-__global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
+__global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
                               int K, int blocks_per_inst, const C *__restrict__ tw,
                               typename C::value_type *__restrict__ bgrid) {
@@ -76,7 +93,7 @@ __global__ void __launch_bounds__(kMaxThreads, sizeof(C) == 8 ? 2 : 1) flux_x_ke
   const int bl = blockIdx.x - inst * blocks_per_inst;
   const size_t row0 = (size_t)bl * PAIRS * 2;
   // the launch uses exactly this many threads, so every loop below has a constant trip count
-  constexpr int nthr = threads_for(N, 12 * PAIRS);
+  constexpr int nthr = flux_threads<N>();
 
   // 1. load and pack the 7 state fields: pencil (p, f) at sm + (p * 12 + f) * P.  Unrolled: all
   // of a thread's loads are issued before the first shared-memory store.
@@ -537,7 +554,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
     }
   }
   const int bpi = N * N / (2 * PAIRS);
-  const int threads = threads_for(N, 12 * PAIRS);
+  const int threads = flux_threads<N>();
   const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<flux_x_kernel<N, C>>((int)smem);
