@@ -120,9 +120,9 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     # (kernel, n, batch, precision): (bytes per launch, source hash, capture)
-    ("flux_x", 256, 1, "fp64"): (632_891_392 + 1_030_445_000, "f1a038060e49a439",
+    ("flux_x", 256, 1, "fp64"): (632_740_864 + 1_029_102_000, "57d75d8d4cd74517",
                                  "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
-    ("flux_x", 256, 1, "fp32"): (315_954_944 + 491_257_344, "f1a038060e49a439",
+    ("flux_x", 256, 1, "fp32"): (315_676_672 + 488_872_448, "57d75d8d4cd74517",
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
 }
 

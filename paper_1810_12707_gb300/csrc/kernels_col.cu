@@ -72,7 +72,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
     CO *dst = out + slab * (size_t)LOUT * cols + col;
     for (int l = l0; l < LOUT; l += TPP) {
       CC v = pen[sm_idx<CC>(DIR > 0 ? l : kept_to_fft(l, K, N))];
-      if (DIR < 0) v = c_scale(v, scale);
+      if (DIR < 0 && scale != (typename CC::value_type)1) v = c_scale(v, scale);
       dst[(size_t)l * cols] = c_cvt<CO>(v);
     }
   }

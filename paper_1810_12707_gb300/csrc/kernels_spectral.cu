@@ -458,7 +458,8 @@ cudaError_t launch_assemble(const cplx64 *flux, const cplx64 *y_in, cplx64 *stat
                             cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op, int stage,
                             const Dims &d, cudaStream_t s, const cplx64 *force) {
   const size_t total = d.spec * d.batch;
-  const double inv_n3 = 1.0 / ((double)d.n * d.n * d.n);
+  // the flux passes leave their spectra doubled (the split's 1/2 is taken here)
+  const double inv_n3 = 0.5 / ((double)d.n * d.n * d.n);
   assemble_kernel<cplx64><<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, state, hist, ystage, rhs_out, phys, coef,
                                                                force, op, stage, d.k, d.batch, inv_n3);
   return cudaGetLastError();
@@ -478,7 +479,7 @@ cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s
                                cplx32 *ystage, cplx64 *rhs_out, const PhysDev *phys, const StepCoef *coef, int op,
                                int stage, const Dims &d, cudaStream_t s, const cplx32 *force) {
   const size_t total = d.spec * d.batch;
-  const float inv_n3 = (float)(1.0 / ((double)d.n * d.n * d.n));
+  const float inv_n3 = (float)(0.5 / ((double)d.n * d.n * d.n));  // with the split's 1/2
   assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, s_hi, s_lo, hist, ystage, rhs_out, phys, coef,
                                                           force, op, stage, d.k, d.batch, inv_n3);
   return cudaGetLastError();

@@ -8,6 +8,8 @@
 // spectra): Z = FFT(row0 + i row1), X0[k] = (Z[k] + conj Z[N-k]) / 2 and
 // X1[k] = -i (Z[k] - conj Z[N-k]) / 2, kept for k = 0..K only.
 //
+// The flux passes store 2 X0 and 2 X1 (the factor 1/2 of the split is left to the assembly, which
+// scales the product spectra by 1/(2 N^3): a power of two, so the results are the same bits).
 // The flux kernel is the fused pass of the method: the 7 state fields of a block's rows are
 // brought to the grid, the 12 products of the RHS are formed pointwise in shared memory (no
 // real-space array ever reaches HBM), and their forward transforms leave as truncated half
@@ -182,7 +184,6 @@ __global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) 
   fft_pencils<N, -1>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
 
   // 5. unpack and store the kept half spectra
-  const R half = (R)0.5;
   for (int q = threadIdx.x; q < 12 * PAIRS * NX; q += nthr) {
     const int k = q % NX;
     const int r = q / NX;
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) 
     const C *pen = sm + (p * 12 + f) * P;
     const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
     C *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
-    dst[k] = C{half * (z.re + zc.re), half * (z.im - zc.im)};
-    dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
+    dst[k] = C{z.re + zc.re, z.im - zc.im};
+    dst[NX + k] = C{z.im + zc.im, zc.re - z.re};
   }
 
   const R m = block_nan_max(smax, reinterpret_cast<R *>(red));
@@ -334,14 +335,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     fft_pencils<N, -1>(12, [&](int id) { return sm + id * P; }, tw);
 
     // 5. unpack and store
-    const R half = (R)0.5;
-    for (int q = tx; q < 12 * NX; q += nthr) {
+      for (int q = tx; q < 12 * NX; q += nthr) {
       const int k = q % NX, f = q / NX;
       const C *pen = sm + f * P;
       const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
       C *dst = out + ((size_t)(inst * 12 + f) * NN + row0) * NX;
-      dst[k] = C{half * (z.re + zc.re), half * (z.im - zc.im)};
-      dst[NX + k] = C{half * (z.im + zc.im), half * (zc.re - z.re)};
+      dst[k] = C{z.re + zc.re, z.im - zc.im};
+      dst[NX + k] = C{z.im + zc.im, zc.re - z.re};
     }
 
     // CFL maximum of this pair: warp maximum, one atomic per warp
