@@ -376,10 +376,9 @@ __global__ void step_dt_kernel(unsigned long long *__restrict__ smax_bits, const
 // spectral terms.  out: [0] ke [1] me [2] eint [3] cross_hel [4] mean_speed [5] mean_bmag
 // [6] smax [7] mean_rho [8..10] mean_m [11..13] mean_b [14] divb_rms [15] t [16] dt_last
 // [17] step [18] status.
-__global__ void diag_finish_kernel(const double *__restrict__ part, int nparts,
-                                   const cplx64 *__restrict__ state, const PhysDev *__restrict__ phys,
-                                   const TimeState *__restrict__ ts, double *__restrict__ out, int n,
-                                   int K) {
+__global__ void diag_finish_kernel(const double *__restrict__ part, int nparts, const double *__restrict__ dpart,
+                                   int ndparts, const cplx64 *__restrict__ state, const PhysDev *__restrict__ phys,
+                                   const TimeState *__restrict__ ts, double *__restrict__ out, int n, int K) {
   __shared__ double red[32];
   const double inv_n3 = 1.0 / ((double)n * n * n);
   for (int q = 0; q < 7; ++q) {
@@ -393,21 +392,12 @@ __global__ void diag_finish_kernel(const double *__restrict__ part, int nparts,
     }
     if (threadIdx.x == 0) out[q] = q < 6 ? v * inv_n3 : v;
   }
-  // sum over the full spectrum of |k . B|^2 (kx > 0 counted twice for the mirrored half)
-  const int NX = K + 1, NK = 2 * K + 1;
-  const size_t spec = (size_t)NK * NK * NX;
   double d = 0.0;
-  for (size_t m = threadIdx.x; m < spec; m += blockDim.x) {
-    const int kxi = (int)(m % NX);
-    const size_t t = m / NX;
-    const double kx = kxi, ky = kept_wave((int)(t % NK), K), kz = kept_wave((int)(t / NK), K);
-    const cplx64 bx = state[4 * spec + m], by = state[5 * spec + m], bz = state[6 * spec + m];
-    const double re = kx * bx.re + ky * by.re + kz * bz.re;
-    const double im = kx * bx.im + ky * by.im + kz * bz.im;
-    d += (kxi > 0 ? 2.0 : 1.0) * (re * re + im * im);
-  }
+  for (int i = threadIdx.x; i < ndparts; i += blockDim.x) d += dpart[i];
   d = block_sum(d, red);
   if (threadIdx.x == 0) {
+    const int NX = K + 1, NK = 2 * K + 1;
+    const size_t spec = (size_t)NK * NK * NX;
     out[7] = state[0].re;
     for (int a = 0; a < 3; ++a) {
       out[8 + a] = state[(1 + a) * spec].re;
@@ -419,6 +409,27 @@ __global__ void diag_finish_kernel(const double *__restrict__ part, int nparts,
     out[17] = (double)ts->step;
     out[18] = (double)ts->status;
   }
+}
+
+// Partial sums of |k . B_hat|^2 over the full spectrum (k_x > 0 counted twice for the mirrored
+// half), one per block over a fixed grid-stride share of the kept modes.
+__global__ void __launch_bounds__(256) divb_partials_kernel(const cplx64 *__restrict__ state,
+                                                            double *__restrict__ dpart, int K) {
+  __shared__ double red[32];
+  const int NX = K + 1, NK = 2 * K + 1;
+  const int spec = NK * NK * NX;  // < 2^31 for every supported N
+  double d = 0.0;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < spec; m += gridDim.x * blockDim.x) {
+    const int kxi = m % NX;
+    const int t = m / NX;
+    const double kx = kxi, ky = kept_wave(t % NK, K), kz = kept_wave(t / NK, K);
+    const cplx64 bx = state[4 * (size_t)spec + m], by = state[5 * (size_t)spec + m], bz = state[6 * (size_t)spec + m];
+    const double re = kx * bx.re + ky * by.re + kz * bz.re;
+    const double im = kx * bx.im + ky * by.im + kz * bz.im;
+    d += (kxi > 0 ? 2.0 : 1.0) * (re * re + im * im);
+  }
+  d = block_sum(d, red);
+  if (threadIdx.x == 0) dpart[blockIdx.x] = d;
 }
 
 // Truncated spectrum -> full half-complex layout [N][N][N/2+1], zeros outside the kept set.
@@ -503,8 +514,11 @@ cudaError_t launch_step_dt(unsigned long long *smax_bits, const PhysDev *phys, T
 }
 
 cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state, const PhysDev *phys,
-                               const TimeState *ts, double *out, const Dims &d, cudaStream_t s) {
-  diag_finish_kernel<<<1, 1024, 0, s>>>(part, nparts, state, phys, ts, out, d.n, d.k);
+                               const TimeState *ts, double *out, const Dims &d, cudaStream_t s, double *dpart) {
+  divb_partials_kernel<<<kDivbBlocks, 256, 0, s>>>(state, dpart, d.k);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_finish_kernel<<<1, 1024, 0, s>>>(part, nparts, dpart, kDivbBlocks, state, phys, ts, out, d.n, d.k);
   return cudaGetLastError();
 }
 

@@ -357,29 +357,31 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // Forward x transform of an initial state (m = rho u formed first)
 // ------------------------------------------------------------------------------------------
 template <int N>
+// Rows from `row_begin` on (a multiple of 2 PAIRS); the real arrays hold rows from `row_begin`
+// with field stride `fstride` (N^3 for whole fields, less for a slab of z-planes).
 __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__restrict__ rho, const double *__restrict__ u,
                              const double *__restrict__ b, cplx64 *__restrict__ out, int K,
-                             const cplx64 *__restrict__ tw) {
+                             const cplx64 *__restrict__ tw, size_t row_begin, size_t fstride) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
-  constexpr size_t NN = (size_t)N * N, N3 = NN * N;
+  constexpr size_t NN = (size_t)N * N;
   constexpr int NX = KT + 1;
-  const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
+  const size_t row0 = row_begin + (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
-    const size_t i0 = (row0 + 2 * p) * N + j, i1 = i0 + N;
+    const size_t i0 = (row0 - row_begin + 2 * p) * N + j, i1 = i0 + N;
     const double r0 = rho[i0], r1 = rho[i1];
     cplx64 *pen = sm + p * 7 * P + sm_idx<cplx64>(j);
     pen[0] = cplx64{r0, r1};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      pen[(1 + d) * P] = cplx64{r0 * u[d * N3 + i0], r1 * u[d * N3 + i1]};
-      pen[(4 + d) * P] = cplx64{b[d * N3 + i0], b[d * N3 + i1]};
+      pen[(1 + d) * P] = cplx64{r0 * u[d * fstride + i0], r1 * u[d * fstride + i1]};
+      pen[(4 + d) * P] = cplx64{b[d * fstride + i0], b[d * fstride + i1]};
     }
   }
   __syncthreads();
@@ -400,16 +402,17 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
 // Inverse x transform to real rows
 // ------------------------------------------------------------------------------------------
 template <int N>
+// Rows from `row_begin` on; `out` holds rows from `row_begin` with field stride `fstride`.
 __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__restrict__ in, double *__restrict__ out, int nf, int K,
-                             const cplx64 *__restrict__ tw) {
+                             const cplx64 *__restrict__ tw, size_t row_begin, size_t fstride) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
   constexpr int P = pencil_pitch<cplx64>(N);
   constexpr int PAIRS = pairs_for(N);
-  constexpr size_t NN = (size_t)N * N, N3 = NN * N;
+  constexpr size_t NN = (size_t)N * N;
   constexpr int NX = KT + 1;
-  const size_t row0 = (size_t)blockIdx.x * PAIRS * 2;
+  const size_t row0 = row_begin + (size_t)blockIdx.x * PAIRS * 2;
   const int nthr = blockDim.x;
 
   for (int q = threadIdx.x; q < nf * PAIRS * NX; q += nthr) {
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     const int r = q / N;
     const int f = r % nf, p = r / nf;
     const cplx64 z = sm[(p * nf + f) * P + sm_idx<cplx64>(j)];
-    const size_t i0 = f * N3 + (row0 + 2 * p) * N + j;
+    const size_t i0 = f * fstride + (row0 - row_begin + 2 * p) * N + j;
     out[i0] = z.re;
     out[i0 + N] = z.im;
   }
@@ -567,30 +570,35 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
 
 template <int N>
 cudaError_t set_n(const double *rho, const double *u, const double *b, cplx64 *out, const Dims &d,
-                  const cplx64 *tw, cudaStream_t s) {
+                  const cplx64 *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
   constexpr int PAIRS = pairs_for(N);
-  const int blocks = N * N / (2 * PAIRS);
+  if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
+  const int blocks = (int)(nrows / (2 * PAIRS));
+  if (blocks == 0) return cudaSuccess;
   const int threads = threads_for(N, 7 * PAIRS);
   const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<set_x_kernel<N>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  set_x_kernel<N><<<blocks, threads, smem, s>>>(rho, u, b, out, d.k, tw);
+  set_x_kernel<N><<<blocks, threads, smem, s>>>(rho, u, b, out, d.k, tw, row_begin, fstride);
   return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cplx64 *tw, cudaStream_t s) {
+cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cplx64 *tw, cudaStream_t s,
+                  size_t row_begin, size_t nrows, size_t fstride) {
   constexpr int PAIRS = pairs_for(N);
-  const int blocks = N * N / (2 * PAIRS);
+  if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
+  const int blocks = (int)(nrows / (2 * PAIRS));
+  if (blocks == 0) return cudaSuccess;
   const int threads = threads_for(N, nf * PAIRS);
   const size_t smem = (size_t)nf * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<get_x_kernel<N>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  get_x_kernel<N><<<blocks, threads, smem, s>>>(in, out, nf, d.k, tw);
+  get_x_kernel<N><<<blocks, threads, smem, s>>>(in, out, nf, d.k, tw, row_begin, fstride);
   return cudaGetLastError();
 }
 
@@ -638,12 +646,24 @@ cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, un
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,
                          const Dims &d, const cplx64 *tw, cudaStream_t s) {
-  MHD_DISPATCH_N(d.n, (set_n<N>(rho, u, b, out, d, tw, s)));
+  const size_t nn = (size_t)d.n * d.n;
+  MHD_DISPATCH_N(d.n, (set_n<N>(rho, u, b, out, d, tw, s, 0, nn, nn * d.n)));
+}
+
+cudaError_t launch_set_x_rows(const double *rho, const double *u, const double *b, cplx64 *out, const Dims &d,
+                              const cplx64 *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
+  MHD_DISPATCH_N(d.n, (set_n<N>(rho, u, b, out, d, tw, s, row_begin, nrows, fstride)));
 }
 
 cudaError_t launch_get_x(const cplx64 *in, double *out, int nfields, const Dims &d,
                          const cplx64 *tw, cudaStream_t s) {
-  MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s)));
+  const size_t nn = (size_t)d.n * d.n;
+  MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s, 0, nn, nn * d.n)));
+}
+
+cudaError_t launch_get_x_rows(const cplx64 *in, double *out, int nfields, const Dims &d, const cplx64 *tw,
+                              cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
+  MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s, row_begin, nrows, fstride)));
 }
 
 cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,

@@ -66,6 +66,9 @@ struct mhd_ctx {
   void *bgrid = nullptr;
   int tile[4] = {0, 0, 0, 0};
   cudaStream_t cap_stream = nullptr;
+  // host-pointer set/get: a copy stream and the events that hand staging slots between streams
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   cudaGraphExec_t graph_exec = nullptr;
   // serving pools: only the first `live` instances are stepped (-1: all), one graph per count
   int live = -1;
@@ -153,7 +156,8 @@ size_t footprint(const mhd::Dims &d, int precision) {
   const Sizes s = sizes_for(d, precision);
   return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + d.n * sizeof(cplx32) + s.part * sizeof(double) +
          (precision == MHD_FP64 ? 0 : 7 * d.spec * sizeof(cplx64)) +
-         d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) + 64 * sizeof(double);
+         d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) +
+         (64 + mhd::kDivbBlocks) * sizeof(double);
 }
 
 void *dalloc(mhd_ctx *c, size_t bytes) {
@@ -306,6 +310,9 @@ void mhd_destroy(mhd_ctx *ctx) {
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : {ctx->ev_start, ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1]})
+      if (e) cudaEventDestroy(e);
     free_all(ctx);
   }
   delete ctx;
@@ -362,7 +369,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
   ok = ok && (c->phys = (mhd::PhysDev *)dalloc(c, p->batch * sizeof(mhd::PhysDev))) != nullptr;
-  ok = ok && (c->diag_out = (double *)dalloc(c, 32 * sizeof(double))) != nullptr;
+  ok = ok && (c->diag_out = (double *)dalloc(c, (32 + mhd::kDivbBlocks) * sizeof(double))) != nullptr;
   ok = ok && (c->flag = (int32_t *)dalloc(c, 4 * sizeof(int32_t))) != nullptr;
   if (!ok) {
     free_all(c);
@@ -392,6 +399,132 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   return MHD_OK;
 }
 
+}  // extern "C"
+
+// ---- host-pointer transfers, pipelined over slabs of z-planes ----
+// The 7 real fields of one instance cross the host link slab by slab on a second stream while the
+// context's stream transforms the slab before (x and y passes); two staging slots live in W1
+// behind the y-pass output, so nothing is allocated.
+namespace {
+
+struct SlabPlan {
+  int dz;           // z-planes per slab
+  double *slot[2];  // 7 fields x dz N^2 doubles each
+};
+
+bool slab_plan(mhd_ctx *c, SlabPlan *pl) {
+  const mhd::Dims &d = c->d;
+  const size_t n = d.n, nn = n * n;
+  const size_t head = (7 * n * d.nk * d.nx + 15) / 16 * 16;  // y-pass output, complex values
+  if (head >= c->w1_len) return false;
+  const size_t avail = (c->w1_len - head) * 2;  // doubles
+  int dz = (int)(n / 8);
+  while (dz > 1 && (size_t)14 * dz * nn > avail) dz /= 2;
+  if ((size_t)14 * dz * nn > avail) return false;
+  pl->dz = dz;
+  pl->slot[0] = reinterpret_cast<double *>(c->W1 + head);
+  pl->slot[1] = pl->slot[0] + (size_t)7 * dz * nn;
+  return true;
+}
+
+mhd_status ensure_copy_stream(mhd_ctx *c) {
+  if (c->copy_stream) return MHD_OK;
+  CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaEventCreateWithFlags(&c->ev_full[i], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
+  }
+  return MHD_OK;
+}
+
+// Host rho, u, B -> truncated spectra `Si` (FP64) of one instance.  Returns MHD_EINVAL without
+// queueing anything when no staging plan fits (the caller then takes the unpipelined path).
+mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const double *b, cplx64 *Si) {
+  SlabPlan pl;
+  if (!slab_plan(c, &pl)) return MHD_EINVAL;
+  mhd_status st = ensure_copy_stream(c);
+  if (st) return st;
+  const mhd::Dims &d = c->d;
+  const mhd::Dims d1 = one(c);
+  const int n = d.n;
+  const size_t nn = (size_t)n * n, n3 = nn * n;
+  cudaError_t e = cudaEventRecord(c->ev_start, c->stream);  // the staging slots are free from here
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0);
+  int i = 0;
+  for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
+    const int dzc = std::min(pl.dz, n - z0), k = i & 1;
+    double *slot = pl.slot[k];
+    const size_t off = (size_t)z0 * nn, cnt = (size_t)dzc * nn;
+    if (i >= 2) e = cudaStreamWaitEvent(c->copy_stream, c->ev_free[k], 0);
+    for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+      const double *src = f == 0 ? rho + off : f < 4 ? u + (f - 1) * n3 + off : b + (f - 4) * n3 + off;
+      e = cudaMemcpyAsync(slot + f * cnt, src, cnt * sizeof(double), cudaMemcpyHostToDevice, c->copy_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_full[k], c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_full[k], 0);
+    if (e == cudaSuccess)
+      e = mhd::launch_set_x_rows(slot, slot + cnt, slot + 4 * cnt, c->W2, d1, c->tw, c->stream, (size_t)z0 * n,
+                                 (size_t)dzc * n, cnt);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_free[k], c->stream);
+    for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+      const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
+      e = mhd::launch_col_forward(c->W2 + slab0 * n * d.nx, c->W1 + slab0 * d.nk * d.nx, n, dzc, d.nx, 1.0, c->tw,
+                                  c->stream);
+    }
+  }
+  if (e == cudaSuccess) e = mhd::launch_col_forward(c->W1, Si, n, 7, d.nk * d.nx, 1.0 / (double)n3, c->tw, c->stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(c->copy_stream);  // the host buffers must outlive the copies in flight
+    return fail(c, MHD_ECUDA, "set_state: %s", cudaGetErrorString(e));
+  }
+  return MHD_OK;
+}
+
+// Truncated FP64 spectra `src` of one instance -> host rho, m, B.  MHD_EINVAL (nothing queued)
+// when no staging plan fits.
+mhd_status get_state_host(mhd_ctx *c, const cplx64 *src, double *rho, double *m, double *b) {
+  SlabPlan pl;
+  if (!slab_plan(c, &pl)) return MHD_EINVAL;
+  mhd_status st = ensure_copy_stream(c);
+  if (st) return st;
+  const mhd::Dims &d = c->d;
+  const mhd::Dims d1 = one(c);
+  const int n = d.n;
+  const size_t nn = (size_t)n * n, n3 = nn * n;
+  cudaError_t e = mhd::launch_col_inverse(src, c->W1, n, 7, d.nk * d.nx, c->tw, c->stream);  // z pass
+  int i = 0;
+  for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
+    const int dzc = std::min(pl.dz, n - z0), k = i & 1;
+    double *slot = pl.slot[k];
+    const size_t off = (size_t)z0 * nn, cnt = (size_t)dzc * nn;
+    if (i >= 2) e = cudaStreamWaitEvent(c->stream, c->ev_free[k], 0);  // slot copied out
+    for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+      const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
+      e = mhd::launch_col_inverse(c->W1 + slab0 * d.nk * d.nx, c->W2 + slab0 * n * d.nx, n, dzc, d.nx, c->tw,
+                                  c->stream);
+    }
+    if (e == cudaSuccess)
+      e = mhd::launch_get_x_rows(c->W2, slot, 7, d1, c->tw, c->stream, (size_t)z0 * n, (size_t)dzc * n, cnt);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_full[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_full[k], 0);
+    for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+      double *dst = f == 0 ? rho + off : f < 4 ? m + (f - 1) * n3 + off : b + (f - 4) * n3 + off;
+      e = cudaMemcpyAsync(dst, slot + f * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_free[k], c->copy_stream);
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(c->copy_stream);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, MHD_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const double *u, const double *b,
                          int32_t on_device) {
   mhd_status st = check_inst(c, inst);
@@ -400,21 +533,25 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
   DeviceGuard g(c->device);
   const mhd::Dims &d = c->d;
   const size_t n3 = (size_t)d.n * d.n * d.n;
-  const double *r = rho, *uu = u, *bb = b;
-  if (!on_device) {
-    double *real = reinterpret_cast<double *>(c->W1);
-    CK(cudaMemcpyAsync(real, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(real + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(real + 4 * n3, b, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    r = real;
-    uu = real + n3;
-    bb = real + 4 * n3;
-  }
   const bool fp64 = c->precision == MHD_FP64;
   cplx64 *Si = fp64 ? state64(c, inst) : c->S64;
-  CK(mhd::launch_set_x(r, uu, bb, c->W2, one(c), c->tw, c->stream));
-  CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 7 * d.n, d.nx, 1.0, c->tw, c->stream));
-  CK(mhd::launch_col_forward(c->W1, Si, d.n, 7, d.nk * d.nx, 1.0 / ((double)n3), c->tw, c->stream));
+  if (!on_device && (st = set_state_host(c, rho, u, b, Si)) != MHD_EINVAL) {
+    if (st) return st;
+  } else {
+    const double *r = rho, *uu = u, *bb = b;
+    if (!on_device) {
+      double *real = reinterpret_cast<double *>(c->W1);
+      CK(cudaMemcpyAsync(real, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(real + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemcpyAsync(real + 4 * n3, b, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      r = real;
+      uu = real + n3;
+      bb = real + 4 * n3;
+    }
+    CK(mhd::launch_set_x(r, uu, bb, c->W2, one(c), c->tw, c->stream));
+    CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 7 * d.n, d.nx, 1.0, c->tw, c->stream));
+    CK(mhd::launch_col_forward(c->W1, Si, d.n, 7, d.nk * d.nx, 1.0 / ((double)n3), c->tw, c->stream));
+  }
   if (fp64) {
     CK(cudaMemsetAsync(c->H + (size_t)inst * 7 * d.spec, 0, 7 * d.spec * sizeof(cplx64), c->stream));
   } else {
@@ -435,6 +572,7 @@ mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, doubl
   DeviceGuard g(c->device);
   const cplx64 *src = nullptr;
   if ((st = state_fp64(c, inst, &src))) return st;
+  if (!on_device && (st = get_state_host(c, src, rho, m, b)) != MHD_EINVAL) return st;
   return spectra_to_real(c, src, rho, m, b, on_device);
 }
 
@@ -958,7 +1096,7 @@ mhd_status mhd_diagnostics(mhd_ctx *c, int32_t inst, mhd_diag *out) {
   if ((st = inverse_zy(c, Si))) return st;
   CK(mhd::launch_diag_x(c->W2, c->phys + inst, c->part, d, c->tw, c->stream));
   CK(mhd::launch_diag_finish(c->part, mhd::diag_x_blocks(d.n), Si, c->phys + inst, c->ts + inst, c->diag_out, d,
-                             c->stream));
+                             c->stream, c->diag_out + 32));
   double h[24];
   CK(cudaMemcpyAsync(h, c->diag_out, 19 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -123,6 +123,14 @@ cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cp
 // real [f][N^3].
 cudaError_t launch_get_x(const cplx64 *in, double *out, int nfields, const Dims &d,
                          const cplx64 *tw, cudaStream_t s);
+// The same two x passes over rows [row_begin, row_begin + nrows) only (a slab of z-planes: row =
+// z N + y), with the real arrays holding just those rows, field stride `fstride` doubles.
+// row_begin and nrows must be multiples of the kernels' row-pair block (N >= 16: a multiple of N
+// suffices).
+cudaError_t launch_set_x_rows(const double *rho, const double *u, const double *b, cplx64 *out, const Dims &d,
+                              const cplx64 *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride);
+cudaError_t launch_get_x_rows(const cplx64 *in, double *out, int nfields, const Dims &d, const cplx64 *tw,
+                              cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride);
 // Inverse x pass of the 7 state fields of one instance with per-block partial sums of the grid
 // diagnostics: part[block][8] = (sum ke, me, eint, u.B, |u|, |B|, max s, unused).
 cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,
@@ -190,9 +198,11 @@ cudaError_t launch_tracer_push(const double *bgrid, double *tr, long long count,
 cudaError_t launch_tracer_push(const float *bgrid, double *tr, long long count, const StepCoef *coef, int n,
                                cudaStream_t s);
 
+// dpart: kDivbBlocks doubles of scratch for the partial sums of the div B norm.
+constexpr int kDivbBlocks = 2 * 152;
 cudaError_t launch_diag_finish(const double *part, int nparts, const cplx64 *state,
                                const PhysDev *phys, const TimeState *ts, double *out,
-                               const Dims &d, cudaStream_t s);
+                               const Dims &d, cudaStream_t s, double *dpart);
 
 // Expand one truncated spectrum to the full half-complex layout [N][N][N/2+1] (zeros outside).
 cudaError_t launch_expand_spectrum(const cplx64 *in, cplx64 *out, const Dims &d, cudaStream_t s);
