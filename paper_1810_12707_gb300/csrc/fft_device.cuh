@@ -7,6 +7,8 @@
 
 #include "mhd_internal.h"
 
+#include <type_traits>
+
 namespace mhd {
 
 template <typename C>
@@ -149,6 +151,97 @@ __device__ __forceinline__ void group_sync() {
   }
 }
 
+// ---- FP64 twiddles in FMA form ----
+// On GB300 the FP64 pipe bounds the FP64 transforms, so their twiddled stages use fewer FP64
+// instructions: every twiddle is kept as W = i^q c (1 + i t) with |t| <= 1, and a radix-2
+// butterfly (a + W x, a - W x) costs six fused multiply-adds: z = x + i t x (two), z' = i^q z (an
+// exact swap and sign change done with integer operations), a +- c z' (four).  The table follows
+// the classic one in the same allocation: tw[0..N) classic W_N^m, then N pairs (c, t), then N
+// bytes q (fp64_twiddle_bytes).
+struct TwF {
+  double c, t;
+  int q;
+};
+
+template <int N, int DIR>
+__device__ __forceinline__ TwF twf_load(const cplx64 *__restrict__ tw, int m) {
+  const double *ct = reinterpret_cast<const double *>(tw + N) + 2 * m;
+  const unsigned char *qt = reinterpret_cast<const unsigned char *>(tw + 2 * N) + m;
+  TwF w;
+  unsigned short qq;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(w.c), "=d"(w.t) : "l"(ct));
+  asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(qq) : "l"(qt));
+  w.q = qq;
+  if (DIR > 0) {  // the inverse uses conj(W) = i^-q c (1 - i t)
+    w.t = -w.t;
+    w.q = (4 - w.q) & 3;
+  }
+  return w;
+}
+
+// The same twiddle turned by a quarter DIR i (the factor omega_4 of the DIF split).
+template <int DIR>
+__device__ __forceinline__ TwF twf_quarter(TwF w) {
+  w.q = (w.q + (DIR < 0 ? 3 : 1)) & 3;
+  return w;
+}
+
+__device__ __forceinline__ double flip_sign(double x, unsigned s) {
+  return __hiloint2double(__double2hiint(x) ^ (int)s, __double2loint(x));
+}
+
+// i^q z, exactly, with integer selects and sign flips.
+__device__ __forceinline__ cplx64 rot_quarter(cplx64 z, int q) {
+  const bool sw = q & 1;
+  const double a = sw ? z.im : z.re, b = sw ? z.re : z.im;
+  const unsigned s_re = (unsigned)((q ^ (q >> 1)) & 1) << 31, s_im = (unsigned)((q >> 1) & 1) << 31;
+  return cplx64{flip_sign(a, s_re), flip_sign(b, s_im)};
+}
+
+// (x0, x1) <- (x0 + W x1, x0 - W x1)
+__device__ __forceinline__ void bfly_fma(cplx64 &x0, cplx64 &x1, const TwF &w) {
+  const cplx64 z = rot_quarter(cplx64{fma(-w.t, x1.im, x1.re), fma(w.t, x1.re, x1.im)}, w.q);
+  const cplx64 a = x0;
+  x0 = cplx64{fma(w.c, z.re, a.re), fma(w.c, z.im, a.im)};
+  x1 = cplx64{fma(-w.c, z.re, a.re), fma(-w.c, z.im, a.im)};
+}
+
+// Length-R DFT of (W^r x_r)_r, r < R, for R = 8, 4, 2, W = W_N^m in DIR's sense, as radix-2
+// layers of the decimation-in-frequency split with every twiddle carried into the butterflies:
+//   R = 8: layer 1 W^4 (x4); layer 2 W^2 (x2) and (W w8)^2 = W^2 w4 (x2); layer 3 W, W w4, W w8,
+//          W w8 w4, with w8 = W_N^(N/8) and w4 = w8^2 a quarter turn.
+// Results in natural order in v.
+template <int N, int R, int DIR>
+__device__ __forceinline__ void dft_twiddled_fma(cplx64 *v, int m, const cplx64 *__restrict__ tw) {
+  if constexpr (R == 8) {
+    const TwF w1 = twf_load<N, DIR>(tw, m), w2 = twf_load<N, DIR>(tw, 2 * m), w4 = twf_load<N, DIR>(tw, 4 * m);
+    const TwF w18 = twf_load<N, DIR>(tw, m + N / 8);  // W w8
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bfly_fma(v[j], v[j + 4], w4);  // P'_j = v_j, Q'_j = v_j+4
+    const TwF w2q = twf_quarter<DIR>(w2);
+    bfly_fma(v[0], v[2], w2);   // PP'_0, PQ'_0
+    bfly_fma(v[1], v[3], w2);   // PP'_1, PQ'_1
+    bfly_fma(v[4], v[6], w2q);  // QP'_0, QQ'_0
+    bfly_fma(v[5], v[7], w2q);  // QP'_1, QQ'_1
+    bfly_fma(v[0], v[1], w1);                     // X0, X4
+    bfly_fma(v[2], v[3], twf_quarter<DIR>(w1));   // X2, X6
+    bfly_fma(v[4], v[5], w18);                    // X1, X5
+    bfly_fma(v[6], v[7], twf_quarter<DIR>(w18));  // X3, X7
+    const cplx64 x0 = v[0], x4 = v[1], x2 = v[2], x6 = v[3], x1 = v[4], x5 = v[5], x3 = v[6], x7 = v[7];
+    v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
+  } else if constexpr (R == 4) {
+    const TwF w1 = twf_load<N, DIR>(tw, m), w2 = twf_load<N, DIR>(tw, 2 * m);
+    bfly_fma(v[0], v[2], w2);  // P'_0, Q'_0
+    bfly_fma(v[1], v[3], w2);  // P'_1, Q'_1
+    bfly_fma(v[0], v[1], w1);                    // X0, X2
+    bfly_fma(v[2], v[3], twf_quarter<DIR>(w1));  // X1, X3
+    const cplx64 x0 = v[0], x2 = v[1], x1 = v[2], x3 = v[3];
+    v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3;
+  } else {
+    bfly_fma(v[0], v[1], twf_load<N, DIR>(tw, m));
+  }
+}
+
 // ---- Stockham pencil FFT ----
 //
 // The transform of length N = product of radices (8 while at least 8 points remain, then 4 or
@@ -170,6 +263,9 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
     constexpr int NB = 8 / R;
     constexpr int TPP = N / 8;
     constexpr int TWSTEP = N / (NS * R);
+    // FP64 stages with twiddles take them inside the butterflies (FMA form, fewer FP64
+    // instructions); the others multiply on load.
+    constexpr bool kFma = std::is_same<C, cplx64>::value && NS > 1;
     C v[8];
     if (active) {
 #pragma unroll
@@ -179,7 +275,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           C x = buf[sm_idx<C>(j + r * (N / R))];
-          if (NS > 1 && r > 0) {
+          if (!kFma && NS > 1 && r > 0) {
             const C w = tw_load(tw + r * k * TWSTEP);
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
           }
@@ -191,7 +287,12 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
     if (active) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        dft_small<R, DIR, C>(v + b * R);
+        if constexpr (kFma) {
+          dft_twiddled_fma<N, R, DIR>(reinterpret_cast<cplx64 *>(v) + b * R, ((t + b * TPP) % NS) * TWSTEP,
+                                      reinterpret_cast<const cplx64 *>(tw));
+        } else {
+          dft_small<R, DIR, C>(v + b * R);
+        }
         const int j = t + b * TPP;
         const int k = j % NS;
         const int base = (j / NS) * NS * R + k;

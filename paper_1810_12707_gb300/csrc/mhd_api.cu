@@ -154,7 +154,8 @@ Sizes sizes_for(const mhd::Dims &d, int precision) {
 
 size_t footprint(const mhd::Dims &d, int precision) {
   const Sizes s = sizes_for(d, precision);
-  return (2 * s.S + s.W1 + s.W2 + d.n) * sizeof(cplx64) + d.n * sizeof(cplx32) + s.part * sizeof(double) +
+  return (2 * s.S + s.W1 + s.W2) * sizeof(cplx64) + mhd::fp64_twiddle_size(d.n) + d.n * sizeof(cplx32) +
+         s.part * sizeof(double) +
          (precision == MHD_FP64 ? 0 : 7 * d.spec * sizeof(cplx64)) +
          d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) +
          (64 + mhd::kDivbBlocks) * sizeof(double);
@@ -189,38 +190,6 @@ void free_all(mhd_ctx *c) {
     else cudaFree(p);
   }
   c->allocs.clear();
-}
-
-// W_N^m = exp(-2 pi i m / N) for m < N from first-octant values and exact symmetries, so that
-// W^{N/4} = -i, W^{N/2} = -1 and W^{3N/4} = i hold exactly.
-std::vector<cplx64> twiddles(int n) {
-  const int q4 = n / 4, q8 = n / 8;
-  std::vector<long double> C(q8 + 1), Sn(q8 + 1);
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int r = 0; r <= q8; ++r) {
-    C[r] = cosl(two_pi * r / n);
-    Sn[r] = sinl(two_pi * r / n);
-  }
-  C[0] = 1.0L;
-  Sn[0] = 0.0L;
-  std::vector<cplx64> w(n);
-  for (int m = 0; m < n; ++m) {
-    const int quad = m / q4, r = m % q4;
-    double cs, sn;
-    if (r <= q8) {
-      cs = (double)C[r];
-      sn = (double)Sn[r];
-    } else {
-      cs = (double)Sn[q4 - r];
-      sn = (double)C[q4 - r];
-    }
-    double c2 = cs, s2 = sn;  // rotate by quad quarter turns: angle + quad * pi/2
-    if (quad == 1) { c2 = -sn; s2 = cs; }
-    if (quad == 2) { c2 = -cs; s2 = -sn; }
-    if (quad == 3) { c2 = sn; s2 = -cs; }
-    w[m] = cplx64{c2, -s2};
-  }
-  return w;
 }
 
 mhd_status check_inst(mhd_ctx *c, int inst) {
@@ -358,7 +327,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->H = (cplx64 *)dalloc(c, s.S * sizeof(cplx64))) != nullptr;
   ok = ok && (c->W1 = (cplx64 *)dalloc(c, s.W1 * sizeof(cplx64))) != nullptr;
   ok = ok && (c->W2 = (cplx64 *)dalloc(c, s.W2 * sizeof(cplx64))) != nullptr;
-  ok = ok && (c->tw = (cplx64 *)dalloc(c, (size_t)c->d.n * sizeof(cplx64))) != nullptr;
+  ok = ok && (c->tw = (cplx64 *)dalloc(c, mhd::fp64_twiddle_size(c->d.n))) != nullptr;
   ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
   if (c->precision != MHD_FP64) ok = ok && (c->S64 = (cplx64 *)dalloc(c, 7 * c->d.spec * sizeof(cplx64))) != nullptr;
   if (c->integrator != MHD_AB2)
@@ -378,11 +347,12 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   }
   std::vector<mhd::PhysDev> pd(p->batch);
   for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
-  const std::vector<cplx64> w = twiddles(c->d.n);
+  const std::vector<cplx64> w = mhd::twiddle_table(c->d.n);
+  const std::vector<unsigned char> w64 = mhd::fp64_twiddle_bytes(c->d.n);
   std::vector<cplx32> w32(w.size());
   for (size_t i = 0; i < w.size(); ++i) w32[i] = cplx32{(float)w[i].re, (float)w[i].im};
   cudaError_t e = cudaMemcpyAsync(c->phys, pd.data(), pd.size() * sizeof(mhd::PhysDev), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w.data(), w.size() * sizeof(cplx64), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w64.data(), w64.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw32, w32.data(), w32.size() * sizeof(cplx32), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);

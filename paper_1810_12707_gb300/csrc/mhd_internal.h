@@ -17,6 +17,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace mhd {
 
 constexpr int kStateFields = 7;  // rho, m_x, m_y, m_z, B_x, B_y, B_z
@@ -87,6 +89,13 @@ inline Dims make_dims(int n, int batch) {
 // NK kept indices to N; forward (sign -1) keeps only the NK kept outputs and multiplies by
 // `scale`.
 // `tile` > 0 forces the number of columns per block (else the library's choice).
+// Host twiddle tables (twiddles.cu).  twiddle_table: W_N^m = exp(-2 pi i m/N), m < N.
+// fp64_twiddle_bytes: the table every FP64 transform reads, fp64_twiddle_size(n) bytes: the
+// classic table, then N pairs (c, t), then N bytes q with W_N^m = i^q c (1 + i t), |t| <= 1.
+std::vector<cplx64> twiddle_table(int n);
+std::vector<unsigned char> fp64_twiddle_bytes(int n);
+constexpr size_t fp64_twiddle_size(int n) { return (size_t)n * (2 * sizeof(cplx64) + 1); }
+
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
                                const cplx64 *tw, cudaStream_t s, int tile = 0);
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,

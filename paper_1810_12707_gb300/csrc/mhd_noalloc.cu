@@ -59,8 +59,8 @@ constexpr size_t kOffW1 = kOffR + round256(kL.r * sizeof(cplx64));
 constexpr size_t kOffW2 = kOffW1 + round256(kL.w1 * sizeof(cplx64));
 constexpr size_t kOffPart = kOffW2 + round256(kL.w2 * sizeof(cplx64));
 constexpr size_t kOffTw16 = kOffPart + round256(kL.part_doubles * sizeof(double));
-constexpr size_t kOffTw32 = kOffTw16 + round256(16 * sizeof(cplx64));
-constexpr size_t kOffPhys = kOffTw32 + round256(32 * sizeof(cplx64));
+constexpr size_t kOffTw32 = kOffTw16 + round256(mhd::fp64_twiddle_size(16));
+constexpr size_t kOffPhys = kOffTw32 + round256(mhd::fp64_twiddle_size(32));
 constexpr size_t kScratchBytes = kOffPhys + round256(sizeof(mhd::PhysDev));  // about 4.7 MB
 
 }  // namespace
@@ -74,29 +74,6 @@ namespace {
 std::mutex g_mu;
 unsigned char *g_base[64] = {nullptr};
 
-// exp(-2 pi i m / n) for m < n, first-octant values and exact quarter-turn symmetries.
-std::vector<cplx64> twiddle_table(int n) {
-  const int q4 = n / 4, q8 = n / 8;
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  std::vector<cplx64> w(n);
-  for (int m = 0; m < n; ++m) {
-    const int quad = m / q4, r = m % q4;
-    const int rr = r <= q8 ? r : q4 - r;
-    double c = r == 0 ? 1.0 : (double)cosl(two_pi * rr / n);
-    double s = r == 0 ? 0.0 : (double)sinl(two_pi * rr / n);
-    if (r > q8) {
-      const double t = c;
-      c = s;
-      s = t;
-    }
-    double c2 = c, s2 = s;
-    if (quad == 1) { c2 = -s; s2 = c; }
-    if (quad == 2) { c2 = -c; s2 = -s; }
-    if (quad == 3) { c2 = s; s2 = -c; }
-    w[m] = cplx64{c2, -s2};
-  }
-  return w;
-}
 
 // Once per device, with that device current: resolve the array's device address and upload the
 // twiddle tables (plain copies into the array; nothing is allocated).
@@ -111,9 +88,9 @@ cudaError_t setup_device(unsigned char **base) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     unsigned char *b = static_cast<unsigned char *>(p);
-    const std::vector<cplx64> t16 = twiddle_table(16), t32 = twiddle_table(32);
-    e = cudaMemcpy(b + kOffTw16, t16.data(), t16.size() * sizeof(cplx64), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + kOffTw32, t32.data(), t32.size() * sizeof(cplx64), cudaMemcpyHostToDevice);
+    const std::vector<unsigned char> t16 = mhd::fp64_twiddle_bytes(16), t32 = mhd::fp64_twiddle_bytes(32);
+    e = cudaMemcpy(b + kOffTw16, t16.data(), t16.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + kOffTw32, t32.data(), t32.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     g_base[dev] = b;
   }
