@@ -120,9 +120,9 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     # (kernel, n, batch, precision): (bytes per launch, source hash, capture)
-    ("flux_x", 256, 1, "fp64"): (632_740_864 + 1_029_102_000, "57d75d8d4cd74517",
+    ("flux_x", 256, 1, "fp64"): (631_591_936 + 1_028_926_000, "c43e44e09251639d",
                                  "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
-    ("flux_x", 256, 1, "fp32"): (315_676_672 + 488_872_448, "57d75d8d4cd74517",
+    ("flux_x", 256, 1, "fp32"): (315_687_680 + 489_102_080, "c43e44e09251639d",
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
 }
 
