@@ -77,13 +77,16 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
     const double k2 = kx * kx + ky * ky + kz * kz;
     const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
 
+    // the product spectra arrive unnormalised: their factor inv_n3 rides on the wavenumbers and
+    // dissipation coefficients they meet (fewer FP64 multiplies than scaling 12 spectra)
+    const double skx = kx * inv_n3, sky = ky * inv_n3, skz = kz * inv_n3, nuk2s = nu * k2 * inv_n3;
     const cplx64 *S = y_in + (size_t)inst * 7 * spec + m;
     const FC *F = flux + (size_t)inst * 12 * spec + m;
     cplx64 y[7], f[12];
 #pragma unroll
     for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) f[q] = c_scale(c_cvt<cplx64>(F[q * spec]), inv_n3);
+    for (int q = 0; q < 12; ++q) f[q] = c_cvt<cplx64>(F[q * spec]);
     const cplx64 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
     const cplx64 Ex = f[6], Ey = f[7], Ez = f[8];
 
@@ -99,11 +102,11 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
       const cplx64 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const cplx64 divT = {kx * T[a][0].re + ky * T[a][1].re + kz * T[a][2].re,
-                             kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im};
+        const cplx64 divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
+                             skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
         const cplx64 g = {divT.re + kk[a] * cs2 * y[0].re, divT.im + kk[a] * cs2 * y[0].im};
         const cplx64 u = f[9 + a];
-        r[1 + a] = cplx64{g.im - nu * k2 * u.re, -g.re - nu * k2 * u.im};
+        r[1 + a] = cplx64{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
       }
       if (force != nullptr && phys[inst].famp != 0.0) {
 #pragma unroll
@@ -115,12 +118,13 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
     }
     // induction: i k x E - eta k^2 B
     {
-      const cplx64 c[3] = {{ky * Ez.re - kz * Ey.re, ky * Ez.im - kz * Ey.im},
-                           {kz * Ex.re - kx * Ez.re, kz * Ex.im - kx * Ez.im},
-                           {kx * Ey.re - ky * Ex.re, kx * Ey.im - ky * Ex.im}};
+      const cplx64 c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
+                           {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
+                           {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
+      const double etak2 = eta * k2;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        r[4 + a] = cplx64{-c[a].im - eta * k2 * y[4 + a].re, c[a].re - eta * k2 * y[4 + a].im};
+        r[4 + a] = cplx64{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
     }
 
     const size_t o7 = (size_t)inst * 7 * spec + m;
@@ -130,19 +134,19 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
       continue;
     }
     const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
+    const double dta1 = dt * a1, dta0 = dt * a0;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       const size_t i = o7 + q * spec;
       const cplx64 rq = r[q];
       if (op == ASM_AB2 || op == ASM_PC_PRED) {
-        cplx64 inc = {a1 * rq.re, a1 * rq.im};
+        // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
+        cplx64 y0 = state[i];
         if (a0 != 0.0) {
           const cplx64 h = hist[i];
-          inc.re += a0 * h.re;
-          inc.im += a0 * h.im;
+          y0 = cplx64{fma(dta0, h.re, y0.re), fma(dta0, h.im, y0.im)};
         }
-        const cplx64 y0 = state[i];
-        const cplx64 yn = {y0.re + dt * inc.re, y0.im + dt * inc.im};
+        const cplx64 yn = {fma(dta1, rq.re, y0.re), fma(dta1, rq.im, y0.im)};
         if (op == ASM_AB2) state[i] = yn;
         else ystage[i] = yn;
         hist[i] = rq;
