@@ -294,7 +294,8 @@ def run_ours(args, name, cfg):
         mhd.mhd_set_state(ctx, i, ic.rho, ic.u, ic.b)
     stream = torch.cuda.current_stream()
     # tile widths of the column FFT passes from the library's autotuner (before any timing)
-    tiles = None if args.no_autotune else mhd.mhd_autotune(ctx, reps=3)["tiles"]
+    tuned = None if args.no_autotune else mhd.mhd_autotune(ctx, reps=3)
+    tiles = tuned["tiles"] if tuned else None
 
     # per-kernel device times from a profiled run (direct launches, events on the library's
     # stream) of K steps, after the warm-up
@@ -345,10 +346,14 @@ def run_ours(args, name, cfg):
         hs.append(h)
     outs = [(pin((n, n, n)), pin((3, n, n, n)), pin((3, n, n, n))) for _ in range(len(hs))]
     ectx = mhd.mhd_init(n, phys, dt=cfg["dt"], precision=prec)
-    if tiles:
+    if tuned:
         for opt, t in zip((mhd.MHD_OPT_TILE_INV_Z, mhd.MHD_OPT_TILE_INV_Y, mhd.MHD_OPT_TILE_FWD_Y,
-                           mhd.MHD_OPT_TILE_FWD_Z), tiles):
+                           mhd.MHD_OPT_TILE_FWD_Z), tuned["tiles"]):
             mhd.mhd_set_option(ectx, opt, t)
+        if prec != mhd.MHD_FP64:
+            for opt, r in zip((mhd.MHD_OPT_RADIX_INV_Z, mhd.MHD_OPT_RADIX_INV_Y, mhd.MHD_OPT_RADIX_FWD_Y,
+                               mhd.MHD_OPT_RADIX_FWD_Z), tuned["radix"]):
+                mhd.mhd_set_option(ectx, opt, r)
 
     def e2e_step():
         for i in range(batch):
@@ -414,7 +419,8 @@ def run_ours(args, name, cfg):
             "vs_baseline": value / (world * PAPER_256_V100) if (n == 256 and batch == 1) else None,
             "dtype": "f64" if prec == mhd.MHD_FP64 else "f32 (double-float state)", "data": "synthetic",
             "config": dict(config_block(name, cfg, world),
-                           col_tiles=tiles if tiles else "library default (autotuner off)"),
+                           col_tiles=tiles if tiles else "library default (autotuner off)",
+                           col_radix=tuned["radix"] if tuned else "library default"),
             "roofline": roof,
             "kernels": per,
             "cpu_baseline": cpu,

@@ -231,6 +231,10 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *                          (inverse z, inverse y, forward y, forward z); 0 (default) = chosen by
  *                          the library; otherwise 1..64, rounded down to a power of two
  *                          (mhd_autotune sets these).
+ *   MHD_OPT_RADIX_INV_Z ... MHD_OPT_RADIX_FWD_Z: transform radix of the same four passes in the
+ *                          mixed mode: 8 or 16 values per thread (two shared-memory stages at
+ *                          N = 256 with 16, three with 8); 0 (default) = 16 at N >= 512, else 8.
+ *                          FP64 contexts accept and ignore them (their passes use radix 8).
  *   MHD_OPT_FLUX_PIPELINE  1: the fused x pass of the mixed mode at N >= 128 runs as a persistent
  *                          kernel that prefetches the next rows with bulk copies (TMA); 0
  *                          (default): one block per row pair, which measured faster on GB300.
@@ -241,20 +245,25 @@ enum {
   MHD_OPT_TILE_INV_Y = 2,
   MHD_OPT_TILE_FWD_Y = 3,
   MHD_OPT_TILE_FWD_Z = 4,
-  MHD_OPT_FLUX_PIPELINE = 5
+  MHD_OPT_FLUX_PIPELINE = 5,
+  MHD_OPT_RADIX_INV_Z = 6,
+  MHD_OPT_RADIX_INV_Y = 7,
+  MHD_OPT_RADIX_FWD_Y = 8,
+  MHD_OPT_RADIX_FWD_Z = 9
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
 
 /* Autotuner of the column FFT passes (the paper has no counterpart: its FFTs are library calls).
  * For each of the four passes (inverse z, inverse y, forward y, forward z), every power-of-two
- * tile width from 1 to 64 columns that fits the thread and shared-memory limits is launched
- * `reps` times (1..100) on the context's own buffers, with the step's shapes (all instances, the
- * working precision), and timed with CUDA events on the context's stream; the fastest width is
- * set with the MHD_OPT_TILE_* options.  The chosen widths go to tiles[4] (HOST, may be NULL) and
- * the mean milliseconds per launch of each chosen width to ms[4] (HOST, may be NULL).  Tile width
- * does not change any result: each column's transform is the same.  The scratch buffers are
- * overwritten; the state is only read.  Synchronises. */
-MHD_API mhd_status mhd_autotune(mhd_ctx *ctx, int32_t reps, int32_t *tiles, double *ms);
+ * tile width from 1 to 64 columns that fits the thread and shared-memory limits, and in the
+ * mixed mode each radix (8 and 16 values per thread), is launched `reps` times (1..100) on the
+ * context's own buffers, with the step's shapes (all instances, the working precision), and timed
+ * with CUDA events on the context's stream; the fastest choice is set with the MHD_OPT_TILE_* and
+ * MHD_OPT_RADIX_* options.  The chosen widths go to tiles[4], the radices to radix[4] and the mean
+ * milliseconds per launch to ms[4] (HOST arrays, each may be NULL).  Tile width does not change
+ * any result (each column's transform is the same); radix changes the rounding of the FP32 passes
+ * only.  The scratch buffers are overwritten; the state is only read.  Synchronises. */
+MHD_API mhd_status mhd_autotune(mhd_ctx *ctx, int32_t reps, int32_t *tiles, int32_t *radix, double *ms);
 
 /* Per-kernel device time of mhd_step, for measurement.  While profiling is on, every kernel that
  * mhd_step launches is bracketed by CUDA events on the context's stream.  mhd_profile(ctx, 1)

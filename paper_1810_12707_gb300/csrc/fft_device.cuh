@@ -90,9 +90,46 @@ __device__ __forceinline__ void dft8(C *v) {
   }
 }
 
+// Length 16 as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.  Length-4 DFTs over n1 for each n2, the
+// twiddles W16^(n2 k1), then length-4 DFTs over n2 for each k1 (W16 = exp(DIR 2 pi i / 16)).
+template <int DIR, typename C>
+__device__ __forceinline__ void dft16(C *v) {
+  using R = typename C::value_type;
+  constexpr R c1 = (R)0.92387953251128675613;  // cos(pi/8)
+  constexpr R s1 = (R)0.38268343236508977173;  // sin(pi/8)
+  constexpr R h = (R)0.70710678118654752440;   // cos(pi/4)
+  C a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+  }
+  const C w1 = {c1, DIR * s1}, w2 = {h, DIR * h}, w3 = {s1, DIR * c1};
+  const C w6 = {-h, DIR * h}, w9 = {-c1, -DIR * s1};
+  a[1][1] = c_mul(a[1][1], w1);
+  a[1][2] = c_mul(a[1][2], w2);
+  a[1][3] = c_mul(a[1][3], w3);
+  a[2][1] = c_mul(a[2][1], w2);
+  a[2][2] = c_mul_i<DIR>(a[2][2]);  // W16^4 = DIR i
+  a[2][3] = c_mul(a[2][3], w6);
+  a[3][1] = c_mul(a[3][1], w3);
+  a[3][2] = c_mul(a[3][2], w6);
+  a[3][3] = c_mul(a[3][3], w9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+  }
+}
+
 template <int R, int DIR, typename C>
 __device__ __forceinline__ void dft_small(C *v) {
-  if constexpr (R == 8) dft8<DIR>(v);
+  if constexpr (R == 16) dft16<DIR>(v);
+  else if constexpr (R == 8) dft8<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v);
   else dft2<DIR>(v);
 }
@@ -242,31 +279,45 @@ __device__ __forceinline__ void dft_twiddled_fma(cplx64 *v, int m, const cplx64 
   }
 }
 
+// ---- values per thread ----
+// FP32 pencils: 16 values per thread (radix 16: two shared-memory stages at N = 256 where radix 8
+// needs three; the FP32 passes are bound by instruction issue).  FP64: 8 (their cost is FP64
+// instructions, which radix 16 does not reduce).  A pencil is transformed by N / VPT threads.
+// Kernels may choose 8 or 16 for FP32 (the radix that suits a pass depends on N and on the pass;
+// the column passes let the autotuner pick); FP64 always uses 8.
+template <typename C>
+__host__ __device__ constexpr int fft_vpt() { return sizeof(C) == 8 ? 16 : 8; }
+template <int N, int VPT>
+__host__ __device__ constexpr int tpp_for() { return N / VPT > 0 ? N / VPT : 1; }
+template <int N, typename C>
+__host__ __device__ constexpr int fft_tpp() { return tpp_for<N, fft_vpt<C>()>(); }
+
 // ---- Stockham pencil FFT ----
 //
-// The transform of length N = product of radices (8 while at least 8 points remain, then 4 or
-// 2) runs as a sequence of stages.  Before a stage, sub-transforms of length NS are complete;
+// The transform of length N = product of radices (VPT = 16 or 8 while that many points remain,
+// then the rest) runs as a sequence of stages.  Before a stage, sub-transforms of length NS are complete;
 // butterfly j (0 <= j < N/R) gathers x[j + r N/R] (r < R), multiplies element r by the twiddle
 // W_{NS R}^{r (j mod NS)}, applies a length-R DFT and scatters the results to
 // (j div NS) NS R + (j mod NS) + r NS.  After the last stage the pencil holds X in natural order
-// (the auto-sorting formulation of Cooley-Tukey by Stockham).  Each of the N/8 threads of a
-// group owns 8 / R butterflies per stage, so it always holds 8 values.  `tw[m]` = W_N^m =
+// (the auto-sorting formulation of Cooley-Tukey by Stockham).  Each of the N/VPT threads of a
+// group owns VPT / R butterflies per stage, so it always holds VPT values.  `tw[m]` = W_N^m =
 // exp(-2 pi i m / N); the inverse uses its conjugate.
 //
 // Every thread of the block must call this (it contains group barriers); threads with
 // `active == false` only take part in the barriers.  The caller separates the transform from the
 // preceding writes and the following reads of the pencil with a block barrier.
-template <int N, int DIR, int NS, typename C>
+template <int N, int DIR, int NS, typename C, int VPT>
 __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
-    constexpr int R = (N / NS >= 8) ? 8 : N / NS;
-    constexpr int NB = 8 / R;
-    constexpr int TPP = N / 8;
+    static_assert(VPT == 8 || (VPT == 16 && sizeof(C) == 8), "radix 16 is an FP32 option");
+    constexpr int R = (N / NS >= VPT) ? VPT : N / NS;
+    constexpr int NB = VPT / R;
+    constexpr int TPP = tpp_for<N, VPT>();
     constexpr int TWSTEP = N / (NS * R);
     // FP64 stages with twiddles take them inside the butterflies (FMA form, fewer FP64
     // instructions); the others multiply on load.
     constexpr bool kFma = std::is_same<C, cplx64>::value && NS > 1;
-    C v[8];
+    C v[VPT];
     if (active) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -301,13 +352,14 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
       }
     }
     group_sync<TPP>();
-    stockham_stages<N, DIR, NS * R, C>(buf, t, active, tw);
+    stockham_stages<N, DIR, NS * R, C, VPT>(buf, t, active, tw);
   }
 }
 
-template <int N, int DIR, typename C>
+// `t` in [0, N / VPT): the thread's index within its pencil's group.
+template <int N, int DIR, typename C, int VPT = fft_vpt<C>()>
 __device__ __forceinline__ void pencil_fft(C *buf, int t, bool active, const C *__restrict__ tw) {
-  stockham_stages<N, DIR, 1, C>(buf, t, active, tw);
+  stockham_stages<N, DIR, 1, C, VPT>(buf, t, active, tw);
 }
 
 // FFT index of kept index j (0..2K) along a truncated axis: j for j <= K, else j - (2K+1) + N.

@@ -21,12 +21,13 @@ namespace mhd {
 // A block has TC = 2^tsh columns and TC * N/8 threads: thread (l0, c) = (tid >> tsh, tid & (TC-1))
 // moves rows l0, l0 + N/8, ... of column c, so consecutive threads touch consecutive columns of a
 // row (coalesced) and no index needs a division.
-template <int N, int DIR, typename CI, typename CO, typename CC>
+// VPT: values per thread of the transform (8, or 16 for FP32), so N / VPT threads per column.
+template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
 __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
                                int cols, typename CC::value_type scale, const CC *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CC *sm = reinterpret_cast<CC *>(smem_raw);
-  constexpr int TPP = N / 8;
+  constexpr int TPP = tpp_for<N, VPT>();
   constexpr int P = pencil_pitch<CC>(N);
   constexpr int K = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   constexpr int NK = 2 * K + 1;
@@ -65,7 +66,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   const int pencil = threadIdx.x / TPP;
   const int t = threadIdx.x - pencil * TPP;
   const bool active = pencil < tc && tile * tc + pencil < cols;
-  pencil_fft<N, DIR, CC>(sm + (active ? pencil : 0) * P, t, active, tw);
+  pencil_fft<N, DIR, CC, VPT>(sm + (active ? pencil : 0) * P, t, active, tw);
   __syncthreads();  // the store loop reads every pencil
 
   if (col_ok) {
@@ -82,8 +83,7 @@ namespace {
 
 // Columns per block: enough that a tile row is at least 128 bytes and a block at least 128
 // threads, but not more than the columns there are.
-int pick_tc(int n, int cols) {
-  const int tpp = n / 8;
+int pick_tc(int tpp, int cols) {
   int tc = 8;
   while (tc * tpp < 128 && tc < 64) tc *= 2;
   while (tc * tpp > 1024) tc /= 2;
@@ -99,65 +99,82 @@ int floor_log2(int v) {
 }
 
 // Largest thread count a launch of this instantiation may use (its registers bound it below 1024).
-template <int N, int DIR, typename CI, typename CO>
+template <int N, int DIR, typename CI, typename CO, int VPT>
 int col_max_threads() {
   static int cached = 0;
   if (cached == 0) {
     cudaFuncAttributes a;
-    cached = cudaFuncGetAttributes(&a, col_fft_kernel<N, DIR, CI, CO, CO>) == cudaSuccess ? a.maxThreadsPerBlock : 256;
+    cached = cudaFuncGetAttributes(&a, col_fft_kernel<N, DIR, CI, CO, CO, VPT>) == cudaSuccess ? a.maxThreadsPerBlock
+                                                                                               : 256;
   }
   return cached;
 }
 
-template <int N, int DIR, typename CI, typename CO>
-cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
+template <int N, int DIR, typename CI, typename CO, int VPT>
+cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
                          cudaStream_t s, int tile) {
-  int tc = tile > 0 ? tile : pick_tc(N, cols);
-  const int max_threads = col_max_threads<N, DIR, CI, CO>();
-  while (tc > 1 && tc * (N / 8) > max_threads) tc /= 2;
+  constexpr int TPP = tpp_for<N, VPT>();
+  int tc = tile > 0 ? tile : pick_tc(TPP, cols);
+  const int max_threads = col_max_threads<N, DIR, CI, CO, VPT>();
+  while (tc > 1 && tc * TPP > max_threads) tc /= 2;
   if (tc < 1) tc = 1;
   const int tsh = floor_log2(tc);  // a requested width that is not a power of two is rounded down
   tc = 1 << tsh;
   const int ntiles = (cols + tc - 1) / tc;
   const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO>>((int)smem);
+    cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO, VPT>>((int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (long long)nslab * ntiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  col_fft_kernel<N, DIR, CI, CO, CO><<<(unsigned)blocks, tc * (N / 8), smem, s>>>(
+  col_fft_kernel<N, DIR, CI, CO, CO, VPT><<<(unsigned)blocks, tc * TPP, smem, s>>>(
       in, out, ntiles, tsh, cols, (typename CO::value_type)scale, tw);
   return cudaGetLastError();
 }
 
+// Radix of a column pass: `vpt` 8 or 16 (FP32 only); 0 picks the library default (radix 8, and
+// radix 16 for FP32 at N >= 512, where it measured faster).
+template <int N, int DIR, typename CI, typename CO>
+cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
+                         cudaStream_t s, int tile, int vpt) {
+  if constexpr (sizeof(CO) == 8) {
+    if (vpt == 16 || (vpt == 0 && N >= 512))
+      return launch_col_v<N, DIR, CI, CO, 16>(in, out, nslab, cols, scale, tw, s, tile);
+  }
+  return launch_col_v<N, DIR, CI, CO, 8>(in, out, nslab, cols, scale, tw, s, tile);
+}
+
 template <int DIR, typename CI, typename CO>
 cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale, const CO *tw,
-                       cudaStream_t s, int tile) {
+                       cudaStream_t s, int tile, int vpt) {
   switch (n) {
-    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s, tile);
-    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s, tile);
+    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-int col_max_tile(int n, int dir, bool fp64, bool mixed_in) {
+int col_max_tile(int n, int dir, bool fp64, bool mixed_in, int vpt) {
+  const bool r16 = !fp64 && vpt == 16;
   auto pick = [&](auto tag_n) -> int {
     constexpr int N = decltype(tag_n)::value;
     int t;
-    if (fp64) t = dir > 0 ? col_max_threads<N, +1, cplx64, cplx64>() : col_max_threads<N, -1, cplx64, cplx64>();
-    else if (dir > 0) t = mixed_in ? col_max_threads<N, +1, cplx64, cplx32>() : col_max_threads<N, +1, cplx32, cplx32>();
-    else t = col_max_threads<N, -1, cplx32, cplx32>();
+    if (fp64) t = dir > 0 ? col_max_threads<N, +1, cplx64, cplx64, 8>() : col_max_threads<N, -1, cplx64, cplx64, 8>();
+    else if (dir > 0 && mixed_in) t = col_max_threads<N, +1, cplx64, cplx32, 8>();
+    else if (dir > 0) t = r16 ? col_max_threads<N, +1, cplx32, cplx32, 16>() : col_max_threads<N, +1, cplx32, cplx32, 8>();
+    else t = r16 ? col_max_threads<N, -1, cplx32, cplx32, 16>() : col_max_threads<N, -1, cplx32, cplx32, 8>();
+    const int tpp = r16 ? tpp_for<N, 16>() : tpp_for<N, 8>();
     int tc = 1;
-    while (tc * 2 * (N / 8) <= t && tc < 64) tc *= 2;
+    while (tc * 2 * tpp <= t && tc < 64) tc *= 2;
     return tc;
   };
   switch (n) {
@@ -173,24 +190,24 @@ int col_max_tile(int n, int dir, bool fp64, bool mixed_in) {
 }
 
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s, int tile) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
+                               const cplx64 *tw, cudaStream_t s, int tile, int) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
 }
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
                                const cplx32 *tw, cudaStream_t s, int tile) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
 }
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s, int tile) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile);
+                               const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, vpt);
 }
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s, int tile) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile, int) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8);
 }
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s, int tile) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, vpt);
 }
 
 }  // namespace mhd

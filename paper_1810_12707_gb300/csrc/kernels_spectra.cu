@@ -19,8 +19,7 @@ constexpr int kMaxThreads = 384;
 
 constexpr int pairs_for(int n) { return (n / 8) >= 16 ? 1 : 16 / (n / 8); }
 
-constexpr int threads_for(int n, int pencils) {
-  int tpp = n / 8;
+constexpr int threads_for(int tpp, int pencils) {
   int g = kMaxThreads / tpp;
   if (g > pencils) g = pencils;
   int t = g * tpp;
@@ -29,13 +28,13 @@ constexpr int threads_for(int n, int pencils) {
 
 template <int N, int DIR, typename Ptr>
 __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const cplx64 *__restrict__ tw) {
-  constexpr int TPP = N / 8;
+  constexpr int TPP = tpp_for<N, 8>();
   const int G = blockDim.x / TPP;
   const int g = threadIdx.x / TPP, t = threadIdx.x - g * TPP;
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR, cplx64>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, cplx64, 8>(ptr(active ? id : 0), t, active, tw);
   }
   __syncthreads();
 }
@@ -174,7 +173,7 @@ template <int N>
 cudaError_t velocity_n(const cplx64 *in, cplx64 *out, const Dims &d, const cplx64 *tw, cudaStream_t s) {
   constexpr int PAIRS = pairs_for(N);
   const int blocks = N * N / (2 * PAIRS);
-  const int threads = threads_for(N, 4 * PAIRS);
+  const int threads = threads_for(tpp_for<N, 8>(), 4 * PAIRS);
   const size_t smem = (size_t)4 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<velocity_x_kernel<N>>((int)smem);

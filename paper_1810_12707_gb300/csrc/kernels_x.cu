@@ -26,9 +26,8 @@ constexpr int kMaxThreads = 384;
 
 constexpr int pairs_for(int n) { return (n / 8) >= 16 ? 1 : 16 / (n / 8); }
 
-constexpr int threads_for(int n, int pencils, int max_threads = kMaxThreads) {
-  // groups of N/8 threads, at most max_threads threads, a multiple of 32
-  int tpp = n / 8;
+constexpr int threads_for(int tpp, int pencils, int max_threads = kMaxThreads) {
+  // groups of tpp threads (one pencil each), at most max_threads threads, a multiple of 32
   int g = max_threads / tpp;
   if (g < 1) g = 1;
   if (g > pencils) g = pencils;
@@ -40,30 +39,35 @@ constexpr int threads_for(int n, int pencils, int max_threads = kMaxThreads) {
 // transform while another waits at a barrier (measured on GB300 over 96..384 threads: 128 best at
 // 256^3 in both precisions, 192 at 512^3); below, the pencil count caps the block at 192 threads.
 constexpr int flux_max_threads(int n) { return n == 256 ? 128 : n == 512 ? 192 : kMaxThreads; }
-template <int N>
+// Values per thread of the flux pass's transforms: FP32 at N <= 256 uses radix 16 (measured
+// faster at 64^3 and 256^3); larger FP32 grids and FP64 use radix 8.
+template <int N, typename C>
+constexpr int flux_vpt() { return sizeof(C) == 8 && N <= 256 ? 16 : 8; }
+template <int N, typename C>
 constexpr int flux_threads() {
-  return threads_for(N, 12 * pairs_for(N), flux_max_threads(N));
+  return threads_for(tpp_for<N, flux_vpt<N, C>()>(), 12 * pairs_for(N), flux_max_threads(N));
 }
-// Blocks per SM the register allocation is sized for: about 170 registers a thread in FP64 and 85
-// in FP32.
+// Blocks per SM the register allocation is sized for: about 170 registers a thread in FP64, 85 in
+// FP32 with radix 8 and 128 with radix 16 (its 16 values per thread).
 template <int N, typename C>
 constexpr int flux_min_blocks() {
-  const int b = (sizeof(C) == 8 ? 768 : 384) / flux_threads<N>();
+  const int budget = sizeof(C) == 8 ? (flux_vpt<N, C>() == 16 ? 512 : 768) : 384;
+  const int b = budget / flux_threads<N, C>();
   return b < 1 ? 1 : b;
 }
 
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
 // N/8 threads of the block taking one pencil at a time.  Each pencil is touched by its group only,
 // so the stages synchronise per group; one block barrier closes the whole transform.
-template <int N, int DIR, typename Ptr, typename C>
+template <int N, int DIR, int VPT, typename Ptr, typename C>
 __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
-  constexpr int TPP = N / 8;
+  constexpr int TPP = tpp_for<N, VPT>();
   const int G = blockDim.x / TPP;
   const int g = threadIdx.x / TPP, t = threadIdx.x - g * TPP;
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR, C>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, C, VPT>(ptr(active ? id : 0), t, active, tw);
   }
   __syncthreads();  // the callers' next phase reads every pencil
 }
@@ -78,7 +82,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // bgrid (nullable): the grid magnetic field is also written out, [inst][3][N^3] in the data's
 // precision, for the tracer push.
 template <int N, typename C>
-__global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
+__global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
                               int K, int blocks_per_inst, const C *__restrict__ tw,
                               typename C::value_type *__restrict__ bgrid) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) 
   const int bl = blockIdx.x - inst * blocks_per_inst;
   const size_t row0 = (size_t)bl * PAIRS * 2;
   // the launch uses exactly this many threads, so every loop below has a constant trip count
-  constexpr int nthr = flux_threads<N>();
+  constexpr int nthr = flux_threads<N, C>();
 
   // 1. load and pack the 7 state fields: pencil (p, f) at sm + (p * 12 + f) * P.  Unrolled: all
   // of a thread's loads are issued before the first shared-memory store.
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) 
   __syncthreads();
 
   // 2. inverse transforms of the 7 fields
-  fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
+  fft_pencils<N, +1, (flux_vpt<N, C>())>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
 
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
   const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(flux_threads<N>(), (flux_min_blocks<N, C>())) 
   __syncthreads();
 
   // 4. forward transforms of the 12 products
-  fft_pencils<N, -1>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  fft_pencils<N, -1, (flux_vpt<N, C>())>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
 
   // 5. unpack and store the kept half spectra
   for (int q = threadIdx.x; q < 12 * PAIRS * NX; q += nthr) {
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __syncthreads();
 
     // 2. inverse transforms of the 7 fields
-    fft_pencils<N, +1>(7, [&](int id) { return sm + id * P; }, tw);
+    fft_pencils<N, +1, (flux_vpt<N, C>())>(7, [&](int id) { return sm + id * P; }, tw);
 
     // 3. products on the grid
     const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __syncthreads();
 
     // 4. forward transforms of the 12 products
-    fft_pencils<N, -1>(12, [&](int id) { return sm + id * P; }, tw);
+    fft_pencils<N, -1, (flux_vpt<N, C>())>(12, [&](int id) { return sm + id * P; }, tw);
 
     // 5. unpack and store
       for (int q = tx; q < 12 * NX; q += nthr) {
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
     }
   }
   __syncthreads();
-  fft_pencils<N, -1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  fft_pencils<N, -1, 8>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
   for (int q = threadIdx.x; q < 7 * PAIRS * NX; q += nthr) {
     const int k = q % NX;
     const int r = q / NX;
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
-  fft_pencils<N, +1>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  fft_pencils<N, +1, 8>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
   for (int q = threadIdx.x; q < nf * PAIRS * N; q += nthr) {
     const int j = q % N;
     const int r = q / N;
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
     sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
   }
   __syncthreads();
-  fft_pencils<N, +1>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
+  fft_pencils<N, +1, 8>(7 * PAIRS, [&](int id) { return sm + id * P; }, tw);
 
   const double cs2 = phys[0].cs * phys[0].cs;
   double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -543,7 +547,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
     if (err != nullptr && smem <= 200 * 1024) {
       cudaError_t e = ensure_smem<flux_x_pipe_kernel<N, C>>((int)smem);
       if (e != cudaSuccess) return e;
-      const int threads = threads_for(N, 12);
+      const int threads = threads_for(tpp_for<N, flux_vpt<N, C>()>(), 12);
       int per_sm = 0, dev = 0, sms = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flux_x_pipe_kernel<N, C>, threads, smem);
       if (e != cudaSuccess) return e;
@@ -557,7 +561,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
     }
   }
   const int bpi = N * N / (2 * PAIRS);
-  const int threads = flux_threads<N>();
+  const int threads = flux_threads<N, C>();
   const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<flux_x_kernel<N, C>>((int)smem);
@@ -575,7 +579,7 @@ cudaError_t set_n(const double *rho, const double *u, const double *b, cplx64 *o
   if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
   const int blocks = (int)(nrows / (2 * PAIRS));
   if (blocks == 0) return cudaSuccess;
-  const int threads = threads_for(N, 7 * PAIRS);
+  const int threads = threads_for(tpp_for<N, 8>(), 7 * PAIRS);
   const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<set_x_kernel<N>>((int)smem);
@@ -592,7 +596,7 @@ cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cp
   if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
   const int blocks = (int)(nrows / (2 * PAIRS));
   if (blocks == 0) return cudaSuccess;
-  const int threads = threads_for(N, nf * PAIRS);
+  const int threads = threads_for(tpp_for<N, 8>(), nf * PAIRS);
   const size_t smem = (size_t)nf * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<get_x_kernel<N>>((int)smem);
@@ -607,7 +611,7 @@ cudaError_t diag_n(const cplx64 *in, const PhysDev *phys, double *part, const Di
                    const cplx64 *tw, cudaStream_t s) {
   constexpr int PAIRS = pairs_for(N);
   const int blocks = N * N / (2 * PAIRS);
-  const int threads = threads_for(N, 7 * PAIRS);
+  const int threads = threads_for(tpp_for<N, 8>(), 7 * PAIRS);
   const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<diag_x_kernel<N>>((int)smem);

@@ -65,6 +65,7 @@ struct mhd_ctx {
   std::vector<double *> tr;
   void *bgrid = nullptr;
   int tile[4] = {0, 0, 0, 0};
+  int radix[4] = {0, 0, 0, 0};  // values per thread of the FP32 column passes (0: default)
   cudaStream_t cap_stream = nullptr;
   // host-pointer set/get: a copy stream and the events that hand staging slots between streams
   cudaStream_t copy_stream = nullptr;
@@ -605,15 +606,15 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
   CF *w2 = reinterpret_cast<CF *>(c->W2);
-  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0]));
-  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1]));
+  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0]));
+  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1], c->radix[1]));
   unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
   LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(bits, phys, ts, coef, d, c->dt_fixed, c->cfl_adv, c->cfl_visc, c->stream));
   }
-  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2]));
-  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3]));
+  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2], c->radix[2]));
+  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3], c->radix[3]));
   return MHD_OK;
 }
 
@@ -813,7 +814,7 @@ mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32
   return MHD_OK;
 }
 
-mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, double *ms) {
+mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, int32_t *radix, double *ms) {
   if (!c) return MHD_EINVAL;
   if (reps < 1 || reps > 100) return fail(c, MHD_EINVAL, "reps must be 1..100");
   DeviceGuard g(c->device);
@@ -825,8 +826,9 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, double *ms) {
     cudaEventDestroy(e0);
     return fail(c, MHD_ECUDA, "event creation failed");
   }
-  // one launch of column pass `kind` with tile width `tile`, on the step's buffers and shapes
-  auto run = [&](int kind, int tile) -> cudaError_t {
+  // one launch of column pass `kind` with tile width `tile` and radix `vpt`, on the step's
+  // buffers and shapes
+  auto run = [&](int kind, int tile, int vpt) -> cudaError_t {
     if (c->precision == MHD_FP64) {
       cplx64 *w1 = c->W1, *w2 = c->W2;
       switch (kind) {
@@ -838,34 +840,39 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, double *ms) {
     }
     cplx32 *w1 = reinterpret_cast<cplx32 *>(c->W1), *w2 = reinterpret_cast<cplx32 *>(c->W2);
     switch (kind) {
-      case 0: return mhd::launch_col_inverse(state_hi(c, 0), w1, d.n, b * 7, d.nk * d.nx, c->tw32, c->stream, tile);
-      case 1: return mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, c->tw32, c->stream, tile);
-      case 2: return mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw32, c->stream, tile);
-      default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw32, c->stream, tile);
+      case 0: return mhd::launch_col_inverse(state_hi(c, 0), w1, d.n, b * 7, d.nk * d.nx, c->tw32, c->stream, tile, vpt);
+      case 1: return mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, c->tw32, c->stream, tile, vpt);
+      case 2: return mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, c->tw32, c->stream, tile, vpt);
+      default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw32, c->stream, tile, vpt);
     }
   };
   const size_t elem = c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32);
   const size_t pitch = (size_t)(d.n + d.n / (128 / (int)elem)) | 1;  // pencil pitch, as the kernels lay it out
-  int best[4];
+  int best[4], best_vpt[4];
   double best_ms[4];
   cudaError_t err = cudaSuccess;
+  const bool fp64 = c->precision == MHD_FP64;
   for (int kind = 0; kind < 4 && err == cudaSuccess; ++kind) {
     best[kind] = 0;
+    best_vpt[kind] = 0;
     best_ms[kind] = 1e300;
-    const int max_tc = mhd::col_max_tile(d.n, kind < 2 ? +1 : -1, c->precision == MHD_FP64);
-    for (int tc = 1; tc <= max_tc && err == cudaSuccess; tc *= 2) {
-      if (tc * pitch * elem > 227 * 1024) break;
-      if ((err = run(kind, tc)) != cudaSuccess) break;  // warm-up (raises the shared-memory limit)
-      if ((err = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
-      for (int r = 0; r < reps && err == cudaSuccess; ++r) err = run(kind, tc);
-      if (err != cudaSuccess || (err = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
-      if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float t = 0.0f;
-      if ((err = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
-      const double per = (double)t / reps;
-      if (per < best_ms[kind]) {
-        best_ms[kind] = per;
-        best[kind] = tc;
+    for (int vpt = 8; vpt <= (fp64 ? 8 : 16) && err == cudaSuccess; vpt *= 2) {
+      const int max_tc = mhd::col_max_tile(d.n, kind < 2 ? +1 : -1, fp64, false, vpt);
+      for (int tc = 1; tc <= max_tc && err == cudaSuccess; tc *= 2) {
+        if (tc * pitch * elem > 227 * 1024) break;
+        if ((err = run(kind, tc, vpt)) != cudaSuccess) break;  // warm-up (raises the shared-memory limit)
+        if ((err = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) err = run(kind, tc, vpt);
+        if (err != cudaSuccess || (err = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
+        if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0.0f;
+        if ((err = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+        const double per = (double)t / reps;
+        if (per < best_ms[kind]) {
+          best_ms[kind] = per;
+          best[kind] = tc;
+          best_vpt[kind] = fp64 ? 0 : vpt;
+        }
       }
     }
   }
@@ -874,7 +881,9 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, double *ms) {
   if (err != cudaSuccess) return fail(c, MHD_ECUDA, "autotune: %s", cudaGetErrorString(err));
   for (int k = 0; k < 4; ++k) {
     c->tile[k] = best[k];
+    c->radix[k] = best_vpt[k];
     if (tiles) tiles[k] = best[k];
+    if (radix) radix[k] = fp64 ? 8 : best_vpt[k];
     if (ms) ms[k] = best_ms[k];
   }
   drop_graphs(c);
@@ -893,6 +902,9 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   } else if (option >= MHD_OPT_TILE_INV_Z && option <= MHD_OPT_TILE_FWD_Z) {
     if (value < 0 || value > 64) return fail(c, MHD_EINVAL, "tile must be 0..64");
     c->tile[option - MHD_OPT_TILE_INV_Z] = (int)value;
+  } else if (option >= MHD_OPT_RADIX_INV_Z && option <= MHD_OPT_RADIX_FWD_Z) {
+    if (value != 0 && value != 8 && value != 16) return fail(c, MHD_EINVAL, "radix must be 0, 8 or 16");
+    c->radix[option - MHD_OPT_RADIX_INV_Z] = (int)value;
   } else {
     return fail(c, MHD_EINVAL, "unknown option %d", option);
   }

@@ -97,18 +97,20 @@ std::vector<unsigned char> fp64_twiddle_bytes(int n);
 constexpr size_t fp64_twiddle_size(int n) { return (size_t)n * (2 * sizeof(cplx64) + 1); }
 
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s, int tile = 0);
+                               const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
                                const cplx32 *tw, cudaStream_t s, int tile = 0);
+// vpt (FP32 passes): values per thread of the transform, 8 (radix 8) or 16 (radix 16); 0 = the
+// library's default for the grid size.
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s, int tile = 0);
+                               const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 // Largest power-of-two tile width (columns per block, <= 64) a column pass can launch with:
 // dir +1 inverse, -1 forward; fp64 the transform type; mixed_in an FP64 input to an FP32 inverse.
-int col_max_tile(int n, int dir, bool fp64, bool mixed_in = false);
+int col_max_tile(int n, int dir, bool fp64, bool mixed_in = false, int vpt = 8);
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s, int tile = 0);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s, int tile = 0);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and the maximum of

@@ -25,7 +25,8 @@ MHD_FP64 = 0
 MHD_FP32_MIXED = 1
 MHD_AB2, MHD_RK4, MHD_PC = 0, 1, 2
 (MHD_OPT_CUDA_GRAPH, MHD_OPT_TILE_INV_Z, MHD_OPT_TILE_INV_Y, MHD_OPT_TILE_FWD_Y, MHD_OPT_TILE_FWD_Z,
- MHD_OPT_FLUX_PIPELINE) = range(6)
+ MHD_OPT_FLUX_PIPELINE, MHD_OPT_RADIX_INV_Z, MHD_OPT_RADIX_INV_Y, MHD_OPT_RADIX_FWD_Y,
+ MHD_OPT_RADIX_FWD_Z) = range(10)
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_ESTATE",
                 5: "MHD_ENONFINITE", 6: "MHD_ETIMEOUT", 7: "MHD_EBUSY"}
 
@@ -140,7 +141,7 @@ def load_library(path: str = LIBRARY):
     lib.mhd_pool_info.restype = I32
     lib.mhd_pool_info.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.mhd_autotune.restype = I32
-    lib.mhd_autotune.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_autotune.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]
     lib.mhd_tracers_set.restype = I32
     lib.mhd_tracers_set.argtypes = [P, I32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
     lib.mhd_tracers_get.restype = I32
@@ -320,13 +321,14 @@ def mhd_set_option(ctx: Context, option: int, value: int) -> None:
 
 
 def mhd_autotune(ctx: Context, reps: int = 5) -> dict:
-    """Time every tile width of the four column FFT passes and keep the fastest; returns
-    {"tiles": [4 widths], "ms": [4 mean ms per launch]} for (inverse z, inverse y, forward y,
-    forward z)."""
+    """Time every tile width (and, in the mixed mode, radix) of the four column FFT passes and
+    keep the fastest; returns {"tiles": [4], "radix": [4], "ms": [4 mean ms per launch]} for
+    (inverse z, inverse y, forward y, forward z)."""
     tiles = (ctypes.c_int32 * 4)()
+    radix = (ctypes.c_int32 * 4)()
     ms = (ctypes.c_double * 4)()
-    _check(ctx, load_library().mhd_autotune(ctx.handle, int(reps), tiles, ms))
-    return {"tiles": list(tiles), "ms": list(ms)}
+    _check(ctx, load_library().mhd_autotune(ctx.handle, int(reps), tiles, radix, ms))
+    return {"tiles": list(tiles), "radix": list(radix), "ms": list(ms)}
 
 
 def mhd_tracers_set(ctx: Context, inst: int, pos) -> None:
