@@ -331,6 +331,8 @@ def run_ours(args, name, cfg):
     pts = batch * n ** 3
     value = world * pts * K / (ms / 1e3)
     diag = mhd.mhd_diagnostics(ctx, 0)
+    mhd.mhd_destroy(ctx)  # the end-to-end context below must fit beside nothing else (1024^3: 150 GB)
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI with pinned host buffers: per step, H2D of every instance's
     # state (rho, u, B), one step, D2H of every instance's state (rho, m, B)
@@ -431,7 +433,6 @@ def run_ours(args, name, cfg):
             "final": {"t": diag["t"], "dt": diag["dt"], "step": diag["step"], "ke": diag["ke"], "me": diag["me"]},
         }
         print(json.dumps(line), flush=True)
-    mhd.mhd_destroy(ctx)
     if dist:
         dist.destroy_process_group()
     return 0
