@@ -120,9 +120,9 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     # (kernel, n, batch, precision): (bytes per launch, source hash, capture)
-    ("flux_x", 256, 1, "fp64"): (631_591_936 + 1_028_926_000, "c43e44e09251639d",
+    ("flux_x", 256, 1, "fp64"): (633_792_768 + 1_029_362_000, "4e1181400a066f05",
                                  "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
-    ("flux_x", 256, 1, "fp32"): (315_687_680 + 489_102_080, "c43e44e09251639d",
+    ("flux_x", 256, 1, "fp32"): (315_694_592 + 489_633_792, "4e1181400a066f05",
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
 }
 
