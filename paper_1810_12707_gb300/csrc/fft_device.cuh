@@ -279,6 +279,63 @@ __device__ __forceinline__ void dft_twiddled_fma(cplx64 *v, int m, const cplx64 
   }
 }
 
+// The first (untwiddled) FP64 radix-8 stage in the same radix-2 layer form: twiddle 1 everywhere
+// except the quarter turns (free) and w8 = c (1 + i DIR), c = sqrt(2)/2, on two butterflies of
+// layer 3 (two additions and four FMAs each): 52 FP64 instructions instead of 56.  With ZP the
+// inputs 3 and 4 are known zeros (zero-padded inverse transforms: the 2/3-rule gap K+1 .. N-K-1
+// always covers them, see pencil_fft) and layer 1 loses two butterflies: 44.
+template <int DIR, bool ZP>
+__device__ __forceinline__ void dft8_first_fma(cplx64 *v) {
+  constexpr double c = 0.70710678118654752440;  // cos(pi/4)
+  // layer 1 (twiddle 1): (v_j, v_j+4) <- (v_j + v_j+4, v_j - v_j+4)
+  if constexpr (ZP) {  // j = 0 with v4 = 0, j = 3 with v3 = 0
+    v[4] = v[0];
+    v[3] = v[7];
+    v[7] = cplx64{-v[7].re, -v[7].im};
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (ZP && (j == 0 || j == 3)) continue;
+    const cplx64 a = v[j], b = v[j + 4];
+    v[j] = c_add(a, b);
+    v[j + 4] = c_sub(a, b);
+  }
+  // layer 2: twiddle 1 on (0,2), (1,3); w4 on (4,6), (5,7)
+  {
+    const cplx64 a0 = v[0], a2 = v[2], a1 = v[1], a3 = v[3];
+    v[0] = c_add(a0, a2);
+    v[2] = c_sub(a0, a2);
+    v[1] = c_add(a1, a3);
+    v[3] = c_sub(a1, a3);
+    const cplx64 q6 = c_mul_i<DIR>(v[6]), q7 = c_mul_i<DIR>(v[7]);
+    const cplx64 a4 = v[4], a5 = v[5];
+    v[4] = c_add(a4, q6);
+    v[6] = c_sub(a4, q6);
+    v[5] = c_add(a5, q7);
+    v[7] = c_sub(a5, q7);
+  }
+  // layer 3: 1 on (0,1), w4 on (2,3), w8 on (4,5), w8 w4 on (6,7)
+  {
+    const cplx64 a0 = v[0], a1 = v[1];
+    v[0] = c_add(a0, a1);
+    v[1] = c_sub(a0, a1);
+    const cplx64 a2 = v[2], r3 = c_mul_i<DIR>(v[3]);
+    v[2] = c_add(a2, r3);
+    v[3] = c_sub(a2, r3);
+    const cplx64 z5 = {v[5].re - DIR * v[5].im, v[5].im + DIR * v[5].re};  // (1 + i DIR) v5
+    const cplx64 a4 = v[4];
+    v[4] = cplx64{fma(c, z5.re, a4.re), fma(c, z5.im, a4.im)};
+    v[5] = cplx64{fma(-c, z5.re, a4.re), fma(-c, z5.im, a4.im)};
+    const cplx64 z7 = c_mul_i<DIR>(cplx64{v[7].re - DIR * v[7].im, v[7].im + DIR * v[7].re});
+    const cplx64 a6 = v[6];
+    v[6] = cplx64{fma(c, z7.re, a6.re), fma(c, z7.im, a6.im)};
+    v[7] = cplx64{fma(-c, z7.re, a6.re), fma(-c, z7.im, a6.im)};
+  }
+  // (X0, X4, X2, X6, X1, X5, X3, X7) -> natural order
+  const cplx64 x0 = v[0], x4 = v[1], x2 = v[2], x6 = v[3], x1 = v[4], x5 = v[5], x3 = v[6], x7 = v[7];
+  v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
+}
+
 // ---- values per thread ----
 // FP32 pencils: 16 values per thread (radix 16: two shared-memory stages at N = 256 where radix 8
 // needs three; the FP32 passes are bound by instruction issue).  FP64: 8 (their cost is FP64
@@ -306,7 +363,7 @@ __host__ __device__ constexpr int fft_tpp() { return tpp_for<N, fft_vpt<C>()>();
 // Every thread of the block must call this (it contains group barriers); threads with
 // `active == false` only take part in the barriers.  The caller separates the transform from the
 // preceding writes and the following reads of the pencil with a block barrier.
-template <int N, int DIR, int NS, typename C, int VPT>
+template <int N, int DIR, int NS, typename C, int VPT, bool ZP>
 __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
     static_assert(VPT == 8 || (VPT == 16 && sizeof(C) == 8), "radix 16 is an FP32 option");
@@ -317,6 +374,11 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
     // FP64 stages with twiddles take them inside the butterflies (FMA form, fewer FP64
     // instructions); the others multiply on load.
     constexpr bool kFma = std::is_same<C, cplx64>::value && NS > 1;
+    // The first FP64 radix-8 stage: FMA layers, and with ZP the zero inputs 3 and 4 skipped.
+    constexpr bool kFirst = std::is_same<C, cplx64>::value && NS == 1 && R == 8;
+    constexpr int K = (N - 1) / 3;
+    static_assert(!(ZP && kFirst) || (3 * (N / 8) > K && 5 * (N / 8) - 1 < N - K),
+                  "inputs 3 and 4 of the first radix-8 stage must lie in the 2/3-rule gap");
     C v[VPT];
     if (active) {
 #pragma unroll
@@ -325,6 +387,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         const int k = j % NS;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
+          if (kFirst && ZP && (r == 3 || r == 4)) continue;  // zeros, never read
           C x = buf[sm_idx<C>(j + r * (N / R))];
           if (!kFma && NS > 1 && r > 0) {
             const C w = tw_load(tw + r * k * TWSTEP);
@@ -341,6 +404,8 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
         if constexpr (kFma) {
           dft_twiddled_fma<N, R, DIR>(reinterpret_cast<cplx64 *>(v) + b * R, ((t + b * TPP) % NS) * TWSTEP,
                                       reinterpret_cast<const cplx64 *>(tw));
+        } else if constexpr (kFirst) {
+          dft8_first_fma<DIR, ZP>(reinterpret_cast<cplx64 *>(v) + b * R);
         } else {
           dft_small<R, DIR, C>(v + b * R);
         }
@@ -352,14 +417,17 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
       }
     }
     group_sync<TPP>();
-    stockham_stages<N, DIR, NS * R, C, VPT>(buf, t, active, tw);
+    stockham_stages<N, DIR, NS * R, C, VPT, false>(buf, t, active, tw);
   }
 }
 
-// `t` in [0, N / VPT): the thread's index within its pencil's group.
-template <int N, int DIR, typename C, int VPT = fft_vpt<C>()>
+// `t` in [0, N / VPT): the thread's index within its pencil's group.  ZP: the pencil is
+// zero-padded by the 2/3 rule (elements K+1 .. N-K-1 are zero, K = (N-1)/3), as every inverse
+// transform of a truncated spectrum is; the FP64 first stage then skips the inputs it knows are
+// zero (they need not even be written).
+template <int N, int DIR, typename C, int VPT = fft_vpt<C>(), bool ZP = false>
 __device__ __forceinline__ void pencil_fft(C *buf, int t, bool active, const C *__restrict__ tw) {
-  stockham_stages<N, DIR, 1, C, VPT>(buf, t, active, tw);
+  stockham_stages<N, DIR, 1, C, VPT, ZP>(buf, t, active, tw);
 }
 
 // FFT index of kept index j (0..2K) along a truncated axis: j for j <= K, else j - (2K+1) + N.

@@ -66,7 +66,7 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   const int pencil = threadIdx.x / TPP;
   const int t = threadIdx.x - pencil * TPP;
   const bool active = pencil < tc && tile * tc + pencil < cols;
-  pencil_fft<N, DIR, CC, VPT>(sm + (active ? pencil : 0) * P, t, active, tw);
+  pencil_fft<N, DIR, CC, VPT, (DIR > 0)>(sm + (active ? pencil : 0) * P, t, active, tw);  // inverse: zero-padded
   __syncthreads();  // the store loop reads every pencil
 
   if (col_ok) {

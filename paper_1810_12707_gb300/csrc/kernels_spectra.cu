@@ -34,7 +34,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const cplx64 *__res
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR, cplx64, 8>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, cplx64, 8, (DIR > 0)>(ptr(active ? id : 0), t, active, tw);  // inverse: zero-padded
   }
   __syncthreads();
 }

@@ -59,6 +59,8 @@ constexpr int flux_min_blocks() {
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
 // N/8 threads of the block taking one pencil at a time.  Each pencil is touched by its group only,
 // so the stages synchronise per group; one block barrier closes the whole transform.
+// Every inverse (DIR = +1) transform here starts from a truncated half spectrum, so its pencil is
+// zero-padded by the 2/3 rule (see pencil_fft).
 template <int N, int DIR, int VPT, typename Ptr, typename C>
 __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
   constexpr int TPP = tpp_for<N, VPT>();
@@ -67,7 +69,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR, C, VPT>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, C, VPT, (DIR > 0)>(ptr(active ? id : 0), t, active, tw);
   }
   __syncthreads();  // the callers' next phase reads every pencil
 }
