@@ -1,5 +1,6 @@
 // fft_device.cuh -- device building blocks: complex arithmetic, small DFTs in registers, and the
-// Stockham pencil FFT executed by a group of N/8 threads on a pencil held in shared memory.
+// Stockham pencil FFT executed by a group of N/VPT threads (VPT = 8, or 16 in FP32) on a pencil
+// held in shared memory.
 //
 // Transform convention (both directions unscaled):  X[k] = sum_j x[j] exp(DIR * 2 pi i j k / N)
 // with DIR = -1 for the forward and +1 for the inverse transform.
@@ -166,7 +167,7 @@ template <typename C>
 __host__ __device__ constexpr int pencil_pitch(int n) { return sm_idx<C>(n) | 1; }
 
 // ---- barrier of one pencil's thread group ----
-// A pencil is transformed by the TPP = N/8 consecutive threads of its group and nobody else
+// A pencil is transformed by the TPP = N/VPT consecutive threads of its group and nobody else
 // touches it meanwhile, so the stages only need that group to synchronise: within a warp
 // (TPP <= 32) a warp barrier over the lanes that exist, otherwise a named barrier per group
 // (ids 1..15; id 0 is __syncthreads), falling back to the block barrier when there are more groups.

@@ -4,7 +4,7 @@
 // nslab * C columns; the C columns of a slab are contiguous in memory.  A block takes TC
 // consecutive columns of one slab, so every row of the tile is one coalesced segment of TC complex
 // values.  The tile is transposed into shared memory as TC pencils of length N (pitch N + 1, which
-// spreads consecutive pencils over the banks), transformed by TC groups of N/8 threads, and
+// spreads consecutive pencils over the banks), transformed by TC groups of N/VPT threads, and
 // written back.
 //   inverse (DIR = +1): L = 2K + 1 kept rows in, scattered to their FFT indices with the rest of
 //                       the pencil zero (the 2/3-rule truncation), all N rows out;
@@ -18,8 +18,8 @@
 namespace mhd {
 
 // CI, CO: element types in and out; CC: type of the transform arithmetic (= the output's).
-// A block has TC = 2^tsh columns and TC * N/8 threads: thread (l0, c) = (tid >> tsh, tid & (TC-1))
-// moves rows l0, l0 + N/8, ... of column c, so consecutive threads touch consecutive columns of a
+// A block has TC = 2^tsh columns and TC * N/VPT threads: thread (l0, c) = (tid >> tsh, tid & (TC-1))
+// moves rows l0, l0 + N/VPT, ... of column c, so consecutive threads touch consecutive columns of a
 // row (coalesced) and no index needs a division.
 // VPT: values per thread of the transform (8, or 16 for FP32), so N / VPT threads per column.
 template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>

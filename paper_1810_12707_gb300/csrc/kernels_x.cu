@@ -57,7 +57,7 @@ constexpr int flux_min_blocks() {
 }
 
 // Run the FFT of `np` pencils (pencil id -> shared-memory pointer `ptr(id)`) with every group of
-// N/8 threads of the block taking one pencil at a time.  Each pencil is touched by its group only,
+// N/VPT threads of the block taking one pencil at a time.  Each pencil is touched by its group only,
 // so the stages synchronise per group; one block barrier closes the whole transform.
 // Every inverse (DIR = +1) transform here starts from a truncated half spectrum, so its pencil is
 // zero-padded by the 2/3 rule (see pencil_fft).
