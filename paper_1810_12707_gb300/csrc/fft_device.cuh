@@ -93,7 +93,9 @@ __device__ __forceinline__ void dft8(C *v) {
 
 // Length 16 as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.  Length-4 DFTs over n1 for each n2, the
 // twiddles W16^(n2 k1), then length-4 DFTs over n2 for each k1 (W16 = exp(DIR 2 pi i / 16)).
-template <int DIR, typename C>
+// ZP: inputs 6..9 are zeros (zero-padded first stage; see pencil_fft): each first-layer length-4
+// DFT then has one zero input and loses a butterfly.
+template <int DIR, typename C, bool ZP = false>
 __device__ __forceinline__ void dft16(C *v) {
   using R = typename C::value_type;
   constexpr R c1 = (R)0.92387953251128675613;  // cos(pi/8)
@@ -103,7 +105,24 @@ __device__ __forceinline__ void dft16(C *v) {
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
     C t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
-    dft4<DIR>(t);
+    if constexpr (ZP) {
+      if (n2 < 2) {  // t[2] = v8 or v9 = 0: (t0 + t2, t0 - t2) = (t0, t0)
+        const C s1 = c_add(t[1], t[3]), d1 = c_mul_i<DIR>(c_sub(t[1], t[3]));
+        t[2] = c_sub(t[0], s1);
+        t[1] = c_add(t[0], d1);
+        t[3] = c_sub(t[0], d1);
+        t[0] = c_add(t[0], s1);
+      } else {  // t[1] = v6 or v7 = 0: (t1 + t3, t1 - t3) = (t3, -t3)
+        const C s0 = c_add(t[0], t[2]), d0 = c_sub(t[0], t[2]);
+        const C d1 = c_mul_i<DIR>(C{-t[3].re, -t[3].im});
+        t[0] = c_add(s0, t[3]);
+        t[2] = c_sub(s0, t[3]);
+        t[1] = c_add(d0, d1);
+        t[3] = c_sub(d0, d1);
+      }
+    } else {
+      dft4<DIR>(t);
+    }
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
   }
@@ -280,36 +299,37 @@ __device__ __forceinline__ void dft_twiddled_fma(cplx64 *v, int m, const cplx64 
   }
 }
 
-// The first (untwiddled) FP64 radix-8 stage in the same radix-2 layer form: twiddle 1 everywhere
+// The first (untwiddled) radix-8 stage in the same radix-2 layer form: twiddle 1 everywhere
 // except the quarter turns (free) and w8 = c (1 + i DIR), c = sqrt(2)/2, on two butterflies of
 // layer 3 (two additions and four FMAs each): 52 FP64 instructions instead of 56.  With ZP the
 // inputs 3 and 4 are known zeros (zero-padded inverse transforms: the 2/3-rule gap K+1 .. N-K-1
 // always covers them, see pencil_fft) and layer 1 loses two butterflies: 44.
-template <int DIR, bool ZP>
-__device__ __forceinline__ void dft8_first_fma(cplx64 *v) {
-  constexpr double c = 0.70710678118654752440;  // cos(pi/4)
+template <int DIR, bool ZP, typename C>
+__device__ __forceinline__ void dft8_first_fma(C *v) {
+  using R = typename C::value_type;
+  constexpr R c = (R)0.70710678118654752440;  // cos(pi/4)
   // layer 1 (twiddle 1): (v_j, v_j+4) <- (v_j + v_j+4, v_j - v_j+4)
   if constexpr (ZP) {  // j = 0 with v4 = 0, j = 3 with v3 = 0
     v[4] = v[0];
     v[3] = v[7];
-    v[7] = cplx64{-v[7].re, -v[7].im};
+    v[7] = C{-v[7].re, -v[7].im};
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (ZP && (j == 0 || j == 3)) continue;
-    const cplx64 a = v[j], b = v[j + 4];
+    const C a = v[j], b = v[j + 4];
     v[j] = c_add(a, b);
     v[j + 4] = c_sub(a, b);
   }
   // layer 2: twiddle 1 on (0,2), (1,3); w4 on (4,6), (5,7)
   {
-    const cplx64 a0 = v[0], a2 = v[2], a1 = v[1], a3 = v[3];
+    const C a0 = v[0], a2 = v[2], a1 = v[1], a3 = v[3];
     v[0] = c_add(a0, a2);
     v[2] = c_sub(a0, a2);
     v[1] = c_add(a1, a3);
     v[3] = c_sub(a1, a3);
-    const cplx64 q6 = c_mul_i<DIR>(v[6]), q7 = c_mul_i<DIR>(v[7]);
-    const cplx64 a4 = v[4], a5 = v[5];
+    const C q6 = c_mul_i<DIR>(v[6]), q7 = c_mul_i<DIR>(v[7]);
+    const C a4 = v[4], a5 = v[5];
     v[4] = c_add(a4, q6);
     v[6] = c_sub(a4, q6);
     v[5] = c_add(a5, q7);
@@ -317,23 +337,23 @@ __device__ __forceinline__ void dft8_first_fma(cplx64 *v) {
   }
   // layer 3: 1 on (0,1), w4 on (2,3), w8 on (4,5), w8 w4 on (6,7)
   {
-    const cplx64 a0 = v[0], a1 = v[1];
+    const C a0 = v[0], a1 = v[1];
     v[0] = c_add(a0, a1);
     v[1] = c_sub(a0, a1);
-    const cplx64 a2 = v[2], r3 = c_mul_i<DIR>(v[3]);
+    const C a2 = v[2], r3 = c_mul_i<DIR>(v[3]);
     v[2] = c_add(a2, r3);
     v[3] = c_sub(a2, r3);
-    const cplx64 z5 = {v[5].re - DIR * v[5].im, v[5].im + DIR * v[5].re};  // (1 + i DIR) v5
-    const cplx64 a4 = v[4];
-    v[4] = cplx64{fma(c, z5.re, a4.re), fma(c, z5.im, a4.im)};
-    v[5] = cplx64{fma(-c, z5.re, a4.re), fma(-c, z5.im, a4.im)};
-    const cplx64 z7 = c_mul_i<DIR>(cplx64{v[7].re - DIR * v[7].im, v[7].im + DIR * v[7].re});
-    const cplx64 a6 = v[6];
-    v[6] = cplx64{fma(c, z7.re, a6.re), fma(c, z7.im, a6.im)};
-    v[7] = cplx64{fma(-c, z7.re, a6.re), fma(-c, z7.im, a6.im)};
+    const C z5 = {v[5].re - DIR * v[5].im, v[5].im + DIR * v[5].re};  // (1 + i DIR) v5
+    const C a4 = v[4];
+    v[4] = C{fma(c, z5.re, a4.re), fma(c, z5.im, a4.im)};
+    v[5] = C{fma(-c, z5.re, a4.re), fma(-c, z5.im, a4.im)};
+    const C z7 = c_mul_i<DIR>(C{v[7].re - DIR * v[7].im, v[7].im + DIR * v[7].re});
+    const C a6 = v[6];
+    v[6] = C{fma(c, z7.re, a6.re), fma(c, z7.im, a6.im)};
+    v[7] = C{fma(-c, z7.re, a6.re), fma(-c, z7.im, a6.im)};
   }
   // (X0, X4, X2, X6, X1, X5, X3, X7) -> natural order
-  const cplx64 x0 = v[0], x4 = v[1], x2 = v[2], x6 = v[3], x1 = v[4], x5 = v[5], x3 = v[6], x7 = v[7];
+  const C x0 = v[0], x4 = v[1], x2 = v[2], x6 = v[3], x1 = v[4], x5 = v[5], x3 = v[6], x7 = v[7];
   v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
 }
 
@@ -375,11 +395,15 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
     // FP64 stages with twiddles take them inside the butterflies (FMA form, fewer FP64
     // instructions); the others multiply on load.
     constexpr bool kFma = std::is_same<C, cplx64>::value && NS > 1;
-    // The first FP64 radix-8 stage: FMA layers, and with ZP the zero inputs 3 and 4 skipped.
-    constexpr bool kFirst = std::is_same<C, cplx64>::value && NS == 1 && R == 8;
+    // The first radix-8 stage: FMA layers, and with ZP the zero inputs 3 and 4 skipped; the first
+    // radix-16 stage with ZP skips its zero inputs 6..9.
+    constexpr bool kFirst = NS == 1 && R == 8;
+    constexpr bool kFirst16 = NS == 1 && R == 16 && ZP;
     constexpr int K = (N - 1) / 3;
     static_assert(!(ZP && kFirst) || (3 * (N / 8) > K && 5 * (N / 8) - 1 < N - K),
                   "inputs 3 and 4 of the first radix-8 stage must lie in the 2/3-rule gap");
+    static_assert(!kFirst16 || (6 * (N / 16) > K && 10 * (N / 16) - 1 < N - K),
+                  "inputs 6..9 of the first radix-16 stage must lie in the 2/3-rule gap");
     C v[VPT];
     if (active) {
 #pragma unroll
@@ -389,6 +413,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           if (kFirst && ZP && (r == 3 || r == 4)) continue;  // zeros, never read
+          if (kFirst16 && r >= 6 && r <= 9) continue;
           C x = buf[sm_idx<C>(j + r * (N / R))];
           if (!kFma && NS > 1 && r > 0) {
             const C w = tw_load(tw + r * k * TWSTEP);
@@ -406,7 +431,9 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
           dft_twiddled_fma<N, R, DIR>(reinterpret_cast<cplx64 *>(v) + b * R, ((t + b * TPP) % NS) * TWSTEP,
                                       reinterpret_cast<const cplx64 *>(tw));
         } else if constexpr (kFirst) {
-          dft8_first_fma<DIR, ZP>(reinterpret_cast<cplx64 *>(v) + b * R);
+          dft8_first_fma<DIR, ZP>(v + b * R);
+        } else if constexpr (kFirst16) {
+          dft16<DIR, C, true>(v + b * R);
         } else {
           dft_small<R, DIR, C>(v + b * R);
         }
