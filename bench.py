@@ -120,9 +120,9 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     # (kernel, n, batch, precision): (bytes per launch, source hash, capture)
-    ("flux_x", 256, 1, "fp64"): (633_792_768 + 1_029_362_000, "4e1181400a066f05",
+    ("flux_x", 256, 1, "fp64"): (632_152_064 + 1_029_261_000, "fe26dad993c76e32",
                                  "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
-    ("flux_x", 256, 1, "fp32"): (315_694_592 + 489_633_792, "4e1181400a066f05",
+    ("flux_x", 256, 1, "fp32"): (315_689_728 + 489_947_136, "fe26dad993c76e32",
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
 }
 
