@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import sympy as sp
 
+import test_oracle_golden as gold
 import test_oracle_integrators as integ
 import test_oracle_invariants as inv
 import test_oracle_linear_waves as lw
@@ -50,6 +51,9 @@ MUTANTS = [
     ("Boris half step", "t[a] = B[a] * dt / 2.0;", "t[a] = B[a] * dt;"),
     ("Boris s factor", "s[a] = 2.0 * t[a] / (1.0 + t2);", "s[a] = t[a];"),
     ("Boris cross sign", "vd[1] = v[1] + (v[2] * t[0] - v[0] * t[2]);", "vd[1] = v[1] - (v[2] * t[0] - v[0] * t[2]);"),
+    ("kinetic energy without 1/2", "s[0] += 0.5 * rho * u2;", "s[0] += rho * u2;"),
+    ("kinetic energy without density", "s[0] += 0.5 * rho * u2;", "s[0] += 0.5 * u2;"),
+    ("magnetic energy without 1/2", "s[1] += 0.5 * b2;", "s[1] += b2;"),
     ("position with old velocity", "v[a] = vn[a];\n      p[a] = wrap_2pi(p[a] + vn[a] * dt);",
      "p[a] = wrap_2pi(p[a] + v[a] * dt);\n      v[a] = vn[a];"),
 ]
@@ -150,6 +154,8 @@ def _battery(om, lib):
     # tracer particles
     failed += trc.interpolation_failures(om, lib)
     failed += trc.push_failures(om, lib)
+    # exact averages of the paper's initial flows
+    failed += gold.golden_failures(om, lib)
     return failed
 
 
