@@ -218,7 +218,9 @@ MHD_API mhd_status mhd_spectra(mhd_ctx *ctx, int32_t inst, double *ek, double *e
 /* Checkpoint support.  The restartable state of an instance is its state spectra, its history
  * (the previous step's RHS spectra), and (t, dt_prev, step).  Both calls move
  * mhd_checkpoint_doubles(ctx) doubles through `buf` (host or device), in a layout private to the
- * library that mhd_restore accepts for the same n and precision.  Both synchronise. */
+ * library that mhd_restore accepts for the same n and precision.  mhd_checkpoint writes every one
+ * of those doubles (unused slots as zeros), so equal states give byte-identical checkpoints.  Both
+ * synchronise. */
 MHD_API size_t mhd_checkpoint_doubles(const mhd_ctx *ctx);
 MHD_API mhd_status mhd_checkpoint(mhd_ctx *ctx, int32_t inst, double *buf, int32_t on_device);
 MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, int32_t on_device);

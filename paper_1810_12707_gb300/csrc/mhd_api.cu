@@ -1127,8 +1127,15 @@ mhd_status mhd_checkpoint(mhd_ctx *c, int32_t inst, double *buf, int32_t on_devi
     if (on_device) CK(cudaMemsetAsync(buf + 3 * sp, 0, sp * sizeof(cplx32), c->stream));
     else memset(buf + 3 * sp, 0, sp * sizeof(cplx32));
   }
-  static_assert(sizeof(mhd::TimeState) <= 8 * sizeof(double), "time state fits the tail");
+  static_assert(sizeof(mhd::TimeState) % sizeof(double) == 0 && sizeof(mhd::TimeState) <= 8 * sizeof(double),
+                "time state fits the tail");
   CK(cudaMemcpyAsync(buf + 4 * sp, c->ts + inst, sizeof(mhd::TimeState), k, c->stream));
+  // the rest of the tail is written as zeros, so equal states give byte-identical checkpoints
+  constexpr size_t used = sizeof(mhd::TimeState) / sizeof(double);
+  if (used < 8) {
+    if (on_device) CK(cudaMemsetAsync(buf + 4 * sp + used, 0, (8 - used) * sizeof(double), c->stream));
+    else memset(buf + 4 * sp + used, 0, (8 - used) * sizeof(double));
+  }
   CK(cudaStreamSynchronize(c->stream));
   return MHD_OK;
 }
