@@ -138,6 +138,17 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
   const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
   R smax = 0;
+  // FP64: the maximum that blocks of this pass have already published is a lower bound of the
+  // pass's maximum.  A point whose FP32 estimate of |u| + c_f lies below `screen` (that bound
+  // less 1e-6 relative and 1e-18 absolute, above the estimate's worst error of about 3e-7
+  // relative) cannot raise it, so its exact speed (two FP64 square roots) is not formed.  The
+  // pass still yields the exact maximum, whichever blocks ran first; a NaN or an infinite
+  // estimate always takes the exact path.
+  float screen = 0.f;
+  if constexpr (sizeof(R) == 8) {
+    const double lb = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long *>(smax_bits + inst));
+    screen = (float)(lb * (1.0 - 1e-6) - 1e-18);
+  }
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
     C *b = sm + p * 12 * P + sm_idx<C>(j);
@@ -180,8 +191,16 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
       bd[2 * 9 * P + h] = ux;
       bd[2 * 10 * P + h] = uy;
       bd[2 * 11 * P + h] = uz;
-      const R s = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + b2 * ir);
-      smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
+      const R u2 = ux * ux + uy * uy + uz * uz, c2 = cs2 + b2 * ir;
+      if constexpr (sizeof(R) == 8) {
+        if (!(sqrtf((float)u2) + sqrtf((float)c2) < screen)) {
+          const R s = sqrt(u2) + sqrt(c2);
+          smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
+        }
+      } else {
+        const R s = sqrt(u2) + sqrt(c2);
+        smax = (s != s || s > smax) ? s : smax;
+      }
     }
   }
   __syncthreads();

@@ -608,6 +608,10 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   CF *w2 = reinterpret_cast<CF *>(c->W2);
   LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0]));
   LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1], c->radix[1]));
+  // The CFL maximum of an advancing pass goes to the first slot (zero at the pass's start: the
+  // dt kernel resets it after reading).  Evaluations that take no step (later RK stages, the
+  // corrector, mhd_rhs) write to a second slot that nothing reads; its maxima are not exact
+  // (the flux pass screens against the slot's earlier content), which changes no result.
   unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
   LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid));
   if (advance) {

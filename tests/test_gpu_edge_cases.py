@@ -122,3 +122,44 @@ def test_unsupported_sizes_and_parameters_are_refused(lib):
         with pytest.raises(lib.MhdError):
             lib.mhd_get_spectrum(ctx, 0, field)
     lib.mhd_destroy(ctx)
+
+
+def cfl_states(n):
+    """States that stress the exactness of the CFL maximum: speeds tied to 1e-9, 1e-6 and 1e-4
+    relative (around the 1e-6 margin of the flux pass's FP32 screening), a peak in the last
+    z-planes (reached by the last blocks of the pass), and a turbulent Orszag-Tang state."""
+    X, Y, Z = inputs.grid(n)
+    zl = Z.max()
+    one = np.ones((n, n, n))
+    zero = np.zeros((3, n, n, n))
+    out = []
+    for eps in (1e-9, 1e-6, 1e-4):
+        u = zero.copy()
+        u[0] = 1.0 + eps * np.sin(X) * np.cos(2 * Y) * np.sin(3 * Z)
+        out.append((one, u, zero))
+    u = zero.copy()
+    u[0] = 1.0 + 0.3 * ((1.0 + np.cos(Z - zl)) / 2) ** 4  # single peak at the last z-plane
+    b = zero.copy()
+    b[2] = 0.5 + 0.1 * np.sin(X + Y)
+    out.append((1.0 + 0.1 * np.cos(Y), u, b))
+    ic = inputs.orszag_tang(n, seed=12, mach=0.5)
+    out.append((ic.rho, ic.u, ic.b))
+    return out
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_cfl_maximum_is_exact(lib, n):
+    """The step size equals the CFL formula at the exact grid maximum of |u| + c_f, taken on the
+    host from the same state (FP64)."""
+    cs, nu = 0.9, 1e-4
+    k = (n - 1) // 3
+    for rho, u, b in cfl_states(n):
+        ctx = lib.mhd_init(n, [(nu, nu, cs)])
+        lib.mhd_set_state(ctx, 0, rho, u, b)
+        r, m, bb = lib.mhd_get_state(ctx, 0)
+        speed = np.sqrt(np.sum((m / r) ** 2, axis=0)) + np.sqrt(cs * cs + np.sum(bb * bb, axis=0) / r)
+        expect = min(0.2 * (2 * np.pi / n) / speed.max(), 0.5 / (nu * k * k))
+        lib.mhd_step(ctx, 1)
+        got = lib.mhd_diagnostics(ctx, 0)["dt"]
+        lib.mhd_destroy(ctx)
+        assert abs(got - expect) <= 1e-14 * expect
