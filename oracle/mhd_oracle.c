@@ -823,6 +823,11 @@ int or_num_shells(int n) {
  *   stats[0]      theta' = sqrt(<(div u_D)^2>), div u_D formed on the grid
  *   stats[1]      S_3 = <d^3> / <d^2>^{3/2},  d = du_x/dx of u_D, on the grid
  *   stats[2..3]   <d^2>, <d^3>
+ *   stats[4]      kinetic helicity <u_D . w>, w = curl u_D, both formed on the grid
+ *   stats[5]      magnetic helicity <A . B> with the periodic, mean-free vector potential of the
+ *                 Coulomb gauge (curl A = B for solenoidal B, div A = 0): A_hat = i k x B_hat / |k|^2
+ *                 for k != 0, A_hat(0) = 0; A and B formed on the grid
+ *   stats[6]      max over the grid of |div B| (div B formed on the grid)
  * `nshell` must equal or_num_shells(n).
  */
 int or_spectra(or_ctx *c, int nshell, double *ek, double *em, double *stats) {
@@ -892,6 +897,52 @@ int or_spectra(or_ctx *c, int nshell, double *ek, double *em, double *stats) {
   stats[1] = m3 / pow(m2, 1.5);
   stats[2] = m2;
   stats[3] = m3;
+  /* helicities: per component a, the field on the grid (into g) and the curl or potential
+   * component on the grid (in tmp), multiplied point by point */
+  double hk = 0.0, hm = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int b1 = (a + 1) % 3, b2 = (a + 2) % 3; /* (curl f)_a = d_b1 f_b2 - d_b2 f_b1 */
+    for (int pass = 0; pass < 2; ++pass) {
+      /* pass 0: u_D and w = curl u_D; pass 1: B and A */
+      for (size_t i = 0; i < n3; ++i) c->tmp[i] = pass == 0 ? uh[a][i] : c->state[F_BX + a][i];
+      or_fft3d(c->tmp, n, +1);
+      for (size_t i = 0; i < n3; ++i) g[i] = creal(c->tmp[i]);
+      for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+          for (int x = 0; x < n; ++x) {
+            const size_t i = ((size_t)z * n + y) * n + x;
+            const double k[3] = {wavenumber(x, n), wavenumber(y, n), wavenumber(z, n)};
+            const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+            const cplx f1 = pass == 0 ? uh[b1][i] : c->state[F_BX + b1][i];
+            const cplx f2 = pass == 0 ? uh[b2][i] : c->state[F_BX + b2][i];
+            cplx v = I * (k[b1] * f2 - k[b2] * f1);
+            if (pass == 1) v = k2 > 0.0 ? v / k2 : 0.0;
+            c->tmp[i] = v;
+          }
+      or_fft3d(c->tmp, n, +1);
+      double acc = 0.0;
+      for (size_t i = 0; i < n3; ++i) acc += g[i] * creal(c->tmp[i]);
+      if (pass == 0) hk += acc;
+      else hm += acc;
+    }
+  }
+  stats[4] = hk / (double)n3;
+  stats[5] = hm / (double)n3;
+  /* div B on the grid */
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const size_t i = ((size_t)z * n + y) * n + x;
+        c->tmp[i] = I * (wavenumber(x, n) * c->state[F_BX][i] + wavenumber(y, n) * c->state[F_BY][i] +
+                         wavenumber(z, n) * c->state[F_BZ][i]);
+      }
+  or_fft3d(c->tmp, n, +1);
+  double dmax = 0.0;
+  for (size_t i = 0; i < n3; ++i) {
+    const double v = fabs(creal(c->tmp[i]));
+    if (!(v <= dmax)) dmax = v;
+  }
+  stats[6] = dmax;
   free(g);
   for (int a = 0; a < 3; ++a) free(uh[a]);
   return 0;

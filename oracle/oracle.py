@@ -269,10 +269,12 @@ class Oracle:
         return pos, vel
 
     def spectra(self) -> dict:
-        """Shell spectra ek, em (index = shell) and theta', S3, <d^2>, <d^3> of d = du_x/dx."""
+        """Shell spectra ek, em (index = shell), theta', S3, <d^2>, <d^3> of d = du_x/dx, the
+        kinetic and magnetic helicities and max |div B| (see ``or_spectra``)."""
         ns = int(self._lib.or_num_shells(self.n))
-        ek, em, st = np.zeros(ns), np.zeros(ns), np.zeros(4)
+        ek, em, st = np.zeros(ns), np.zeros(ns), np.zeros(7)
         rc = self._lib.or_spectra(self._h, ns, _dp(ek), _dp(em), _dp(st))
         if rc != 0:
             raise RuntimeError(f"or_spectra failed ({rc})")
-        return {"ek": ek, "em": em, "theta": st[0], "s3": st[1], "d2": st[2], "d3": st[3]}
+        return {"ek": ek, "em": em, "theta": st[0], "s3": st[1], "d2": st[2], "d3": st[3],
+                "kin_hel": st[4], "mag_hel": st[5], "divb_max": st[6]}

@@ -8,6 +8,9 @@ by hand from the printed formulas and parameters.
   B_0 and div B = 0;
 * the oracle's forward transform with the curl taken as i k x u_hat gives the enstrophy and the
   kinetic helicity by Parseval (k0 = 1 as printed, and 2), and w = k0 u on the Beltrami rows;
+* the oracle's helicity diagnostics (formed on the grid): <u . w> = k0 hel for the flow as
+  velocity, and <A . B> = hel / k0 for the flow as magnetic field (all its modes lie at
+  |k| = k0, so A = curl B / k0^2; the Taylor-Green row has hel = 0 at |k|^2 = 3 k0^2);
 * on the Beltrami rows at rho = 1, B = 0 the advection u . grad u = grad(|u|^2 / 2) - u x w is a
   gradient, so the curl of the momentum RHS is exactly -nu k0^2 w;
 * the energy-exchange initial states (Alfven Mach number 1) have equal kinetic and magnetic
@@ -85,6 +88,15 @@ def golden_failures(om, lib=None):
                 failed.append(f"{row['name']} helicity")
             if row["beltrami"] and np.max(np.abs(wh - k0 * uh)) > 1e-14:
                 failed.append(f"{row['name']} beltrami")
+            # helicities of the oracle's spectra call: the flow as velocity gives <u . w> = k0 hel;
+            # as magnetic field, all its modes at |k| = k0 (or hel = 0), <A . B> = <B . curl B> / k0^2
+            o = om.Oracle(n, nu, nu, 1.0, lib=lib)
+            o.set_state(one, u, u)
+            r = o.spectra()
+            if abs(r["kin_hel"] - k0 * float(row["hel"])) > 1e-12:
+                failed.append(f"{row['name']} kinetic helicity")
+            if abs(r["mag_hel"] - float(row["hel"]) / k0) > 1e-12 or r["divb_max"] > 1e-13:
+                failed.append(f"{row['name']} magnetic helicity")
             # the momentum RHS of a Beltrami flow: only viscosity reaches the vorticity
             if row["beltrami"]:
                 o = om.Oracle(n, nu, nu, 1.0, lib=lib)

@@ -54,6 +54,10 @@ MUTANTS = [
     ("kinetic energy without 1/2", "s[0] += 0.5 * rho * u2;", "s[0] += rho * u2;"),
     ("kinetic energy without density", "s[0] += 0.5 * rho * u2;", "s[0] += 0.5 * u2;"),
     ("magnetic energy without 1/2", "s[1] += 0.5 * b2;", "s[1] += b2;"),
+    ("helicity curl sign", "cplx v = I * (k[b1] * f2 - k[b2] * f1);", "cplx v = I * (k[b2] * f1 - k[b1] * f2);"),
+    ("magnetic helicity without 1/k^2", "if (pass == 1) v = k2 > 0.0 ? v / k2 : 0.0;", "if (pass == 1) v = k2 > 0.0 ? v : 0.0;"),
+    ("div B max drops y", "c->tmp[i] = I * (wavenumber(x, n) * c->state[F_BX][i] + wavenumber(y, n) * c->state[F_BY][i]",
+     "c->tmp[i] = I * (wavenumber(x, n) * c->state[F_BX][i] + 0.0 * c->state[F_BY][i]"),
     ("position with old velocity", "v[a] = vn[a];\n      p[a] = wrap_2pi(p[a] + vn[a] * dt);",
      "p[a] = wrap_2pi(p[a] + v[a] * dt);\n      v[a] = vn[a];"),
 ]

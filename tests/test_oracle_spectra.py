@@ -6,8 +6,10 @@ and the initial spectrum E(k) = A k^4 exp(-2 k^2 / k0^2)).
   trigonometric velocities written out by hand;
 * Parseval: the shell sums add up to the oracle's grid energies (kinetic only for rho = 1);
 * brute force: on a random state with non-uniform density the spectra, theta' (by Parseval, a
-  different route from the oracle's grid average) and S_3 from numpy's FFT of the oracle's own
-  real-space fields;
+  different route from the oracle's grid average), S_3, the kinetic and magnetic helicities (by
+  Parseval; the oracle forms them on the grid) and max |div B| from numpy's FFT of the oracle's
+  own real-space fields;
+* max |div B| of a trigonometric field written out by hand;
 * the E(k) initial condition has, shell by shell, the requested spectrum.
 """
 import numpy as np
@@ -62,6 +64,14 @@ def closed_form_failures(om, lib=None):
     m2, m3 = 0.5 + 2 * beta * beta, 1.5 * beta
     if abs(r["d2"] - m2) > 1e-13 or abs(r["d3"] - m3) > 1e-13 or abs(r["s3"] - m3 / m2 ** 1.5) > 1e-13:
         failed.append("skewness")
+    # max |div B| of B = (a sin 2x, c cos 3y, 0): div B = 2a cos 2x - 3c sin 3y reaches 2a + 3c at
+    # the grid points x = 0, y = pi/2
+    b = zero.copy()
+    b[0] = 0.7 * np.sin(2 * X)
+    b[1] = 0.4 * np.cos(3 * Y)
+    r = _state(om, n, one, zero, b, lib).spectra()
+    if abs(r["divb_max"] - (2 * 0.7 + 3 * 0.4)) > 1e-13:
+        failed.append("div B max")
     return failed
 
 
@@ -72,7 +82,7 @@ def brute_force_failures(om, lib=None, n=16, seed=3):
     X, Y, Z = inputs.grid(n)
     rho = 1.0 + 0.3 * np.cos(X + 2 * Y) * np.sin(Z - 0.4) + 0.1 * np.sin(3 * Z)
     u = inputs.random_solenoidal(n, rng, kmax2=9) + 0.2 * np.stack([np.sin(2 * X), np.cos(Y), 0 * X])
-    b = inputs.random_solenoidal(n, rng, kmax2=9)
+    b = inputs.random_solenoidal(n, rng, kmax2=9) + 0.1 * np.stack([np.cos(X - Z), 0 * X, np.sin(2 * Z)])
     o = _state(om, n, rho, u, b, lib)
     r = o.spectra()
     rho_g, m_g, b_g = o.get_state()
@@ -94,6 +104,22 @@ def brute_force_failures(om, lib=None, n=16, seed=3):
     m2, m3 = np.mean(d ** 2), np.mean(d ** 3)
     if abs(m2 - r["d2"]) > 1e-12 * m2 or abs(m3 - r["d3"]) > 1e-11 * m2 ** 1.5:
         failed.append("brute skewness")
+    # helicities by Parseval over numpy's spectra (the oracle forms them on the grid), and
+    # max |div B| from numpy's inverse transform
+    def curl(fh):
+        return np.stack([1j * (KY * fh[2] - KZ * fh[1]), 1j * (KZ * fh[0] - KX * fh[2]),
+                         1j * (KX * fh[1] - KY * fh[0])])
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    ah = curl(bh) / np.where(k2 > 0, k2, 1.0)
+    hk = float(np.real(np.sum(np.conj(uh) * curl(uh))))
+    hm = float(np.real(np.sum(np.conj(ah) * bh)))
+    dmax = np.max(np.abs(np.real(np.fft.ifftn(1j * (KX * bh[0] + KY * bh[1] + KZ * bh[2])) * n ** 3)))
+    if abs(hk - r["kin_hel"]) > 1e-12 * np.sum(np.abs(uh) ** 2) * n:
+        failed.append("brute kinetic helicity")
+    if abs(hm - r["mag_hel"]) > 1e-12 * np.sum(np.abs(bh) ** 2):
+        failed.append("brute magnetic helicity")
+    if abs(dmax - r["divb_max"]) > 1e-12 * dmax:
+        failed.append("brute div B max")
     return failed
 
 
