@@ -191,12 +191,17 @@ MHD_API mhd_status mhd_tracers_get(mhd_ctx *ctx, int32_t inst, double *pos, doub
 MHD_API int64_t mhd_tracers_count(mhd_ctx *ctx, int32_t inst);
 
 /* Velocity-derivative statistics of the hydrodynamic-flow section, all of the dealiased velocity
- * u = m / rho (its spectrum cut to the kept modes): */
+ * u = m / rho (its spectrum cut to the kept modes), and the helicities and div B of the state: */
 typedef struct {
-  double theta; /* theta' = <(div u)^2>^(1/2) */
-  double s3;    /* S_3 = <d^3> / <d^2>^(3/2), d = du_x/dx */
-  double d2;    /* <d^2> */
-  double d3;    /* <d^3> */
+  double theta;    /* theta' = <(div u)^2>^(1/2) */
+  double s3;       /* S_3 = <d^3> / <d^2>^(3/2), d = du_x/dx */
+  double d2;       /* <d^2> */
+  double d3;       /* <d^3> */
+  double kin_hel;  /* kinetic helicity <u . curl u> */
+  double mag_hel;  /* magnetic helicity <A . B>, A the periodic mean-free vector potential of the
+                      Coulomb gauge: A_hat = i k x B_hat / |k|^2 (k != 0), so curl A = B for a
+                      solenoidal B */
+  double divb_max; /* max over the grid of |div B| */
 } mhd_flow_stats;
 
 /* Number of spectral shells of an n^3 grid, round(sqrt(3) k_max) + 1 with k_max = floor((n-1)/3);
@@ -204,7 +209,7 @@ typedef struct {
 MHD_API int32_t mhd_num_shells(int32_t n);
 
 /* Shell spectra of instance `inst` (paper, section "for hydrodynamic flow": kinetic and magnetic
- * energy spectra, theta' and S_3).  Mode k belongs to shell round(|k|); per shell s,
+ * energy spectra, theta' and S_3; the helicities and max |div B| of the same state).  Mode k belongs to shell round(|k|); per shell s,
  *   ek[s] = sum |u_hat(k)|^2 / 2,   em[s] = sum |B_hat(k)|^2 / 2
  * over the kept modes of the full spectrum (both k and -k), with f_hat(k) = N^-3 sum f e^{-ik.x},
  * so sum_s em[s] = <|B|^2>/2 and, when rho = 1, sum_s ek[s] = <|u|^2>/2.

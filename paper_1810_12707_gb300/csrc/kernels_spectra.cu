@@ -1,6 +1,7 @@
 // kernels_spectra.cu -- shell spectra and velocity-derivative statistics of one instance (paper,
 // section "for hydrodynamic flow": theta' = <(du_i/dx_i)^2>^(1/2) and the skewness
-// S_3 = <(du_1/dx_1)^3> / <(du_1/dx_1)^2>^(3/2); kinetic and magnetic energy spectra).
+// S_3 = <(du_1/dx_1)^3> / <(du_1/dx_1)^2>^(3/2); kinetic and magnetic energy spectra), with the
+// kinetic and magnetic helicities and the largest |div B| on the grid.
 //
 // The velocity u = m / rho exists only on the grid, so one fused x pass brings rho and m to real
 // rows (inverse x), divides, and sends u back (forward x); the y and z column passes then give the
@@ -105,19 +106,31 @@ __global__ void __launch_bounds__(kMaxThreads) velocity_x_kernel(const cplx64 *_
   }
 }
 
-// One block per shell s.  uh, bh: 3 truncated spectra each (stride `spec`); out[s][3] =
-// (sum w |u_hat|^2 / 2, sum w |B_hat|^2 / 2, sum w |k . u_hat|^2) over the shell, with w = 1 on the
-// k_x = 0 plane and 2 elsewhere (the half spectrum stands for k and -k); dh = i k_x u_hat_x on
+// Re(conj(f) . (i k x f)) of one mode: with t = k x f, (i t)_a = (-Im t_a, Re t_a).
+__device__ __forceinline__ double curl_dot(double kx, double ky, double kz, cplx64 fx, cplx64 fy, cplx64 fz) {
+  const cplx64 tx{ky * fz.re - kz * fy.re, ky * fz.im - kz * fy.im};
+  const cplx64 ty{kz * fx.re - kx * fz.re, kz * fx.im - kx * fz.im};
+  const cplx64 tz{kx * fy.re - ky * fx.re, kx * fy.im - ky * fx.im};
+  return (fx.im * tx.re - fx.re * tx.im) + (fy.im * ty.re - fy.re * ty.im) + (fz.im * tz.re - fz.re * tz.im);
+}
+
+// One block per shell s.  uh, bh: 3 truncated spectra each (stride `spec`); out[s][5] =
+// (sum w |u_hat|^2 / 2, sum w |B_hat|^2 / 2, sum w |k . u_hat|^2, sum w Re(conj(u_hat) . i k x u_hat),
+// sum w Re(conj(B_hat) . i k x B_hat) / |k|^2) over the shell, with w = 1 on the k_x = 0 plane and 2
+// elsewhere (the half spectrum stands for k and -k).  By Parseval the last two are the shell's
+// shares of the kinetic helicity <u . curl u> and of the magnetic helicity <A . B>, A_hat =
+// i k x B_hat / |k|^2 (Coulomb gauge, A_hat(0) = 0).  dh = i k_x u_hat_x and gh = i k . B_hat on
 // every mode (each mode is visited by exactly one shell's block).
 __global__ void __launch_bounds__(256) shell_kernel(const cplx64 *__restrict__ uh, const cplx64 *__restrict__ bh,
-                                                    cplx64 *__restrict__ dh, double *__restrict__ out, int K) {
+                                                    cplx64 *__restrict__ dh, cplx64 *__restrict__ gh,
+                                                    double *__restrict__ out, int K) {
   __shared__ double red[32];
   const int NX = K + 1, NK = 2 * K + 1;
   const size_t spec = (size_t)NK * NK * NX;
   const int s = blockIdx.x;
   const long long lo_b = s == 0 ? 0 : (long long)(2 * s - 1) * (2 * s - 1);
   const long long hi_b = (long long)(2 * s + 1) * (2 * s + 1);
-  double ek = 0.0, em = 0.0, th = 0.0;
+  double ek = 0.0, em = 0.0, th = 0.0, hk = 0.0, hm = 0.0;
   for (int r = threadIdx.x; r < NK * NK; r += blockDim.x) {
     const int kz = kept_wave(r / NK, K), ky = kept_wave(r % NK, K);
     const long long q4 = 4LL * (ky * ky + kz * kz);
@@ -138,15 +151,24 @@ __global__ void __launch_bounds__(256) shell_kernel(const cplx64 *__restrict__ u
       const double dr = kx * ux.re + ky * uy.re + kz * uz.re, di = kx * ux.im + ky * uy.im + kz * uz.im;
       th += w * (dr * dr + di * di);
       dh[m] = cplx64{-kx * ux.im, kx * ux.re};
+      hk += w * curl_dot(kx, ky, kz, ux, uy, uz);
+      const long long k2 = (long long)kx * kx + (long long)ky * ky + (long long)kz * kz;
+      if (k2 > 0) hm += w * curl_dot(kx, ky, kz, bx, by, bz) / (double)k2;
+      const double gr = kx * bx.re + ky * by.re + kz * bz.re, gi = kx * bx.im + ky * by.im + kz * bz.im;
+      gh[m] = cplx64{-gi, gr};
     }
   }
   const double a = block_sum(ek, red);
   const double b = block_sum(em, red);
   const double c = block_sum(th, red);
+  const double e = block_sum(hk, red);
+  const double f = block_sum(hm, red);
   if (threadIdx.x == 0) {
-    out[3 * s + 0] = a;
-    out[3 * s + 1] = b;
-    out[3 * s + 2] = c;
+    out[5 * s + 0] = a;
+    out[5 * s + 1] = b;
+    out[5 * s + 2] = c;
+    out[5 * s + 3] = e;
+    out[5 * s + 4] = f;
   }
 }
 
@@ -165,6 +187,16 @@ __global__ void __launch_bounds__(256) moments_kernel(const double *__restrict__
     part[2 * blockIdx.x] = a;
     part[2 * blockIdx.x + 1] = b;
   }
+}
+
+// part[block] = max |v| over a fixed grid-stride share of the n values of v (a NaN is kept).
+__global__ void __launch_bounds__(256) absmax_kernel(const double *__restrict__ v, size_t n, double *__restrict__ part) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = nan_max(m, fabs(v[i]));
+  const double r = block_nan_max(m, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
 namespace {
@@ -205,9 +237,14 @@ cudaError_t launch_velocity_x(const cplx64 *in, cplx64 *out, const Dims &d, cons
   }
 }
 
-cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, double *out, const Dims &d,
+cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, cplx64 *gh, double *out, const Dims &d,
                           cudaStream_t s) {
-  shell_kernel<<<num_shells(d.k), 256, 0, s>>>(uh, bh, dh, out, d.k);
+  shell_kernel<<<num_shells(d.k), 256, 0, s>>>(uh, bh, dh, gh, out, d.k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const double *v, size_t n, double *part, int blocks, cudaStream_t s) {
+  absmax_kernel<<<blocks, 256, 0, s>>>(v, n, part);
   return cudaGetLastError();
 }
 

@@ -1028,7 +1028,7 @@ mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t
   const size_t n3 = (size_t)d.n * d.n * d.n;
   const size_t part_len = sizes_for(c->d, c->precision).part;
   const int mblocks = (int)std::min<size_t>(2 * 152, part_len / 2);
-  if ((size_t)3 * ns > part_len || mblocks < 1) return fail(c, MHD_EINVAL, "scratch too small for the spectra");
+  if ((size_t)5 * ns > part_len || mblocks < 1) return fail(c, MHD_EINVAL, "scratch too small for the spectra");
   const cplx64 *Si = nullptr;
   if ((st = state_fp64(c, inst, &Si))) return st;
   // u_hat: inverse z, y of the state; u = m / rho with the x passes; forward y, z
@@ -1036,9 +1036,12 @@ mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t
   CK(mhd::launch_velocity_x(c->W2, c->W1, d, c->tw, c->stream));
   CK(mhd::launch_col_forward(c->W1, c->W2, d.n, 3 * d.n, d.nx, 1.0, c->tw, c->stream));
   CK(mhd::launch_col_forward(c->W2, c->W1, d.n, 3, d.nk * d.nx, 1.0 / (double)n3, c->tw, c->stream));
-  // shells, and the spectrum of du_x/dx into W2
-  CK(mhd::launch_shells(c->W1, Si + 4 * d.spec, c->W2, c->part, d, c->stream));
-  std::vector<double> sh((size_t)3 * ns);
+  // shells; the spectrum of du_x/dx into W2 and that of div B into W1 past n^3 complex values
+  // (clear of u_hat, 3 spec values, and of all that the du_x/dx chain below writes into W1: its
+  // z-pass output and n^3 real values; W1 holds at least 7 n^3 doubles)
+  cplx64 *gh = c->W1 + n3;
+  CK(mhd::launch_shells(c->W1, Si + 4 * d.spec, c->W2, gh, c->part, d, c->stream));
+  std::vector<double> sh((size_t)5 * ns);
   CK(cudaMemcpyAsync(sh.data(), c->part, sh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   // du_x/dx on the grid, then its moments
@@ -1049,13 +1052,24 @@ mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t
   CK(mhd::launch_moments(real, n3, c->part, mblocks, c->stream));
   std::vector<double> mp((size_t)2 * mblocks);
   CK(cudaMemcpyAsync(mp.data(), c->part, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  // div B on the grid (into W2), then its largest magnitude
+  CK(mhd::launch_col_inverse(gh, c->W2, d.n, 1, d.nk * d.nx, c->tw, c->stream));
+  CK(mhd::launch_col_inverse(c->W2, c->W1, d.n, d.n, d.nx, c->tw, c->stream));
+  double *dreal = reinterpret_cast<double *>(c->W2);
+  CK(mhd::launch_get_x(c->W1, dreal, 1, d, c->tw, c->stream));
+  CK(mhd::launch_absmax(dreal, n3, c->part, mblocks, c->stream));  // after the copy of mp (stream order)
+  std::vector<double> ap((size_t)mblocks);
+  CK(cudaMemcpyAsync(ap.data(), c->part, ap.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  double th = 0.0, m2 = 0.0, m3 = 0.0;
+  double th = 0.0, m2 = 0.0, m3 = 0.0, hk = 0.0, hm = 0.0, dmax = 0.0;
   for (int s = 0; s < ns; ++s) {
-    if (ek) ek[s] = sh[3 * s];
-    if (em) em[s] = sh[3 * s + 1];
-    th += sh[3 * s + 2];
+    if (ek) ek[s] = sh[5 * s];
+    if (em) em[s] = sh[5 * s + 1];
+    th += sh[5 * s + 2];
+    hk += sh[5 * s + 3];
+    hm += sh[5 * s + 4];
   }
+  for (int b = 0; b < mblocks; ++b) dmax = (ap[b] != ap[b] || ap[b] > dmax) ? ap[b] : dmax;
   for (int b = 0; b < mblocks; ++b) {
     m2 += mp[2 * b];
     m3 += mp[2 * b + 1];
@@ -1067,6 +1081,9 @@ mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t
     stats->d2 = m2;
     stats->d3 = m3;
     stats->s3 = m3 / pow(m2, 1.5);
+    stats->kin_hel = hk;
+    stats->mag_hel = hm;
+    stats->divb_max = dmax;
   }
   return MHD_OK;
 }

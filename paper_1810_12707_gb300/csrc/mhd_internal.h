@@ -191,13 +191,15 @@ cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out
 // 24 doubles to `out` (see mhd_api.cu for the order).
 // Shell spectra (kernels_spectra.cu).  launch_velocity_x: rho, m (fields 0..3 of [7][z][y][kx],
 // one instance) -> u = m / rho -> forward x -> [3][z][y][kx].  launch_shells: one block per shell,
-// out[s][3] = (E_u, E_B, sum |k.u_hat|^2) of shell s, dh = i k_x u_hat_x on every kept mode.
-// launch_moments: part[b][2] = (sum v^2, sum v^3) of a fixed share of v.
+// out[s][5] = (E_u, E_B, sum |k.u_hat|^2, kinetic helicity, magnetic helicity) of shell s,
+// dh = i k_x u_hat_x and gh = i k . B_hat on every kept mode.  launch_moments: part[b][2] =
+// (sum v^2, sum v^3) of a fixed share of v; launch_absmax: part[b] = max |v| of a fixed share.
 int num_shells(int k);
 cudaError_t launch_velocity_x(const cplx64 *in, cplx64 *out, const Dims &d, const cplx64 *tw, cudaStream_t s);
-cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, double *out, const Dims &d,
+cudaError_t launch_shells(const cplx64 *uh, const cplx64 *bh, cplx64 *dh, cplx64 *gh, double *out, const Dims &d,
                           cudaStream_t s);
 cudaError_t launch_moments(const double *v, size_t n, double *part, int blocks, cudaStream_t s);
+cudaError_t launch_absmax(const double *v, size_t n, double *part, int blocks, cudaStream_t s);
 
 // Tracer particles (kernels_tracers.cu).  Particle data: tr[6][count] = x, y, z, vx, vy, vz (FP64,
 // positions in [0, 2 pi)).  launch_tracer_init: velocities = CIC of u = m / rho from the real

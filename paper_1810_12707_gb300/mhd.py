@@ -62,7 +62,8 @@ class MhdPhys(ctypes.Structure):
 
 class MhdFlowStats(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("s3", ctypes.c_double), ("d2", ctypes.c_double),
-                ("d3", ctypes.c_double)]
+                ("d3", ctypes.c_double), ("kin_hel", ctypes.c_double), ("mag_hel", ctypes.c_double),
+                ("divb_max", ctypes.c_double)]
 
 
 class MhdDiag(ctypes.Structure):
@@ -354,14 +355,16 @@ def mhd_num_shells(n: int) -> int:
 
 
 def mhd_spectra(ctx: Context, inst: int = 0) -> dict:
-    """Shell spectra ek, em (index = shell round(|k|)) and theta', S3, <d^2>, <d^3> of d = du_x/dx."""
+    """Shell spectra ek, em (index = shell round(|k|)), theta', S3, <d^2>, <d^3> of d = du_x/dx,
+    the kinetic and magnetic helicities and max |div B|."""
     ns = mhd_num_shells(ctx.n)
     ek, em = np.zeros(ns), np.zeros(ns)
     st = MhdFlowStats()
     dp = ctypes.POINTER(ctypes.c_double)
     _check(ctx, load_library().mhd_spectra(ctx.handle, int(inst), ek.ctypes.data_as(dp), em.ctypes.data_as(dp), ns,
                                            ctypes.byref(st)))
-    return {"ek": ek, "em": em, "theta": st.theta, "s3": st.s3, "d2": st.d2, "d3": st.d3}
+    return {"ek": ek, "em": em, "theta": st.theta, "s3": st.s3, "d2": st.d2, "d3": st.d3,
+            "kin_hel": st.kin_hel, "mag_hel": st.mag_hel, "divb_max": st.divb_max}
 
 
 def mhd_set_forcing(ctx: Context, inst: int, amp: float, A: float = 1.0, B: float = 1.0, C: float = 1.0,

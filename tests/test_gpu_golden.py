@@ -7,6 +7,8 @@ the four flows as four instances of one batched context, in FP64 and in the mixe
   <u . B> = 0, B_hat(0) = B_0, div B = 0;
 * enstrophy and kinetic helicity by Parseval from the library's own half spectra of m (= u at
   rho = 1), and w = k0 u on the Beltrami rows;
+* the helicity diagnostics: <u . w> = k0 hel and, for the flow as magnetic field, <A . B> =
+  hel / k0 with div B = 0;
 * the curl of the momentum RHS of a Beltrami row at rho = 1, B = 0 is -nu k0^2 w.
 """
 import numpy as np
@@ -65,6 +67,25 @@ def test_paper_flows_diagnostics_and_spectra(lib, precision, k0):
         assert abs(half_parseval(uh, wh) - k0 * float(row["hel"])) <= 10 * tol, row["name"]
         if row["beltrami"]:
             assert np.max(np.abs(wh - k0 * uh)) <= tol, row["name"]
+    lib.mhd_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("k0", [1, 2])
+def test_paper_flows_helicities(lib, precision, k0):
+    """The library's helicity diagnostics: the flow as velocity gives <u . w> = k0 hel; the flow as
+    magnetic field (all modes at |k| = k0, or hel = 0) gives <A . B> = hel / k0 and div B = 0."""
+    n = 32
+    rows = gold.load_flows()
+    ctx = lib.mhd_init(n, [(0.02, 0.02, 1.0)] * len(rows), precision=precision)
+    for i, row in enumerate(rows):
+        u = inputs.paper_flow(n, row["flow"], k0=k0)
+        lib.mhd_set_state(ctx, i, np.ones((n, n, n)), u, u)
+    for i, row in enumerate(rows):
+        r = lib.mhd_spectra(ctx, i)
+        assert abs(r["kin_hel"] - k0 * float(row["hel"])) <= 1e-12, row["name"]
+        assert abs(r["mag_hel"] - float(row["hel"]) / k0) <= 1e-12, row["name"]
+        assert r["divb_max"] <= 1e-12, row["name"]
     lib.mhd_destroy(ctx)
 
 

@@ -1,7 +1,9 @@
 """Shell spectra, theta' and S_3 through the C ABI (paper, section "for hydrodynamic flow"),
 against the oracle: element by element on the same seeded states, at grid sizes that take every
-x-pass layout (8, 4, 2 and 1 row pairs per block), after steps, and in both precisions; plus the
-sum rules, bitwise repeatability and the negative derivative skewness of decaying turbulence.
+x-pass layout (8, 4, 2 and 1 row pairs per block), after steps, and in both precisions, with the
+kinetic and magnetic helicities and max |div B|; plus the sum rules, bitwise repeatability, the
+negative derivative skewness of decaying turbulence, and max |div B| of a field written out by
+hand.
 """
 import numpy as np
 import pytest
@@ -37,6 +39,12 @@ def check_close(g, e, rtol):
         assert g[key] == pytest.approx(e[key], rel=rtol), key
     assert abs(g["d3"] - e["d3"]) <= rtol * e["d2"] ** 1.5
     assert abs(g["s3"] - e["s3"]) <= 10 * rtol
+    # helicities against their bounds: |<u . w>| <= sqrt(3) k_max <|u|^2>, |<A . B>| <= <|B|^2>
+    kmax = (len(e["ek"]) - 1) / np.sqrt(3) + 1
+    u2, b2 = 2 * np.sum(e["ek"]), 2 * np.sum(e["em"])
+    assert abs(g["kin_hel"] - e["kin_hel"]) <= rtol * np.sqrt(3) * kmax * u2
+    assert abs(g["mag_hel"] - e["mag_hel"]) <= rtol * b2
+    assert abs(g["divb_max"] - e["divb_max"]) <= rtol * np.sqrt(3) * kmax * np.sqrt(b2)
 
 
 @pytest.mark.parametrize("n", [16, 32, 64, 128])
@@ -108,3 +116,19 @@ def test_decaying_turbulence_develops_negative_skewness(lib):
     assert -0.7 < r1["s3"] < -0.2
     assert r1["theta"] > 1e-3
     assert (k * r1["ek"]).sum() / r1["ek"].sum() > (k * r0["ek"]).sum() / r0["ek"].sum()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_divb_max_closed_form(lib, precision):
+    """B = (a sin 2x, c cos 3y, 0): div B = 2a cos 2x - 3c sin 3y reaches 2a + 3c at the grid
+    points x = 0, y = pi/2 (N = 32, 64)."""
+    for n in (32, 64):
+        X, Y, _ = inputs.grid(n)
+        b = np.zeros((3, n, n, n))
+        b[0] = 0.7 * np.sin(2 * X)
+        b[1] = 0.4 * np.cos(3 * Y)
+        ctx = lib.mhd_init(n, [(0.01, 0.01, 1.0)], precision=precision)
+        lib.mhd_set_state(ctx, 0, np.ones((n, n, n)), np.zeros((3, n, n, n)), b)
+        r = lib.mhd_spectra(ctx, 0)
+        lib.mhd_destroy(ctx)
+        assert abs(r["divb_max"] - 2.6) <= 1e-13
