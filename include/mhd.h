@@ -57,9 +57,12 @@ typedef enum {
 
 typedef enum {
   MHD_FP64 = 0,       /* IEEE double everywhere */
-  MHD_FP32_MIXED = 1  /* FFT passes and grid products in FP32; state, history, AB2 update, the
-                         pressure and dissipation terms, CFL dt, k = 0 modes and all diagnostics
-                         in FP64 */
+  MHD_FP32_MIXED = 1  /* FFT passes, grid products and the RHS assembly in FP32; the state kept
+                         as a double-float pair of FP32 arrays (hi + lo, a 48-bit significand)
+                         and advanced with an error-free two-sum; history and RK stage states in
+                         FP32; dt computed in FP64 (from an FP32 CFL maximum); the k = 0 modes,
+                         whose RHS is exactly zero, held exactly; diagnostics, spectra and
+                         set/get of the state in FP64 */
 } mhd_precision;
 
 /* Explicit time solvers (paper, section "Code G-MHD3D", Table I; its results use
