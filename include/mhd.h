@@ -23,8 +23,11 @@
  *   - a pointer flagged `on_device` = 1 is a CUDA device pointer of the current device, else a
  *     host pointer (pageable or pinned); input arrays are only read during the call and never
  *     retained; output arrays are written before the call returns;
- *   - every entry point returns an mhd_status; nothing throws across the ABI.  After an error
- *     other than MHD_ENONFINITE the context may only be destroyed; mhd_last_error() explains;
+ *   - every entry point returns an mhd_status; nothing throws across the ABI; mhd_last_error()
+ *     explains.  MHD_EINVAL, MHD_ESTATE and MHD_EBUSY are found before any work is issued and
+ *     leave the context usable (mhd_tracers_set has dropped the instance's earlier tracers by
+ *     the time it rejects a position), as does MHD_ENONFINITE; after MHD_ENOMEM, MHD_ECUDA or
+ *     MHD_ETIMEOUT the context may only be destroyed;
  *   - work is issued on the stream given at init; entry points that return host data
  *     synchronise that stream, mhd_step does not.
  */
