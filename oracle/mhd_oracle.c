@@ -16,7 +16,9 @@
  * (section "Governing equations"), with no energy equation (isothermal closure), plus the
  * optional ABC body force rho f of section "for magnetohydrodynamic flow" in the momentum
  * equation.  Diagnostics: grid energies and means, and the shell spectra, theta' and S_3 of the
- * hydrodynamic-flow section (or_spectra).
+ * hydrodynamic-flow section with the kinetic and magnetic helicities and max |div B|
+ * (or_spectra).  Tracer particles of section "Tracer Particles" (cloud-in-cell interpolation and
+ * a Boris push, or_tracers_*).
  *
  * Spatial discretisation (paper, section "Code G-MHD3D"; Table I): pseudo-spectral.  Derivatives
  * are products with i k in Fourier space, nonlinear products are formed in real space.  Products
