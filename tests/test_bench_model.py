@@ -33,9 +33,8 @@ def test_model_bytes_equal_the_pass_counts():
 
 def test_measured_reads_equal_the_algorithmic_reads():
     """Every pass reads its inputs from HBM once: within 0.1 % for the column passes and the
-    assembly, within 1 % for the flux pass, whose row-pair chunks (2 (K+1) complex values, 2752
-    bytes at 256^3) do not start on 32-byte sector boundaries, so their edge sectors are read in
-    part (0.5 % measured)."""
+    assembly, within 1 % for the flux pass (0.5 % measured: about three 32-byte sectors per
+    block beyond its inputs)."""
     for kernel, (r, _) in COUNTS.items():
         assert NCU_READ[kernel] == pytest.approx(r * C, rel=1e-2 if kernel == "flux_x" else 1e-3), kernel
 
