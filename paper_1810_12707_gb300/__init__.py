@@ -7,4 +7,4 @@ C ABI.
 ``paper_1810_12707_gb300.build_lib`` compiles the sm_103a library.
 Nothing is loaded at import time.
 """
-__all__ = ["mhd", "inputs", "build_lib"]
+__all__ = ["mhd", "inputs", "serving", "build_lib"]
