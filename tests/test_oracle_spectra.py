@@ -171,12 +171,14 @@ def test_decaying_turbulence_has_the_requested_spectrum(oracle_mod, k0):
 
 
 def test_shell_rules_agree_on_every_wavenumber():
-    """The CUDA path assigns a mode to shell s by the integer bounds (2s - 1)^2 <= 4|k|^2 <
-    (2s + 1)^2, the oracle by floor(sqrt(|k|^2) + 0.5) in FP64.  |k|^2 is an integer and no
-    integer lies on a boundary (s + 1/2)^2, so both give round(|k|); checked for every |k|^2 of
-    the largest grid (N = 1024, k_max = 341)."""
+    """The CUDA path assigns a mode to shell s by the integer bounds lo(s) <= 4|k|^2 <
+    (2s + 1)^2 with lo(s) = (2s - 1)^2 for s >= 1 and lo(0) = 0, the oracle by
+    floor(sqrt(|k|^2) + 0.5) in FP64.  |k|^2 is an integer and no integer lies on a boundary
+    (s + 1/2)^2, so both give round(|k|); checked for every |k|^2 of the largest grid (N = 1024,
+    k_max = 341)."""
     kmax = (1024 - 1) // 3
     k2 = np.arange(3 * kmax * kmax + 1, dtype=np.int64)
     s_fp = np.floor(np.sqrt(k2.astype(np.float64)) + 0.5).astype(np.int64)
-    assert np.all((2 * s_fp - 1) ** 2 <= 4 * k2) and np.all(4 * k2 < (2 * s_fp + 1) ** 2)
+    lo = np.where(s_fp == 0, 0, (2 * s_fp - 1) ** 2)
+    assert np.all(lo <= 4 * k2) and np.all(4 * k2 < (2 * s_fp + 1) ** 2)
     assert np.all(k2[s_fp == 0] == 0)
