@@ -104,3 +104,24 @@ def test_beltrami_rhs_viscous_decay(lib, precision, k0):
         wh = gold.curl_hat(np.stack([np.fft.fftn(c) / n ** 3 for c in u]), n)
         assert np.max(np.abs(ch + nu * k0 * k0 * wh)) <= 10 * TOL[precision], row["name"]
     lib.mhd_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_circular_fields_diagnostics(lib, precision):
+    """Grid diagnostics in closed form (u = U (sin z, cos z, 0), B = b (0, cos x, sin x), uniform
+    rho0: |u| = U and |B| = b everywhere), with the library's Mach numbers and Alfven speed."""
+    n = 32
+    X, Y, Z = inputs.grid(n)
+    rho0, U, b, cs = 2.0, 0.7, 0.3, 1.3
+    ctx = lib.mhd_init(n, [(0.01, 0.01, cs)], precision=precision)
+    lib.mhd_set_state(ctx, 0, np.full((n, n, n), rho0), U * np.stack([np.sin(Z), np.cos(Z), 0 * Z]),
+                      b * np.stack([0 * X, np.cos(X), np.sin(X)]))
+    d = lib.mhd_diagnostics(ctx, 0)
+    lib.mhd_destroy(ctx)
+    va = b / np.sqrt(rho0)
+    want = {"ke": rho0 * U * U / 2, "me": b * b / 2, "eint": cs * cs * rho0 * np.log(rho0), "mean_speed": U,
+            "mean_bmag": b, "smax": U + np.sqrt(cs * cs + b * b / rho0), "mean_rho": rho0,
+            "mach_s": U / cs, "v_a": va, "mach_a": U / va}
+    for key, v in want.items():
+        assert abs(d[key] - v) <= 1e-13 * max(1.0, abs(v)), key
+    assert abs(d["cross_hel"]) <= 1e-14 and d["divb_rms"] <= 1e-14

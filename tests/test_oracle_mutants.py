@@ -58,6 +58,10 @@ MUTANTS = [
     ("magnetic helicity without 1/k^2", "if (pass == 1) v = k2 > 0.0 ? v / k2 : 0.0;", "if (pass == 1) v = k2 > 0.0 ? v : 0.0;"),
     ("div B max drops y", "c->tmp[i] = I * (wavenumber(x, n) * c->state[F_BX][i] + wavenumber(y, n) * c->state[F_BY][i]",
      "c->tmp[i] = I * (wavenumber(x, n) * c->state[F_BX][i] + 0.0 * c->state[F_BY][i]"),
+    ("internal energy without Cs^2", "s[2] += cs2 * rho * log(rho);", "s[2] += rho * log(rho);"),
+    ("mean speed of m", "s[4] += sqrt(u2);", "s[4] += sqrt(u2) * rho;"),
+    ("diagnostic fast speed without B", "const double v = sqrt(u2) + sqrt(cs2 + b2 / rho);",
+     "const double v = sqrt(u2) + sqrt(cs2);"),
     ("position with old velocity", "v[a] = vn[a];\n      p[a] = wrap_2pi(p[a] + vn[a] * dt);",
      "p[a] = wrap_2pi(p[a] + v[a] * dt);\n      v[a] = vn[a];"),
 ]
