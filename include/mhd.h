@@ -236,7 +236,10 @@ MHD_API size_t mhd_checkpoint_doubles(const mhd_ctx *ctx);
 MHD_API mhd_status mhd_checkpoint(mhd_ctx *ctx, int32_t inst, double *buf, int32_t on_device);
 MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, int32_t on_device);
 
-/* Execution options of a context (mhd_set_option).  Changing one discards the captured step.
+/* Execution options of a context (mhd_set_option; the paper has no counterpart: these choose how
+ * the library runs a step, never what it computes, except the radix, which changes FP32
+ * rounding).  Changing one discards the captured step.  MHD_EINVAL for an unknown option or a
+ * value outside the ranges below, before anything changes.
  *   MHD_OPT_CUDA_GRAPH     1 (default): mhd_step captures one step as a CUDA graph on its first
  *                          call (after one direct step) and replays it; 0: direct launches.
  *                          Profiling (mhd_profile) always uses direct launches.
@@ -278,11 +281,12 @@ MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
  * only.  The scratch buffers are overwritten; the state is only read.  Synchronises. */
 MHD_API mhd_status mhd_autotune(mhd_ctx *ctx, int32_t reps, int32_t *tiles, int32_t *radix, double *ms);
 
-/* Per-kernel device time of mhd_step, for measurement.  While profiling is on, every kernel that
- * mhd_step launches is bracketed by CUDA events on the context's stream.  mhd_profile(ctx, 1)
- * clears the totals and starts recording, mhd_profile(ctx, 0) stops.  mhd_profile_read
- * synchronises and fills up to `max` entries (name, summed milliseconds, launch count), one per
- * kernel kind, and stores how many it wrote in *count. */
+/* Per-kernel device time of mhd_step, for measurement (a service of the library, not of the
+ * paper).  While profiling is on, every kernel that mhd_step launches is bracketed by CUDA events
+ * on the context's stream.  mhd_profile(ctx, 1) clears the totals and starts recording,
+ * mhd_profile(ctx, 0) stops.  mhd_profile_read synchronises and fills up to `max` entries (name,
+ * summed milliseconds, launch count), one per kernel kind, and stores how many it wrote in
+ * *count.  MHD_EINVAL for a NULL context or count, or a NULL `out` with max > 0. */
 typedef struct {
   const char *name; /* static string owned by the library */
   double total_ms;
@@ -291,7 +295,7 @@ typedef struct {
 MHD_API mhd_status mhd_profile(mhd_ctx *ctx, int32_t enable);
 MHD_API mhd_status mhd_profile_read(mhd_ctx *ctx, mhd_kernel_time *out, int32_t max, int32_t *count);
 
-/* ---- Serving pools ----
+/* ---- Serving pools (the paper has no counterpart; a service of the library) ----
  * A pool holds up to p->batch instances ("slots") of one grid size and precision, all resident in
  * device memory, and steps the live ones together (continuous batching): runs are admitted while
  * others are in flight and retired as they finish, and every run's result is bitwise the result
