@@ -9,8 +9,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_missing_library_raises():
+def test_missing_library_raises(monkeypatch):
     from paper_1810_12707_gb300 import mhd
+    monkeypatch.setattr(mhd, "_lib", None)  # as in a fresh process: nothing loaded yet
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mhd.load_library(os.path.join(ROOT, "does-not-exist", "libmhd_gb300.so"))
 
