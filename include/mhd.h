@@ -254,7 +254,13 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *   MHD_OPT_FLUX_PIPELINE  1: the fused x pass of the mixed mode at N >= 128 runs as a persistent
  *                          kernel that prefetches the next rows with bulk copies (TMA); 0
  *                          (default): one block per row pair, which measured faster on GB300.
- *                          Results are identical. */
+ *                          Results are identical.
+ *   MHD_OPT_WAIT_POLLS     poll limit, 0..4194304 (default 4194304), of that pipelined kernel's
+ *                          wait for each of its copies.  A wait that runs out makes the block
+ *                          record the failure, wait (up to 4194304 polls each) for the copies it
+ *                          still has in flight, and return; mhd_synchronize then reports
+ *                          MHD_ETIMEOUT and the context may only be destroyed.  0 gives up at
+ *                          once, so that a caller can exercise that path without a fault. */
 enum {
   MHD_OPT_CUDA_GRAPH = 0,
   MHD_OPT_TILE_INV_Z = 1,
@@ -265,7 +271,8 @@ enum {
   MHD_OPT_RADIX_INV_Z = 6,
   MHD_OPT_RADIX_INV_Y = 7,
   MHD_OPT_RADIX_FWD_Y = 8,
-  MHD_OPT_RADIX_FWD_Z = 9
+  MHD_OPT_RADIX_FWD_Z = 9,
+  MHD_OPT_WAIT_POLLS = 10
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
 
@@ -338,11 +345,12 @@ MHD_API mhd_status mhd_pool_info(const mhd_pool *pool, int32_t *live, int32_t *m
  *   stream          cudaStream_t to queue the work on (NULL = legacy default stream)
  * Intermediate spectra live in one file-scope device array of about 4.7 MB that every GPU which
  * loads the library keeps until the process exits.  The first call on a device resolves that
- * array's address and uploads its twiddle tables; make it before any stream capture.  All calls
- * on a device share the array and it keeps the last call's contents, so calls that overlap on the
- * GPU race; none of it needs to start at zero.  The call queues its work and returns without
- * synchronising: the outputs are valid once the stream has reached that point.  MHD_ECUDA if a
- * CUDA call fails. */
+ * array's address, uploads its twiddle tables and synchronises the device; make it before any
+ * stream capture.  All calls on a device share the array and it keeps the last call's contents,
+ * so calls that overlap on the GPU race; each call clears the one word that must start at zero.
+ * After the first call on a device, the call queues its work (the parameters too, as kernel
+ * arguments) and returns without synchronising: the outputs are valid once the stream has reached
+ * that point.  MHD_ECUDA if a CUDA call fails. */
 MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, const double *rho, const double *u,
                                    const double *b, double *drho, double *dm, double *db, void *stream);
 

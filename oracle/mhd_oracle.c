@@ -718,6 +718,15 @@ int or_step(or_ctx *c, int nsteps) {
   return 0;
 }
 
+/* Fix the step size of the following steps (dt > 0), or go back to the CFL step (dt <= 0).  For
+ * tests that replay a step-size sequence decided elsewhere; the history is kept, so the next AB2
+ * step uses r = dt / (the previous step's dt) as usual. */
+int or_set_fixed_dt(or_ctx *c, double dt) {
+  if (!c || !isfinite(dt)) return -1;
+  c->p.dt_fixed = dt > 0.0 ? dt : 0.0;
+  return 0;
+}
+
 /* History (f^{n-1}) access for checkpoint tests. */
 int or_get_history(or_ctx *c, int field, cplx *out, double *dt_prev, double *t, int64_t *step) {
   if (field < 0 || field >= NSTATE) return -1;

@@ -61,6 +61,7 @@ def _declare(lib):
     lib.or_rhs.argtypes = [P, D, D, D]
     lib.or_rhs_spectrum.argtypes = [P, ctypes.c_int, D]
     lib.or_step.argtypes = [P, ctypes.c_int]
+    lib.or_set_fixed_dt.argtypes = [P, ctypes.c_double]
     lib.or_get_history.argtypes = [P, ctypes.c_int, D, D, D, ctypes.POINTER(ctypes.c_int64)]
     lib.or_diagnostics.argtypes = [P, D]
     lib.or_fft1d.argtypes = [D, ctypes.c_int, ctypes.c_int]
@@ -230,6 +231,11 @@ class Oracle:
 
     def step(self, nsteps: int = 1) -> int:
         return int(self._lib.or_step(self._h, int(nsteps)))
+
+    def set_fixed_dt(self, dt: float) -> None:
+        """Take the following steps with step size `dt` (> 0), or with the CFL step (dt <= 0)."""
+        if self._lib.or_set_fixed_dt(self._h, float(dt)) != 0:
+            raise ValueError("bad step size")
 
     def history(self, field: int):
         out = np.empty(self.shape, dtype=np.complex128)

@@ -231,15 +231,18 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
 // the next pair (one contiguous chunk of 2 * NX complex values per field) are fetched with bulk
 // asynchronous copies into the other of two staging buffers while the current pair is
 // transformed, so the copy engine keeps HBM busy during the FFT work.  The arithmetic, its order
-// and the results are those of flux_x_kernel.  A barrier wait that does not complete within its
-// poll limit sets *err and ends the block (after one more bounded wait for its own copies).
-constexpr uint32_t kMaxPolls = 1u << 22;
+// and the results are those of flux_x_kernel.  A wait for a copy that does not complete within
+// `wait_polls` polls (kWaitPolls unless a caller lowers it; 0 gives up at once) sets *err = 1.
+// Before the block returns, thread 0 then waits, with the full limit kWaitPolls each, for BOTH
+// copies the block may still have in flight -- the one it gave up on and the prefetch of the
+// next row pair -- so that no bulk copy lands in shared memory after the block has released it;
+// if one of those waits also runs out, *err = 2.
 
 template <int N, typename C>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     flux_x_pipe_kernel(const C *__restrict__ in, C *__restrict__ out, const PhysDev *__restrict__ phys,
                        unsigned long long *__restrict__ smax_bits, int K, long long total_pairs,
-                       const C *__restrict__ tw, int *err) {
+                       const C *__restrict__ tw, int *err, uint32_t wait_polls) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
   extern __shared__ __align__(128) unsigned char smem_pipe[];
@@ -282,11 +285,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         issue(nxt, buf ^ 1);
       }
     }
-    const bool ok = mbar_wait(&mbar[buf], (iter >> 1) & 1, kMaxPolls);
+    const bool ok = mbar_wait(&mbar[buf], (iter >> 1) & 1, wait_polls);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        if (issued_next) mbar_wait(&mbar[buf ^ 1], ((iter + 1) >> 1) & 1, kMaxPolls);
+        // drain: the copy into stage[buf] that the wait gave up on, and the prefetch into
+        // stage[buf ^ 1] issued above; the block's shared memory stays allocated while thread 0
+        // is still running
+        bool drained = mbar_wait(&mbar[buf], (iter >> 1) & 1, kWaitPolls);
+        if (issued_next) drained = mbar_wait(&mbar[buf ^ 1], ((iter + 1) >> 1) & 1, kWaitPolls) && drained;
+        if (!drained) atomicExch(err, 2);
       }
       return;
     }
@@ -558,7 +566,7 @@ namespace {
 
 template <int N, typename C>
 cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
-                   cudaStream_t s, int *err, typename C::value_type *bgrid) {
+                   cudaStream_t s, int *err, typename C::value_type *bgrid, uint32_t wait_polls) {
   constexpr int PAIRS = pairs_for(N);
   if constexpr (PAIRS == 1 && sizeof(C) == 8) {
     if (bgrid != nullptr) err = nullptr;  // the pipelined variant does not write the grid field
@@ -577,7 +585,8 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
       const long long total = (long long)d.batch * N * N / 2;
       long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
       if (blocks > total) blocks = total;
-      flux_x_pipe_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, total, tw, err);
+      flux_x_pipe_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, total, tw, err,
+                                                                          wait_polls);
       return cudaGetLastError();
     }
   }
@@ -660,13 +669,15 @@ int flux_x_blocks_per_instance(int n) { return n * n / (2 * pairs_for(n)); }
 int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
 
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err, double *bgrid) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid)));
+                          const Dims &d, const cplx64 *tw, cudaStream_t s, int *err, double *bgrid,
+                          uint32_t wait_polls) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls)));
 }
 
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
-                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err, float *bgrid) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid)));
+                          const Dims &d, const cplx32 *tw, cudaStream_t s, int *err, float *bgrid,
+                          uint32_t wait_polls) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls)));
 }
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,

@@ -58,6 +58,7 @@ struct mhd_ctx {
   // options and the captured step
   bool use_graph = true;
   bool flux_pipeline = false;
+  uint32_t wait_polls = mhd::kWaitPolls;  // poll limit of the pipelined flux pass's copy waits
   bool forced = false;  // some instance has the ABC body force on
   // tracer particles: per instance a count and device data tr[6][count]; the grid magnetic field
   // the step's flux pass writes for them ([batch][3][N^3], working precision)
@@ -613,7 +614,8 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   // corrector, mhd_rhs) write to a second slot that nothing reads; its maxima are not exact
   // (the flux pass screens against the slot's earlier content), which changes no result.
   unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
-  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid));
+  LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid,
+                               c->wait_polls));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(bits, phys, ts, coef, d, c->dt_fixed, c->cfl_adv, c->cfl_visc, c->stream));
   }
@@ -903,6 +905,10 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   } else if (option == MHD_OPT_FLUX_PIPELINE) {
     if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "pipeline option must be 0 or 1");
     c->flux_pipeline = value != 0;
+  } else if (option == MHD_OPT_WAIT_POLLS) {
+    if (value < 0 || value > (int64_t)mhd::kWaitPolls)
+      return fail(c, MHD_EINVAL, "wait poll limit must be 0..%u", (unsigned)mhd::kWaitPolls);
+    c->wait_polls = (uint32_t)value;
   } else if (option >= MHD_OPT_TILE_INV_Z && option <= MHD_OPT_TILE_FWD_Z) {
     if (value < 0 || value > 64) return fail(c, MHD_EINVAL, "tile must be 0..64");
     c->tile[option - MHD_OPT_TILE_INV_Z] = (int)value;
@@ -941,7 +947,8 @@ mhd_status mhd_synchronize(mhd_ctx *c) {
   CK(cudaMemcpyAsync(&any, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (err) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up");
+  if (err == 1) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up (its copies were drained)");
+  if (err) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up and a copy did not complete in the drain");
   return any ? MHD_ENONFINITE : MHD_OK;
 }
 

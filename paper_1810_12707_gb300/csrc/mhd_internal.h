@@ -116,14 +116,17 @@ cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, 
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and the maximum of
 // |u| + c_f per instance, accumulated as an atomic maximum on the bits into smax_bits[batch]
 // (which must start at 0).  With `err` non-null, FP32 and N >= 128 the persistent, bulk-copy
-// pipelined variant runs; a bounded wait that gives up sets *err = 1.  With `bgrid` non-null the
-// grid magnetic field is written to bgrid[inst][3][N^3] as well (the plain variant runs).
+// pipelined variant runs: a wait for a copy that gives up after `wait_polls` polls sets *err = 1
+// (and *err = 2 if the copies still in flight do not complete within kWaitPolls polls each).
+// With `bgrid` non-null the grid magnetic field is written to bgrid[inst][3][N^3] as well (the
+// plain variant runs).
+constexpr uint32_t kWaitPolls = 1u << 22;
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx64 *tw, cudaStream_t s, int *err = nullptr,
-                          double *bgrid = nullptr);
+                          double *bgrid = nullptr, uint32_t wait_polls = kWaitPolls);
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr,
-                          float *bgrid = nullptr);
+                          float *bgrid = nullptr, uint32_t wait_polls = kWaitPolls);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with

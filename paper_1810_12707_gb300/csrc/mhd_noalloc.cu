@@ -11,13 +11,18 @@
 // Properties callers rely on:
 //   * no cudaMalloc / cudaFree / allocating library routine is called, ever;
 //   * n is limited to kNoallocMaxN (32): larger grids return MHD_EINVAL before any GPU work;
-//   * the first call on a device looks up the device address of the array (cudaGetSymbolAddress)
-//     and uploads the twiddle tables; make that first call before any stream capture;
+//   * the first call on a device looks up the device address of the array (cudaGetSymbolAddress),
+//     uploads the twiddle tables into it and waits for the device (cudaDeviceSynchronize) so that
+//     the tables are in place whatever stream the work is queued on; make that first call before
+//     any stream capture;
 //   * every call on a device shares the one array and it keeps the last call's contents: calls
 //     that overlap on the GPU (different streams, or different host threads without ordering)
-//     race.  Nothing needs to start at zero: every pass overwrites the region it later reads;
-//   * work is queued on `stream` (NULL = legacy default stream); outputs are valid once the
-//     stream reaches the end of the call's work.  The call does not synchronise the stream.
+//     race.  The one region that must start at zero, the word the flux pass takes its atomic
+//     CFL maximum on, is cleared by each call; every other pass overwrites what it later reads;
+//   * work is queued on `stream` (NULL = legacy default stream), the physical parameters
+//     included (a one-thread kernel takes them by value, so no host buffer is read after the
+//     call returns); outputs are valid once the stream reaches the end of the call's work.
+//     After the first call on a device the call does not synchronise the stream.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -76,7 +81,10 @@ unsigned char *g_base[64] = {nullptr};
 
 
 // Once per device, with that device current: resolve the array's device address and upload the
-// twiddle tables (plain copies into the array; nothing is allocated).
+// twiddle tables (plain copies into the array; nothing is allocated).  A copy from pageable host
+// memory may return before the data has reached the device, and the caller's stream need not be
+// ordered after the legacy stream the copies use, so the device is synchronised before the
+// address is published.
 cudaError_t setup_device(unsigned char **base) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -91,11 +99,17 @@ cudaError_t setup_device(unsigned char **base) {
     const std::vector<unsigned char> t16 = mhd::fp64_twiddle_bytes(16), t32 = mhd::fp64_twiddle_bytes(32);
     e = cudaMemcpy(b + kOffTw16, t16.data(), t16.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + kOffTw32, t32.data(), t32.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
     g_base[dev] = b;
   }
   *base = g_base[dev];
   return cudaSuccess;
+}
+
+// The instance's parameters, written on the caller's stream from kernel arguments.
+__global__ void set_phys_kernel(mhd::PhysDev *pd, double nu, double eta, double cs) {
+  *pd = mhd::PhysDev{nu, eta, cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
 }
 
 }  // namespace
@@ -124,8 +138,10 @@ extern "C" MHD_API mhd_status mhd_rhs_noalloc(int32_t n, const mhd_phys *phys, c
   double *part = reinterpret_cast<double *>(base + kOffPart);
   const cplx64 *tw = reinterpret_cast<const cplx64 *>(base + (n == 16 ? kOffTw16 : kOffTw32));
   mhd::PhysDev *pd = reinterpret_cast<mhd::PhysDev *>(base + kOffPhys);
-  const mhd::PhysDev hp{phys->nu, phys->eta, phys->cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
-  NA_CK(cudaMemcpyAsync(pd, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+  set_phys_kernel<<<1, 1, 0, s>>>(pd, phys->nu, phys->eta, phys->cs);
+  NA_CK(cudaGetLastError());
+  // the flux pass takes an atomic maximum here (and screens against it): start from zero
+  NA_CK(cudaMemsetAsync(part, 0, sizeof(unsigned long long), s));
 
   // state spectra from the real-space fields (m = rho u), truncated and normalised
   const size_t n3 = (size_t)n * n * n;
