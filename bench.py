@@ -93,10 +93,12 @@ def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
     spec = nk * nk * nx
     # complex value of the passes: 16 B in FP64, 8 B in the mixed mode, whose state is a pair of
     # FP32 arrays (hi, lo) and whose history is FP32
-    c = 16.0 if precision == "fp64" else 8.0
-    state_read = 16.0 if precision == "fp64" else 8.0   # the inverse z pass reads hi only
+    # (the double-float mode moves FP64-sized values: hi + lo FP32 pairs)
+    wide = precision in ("fp64", "fp64df")
+    c = 16.0 if wide else 8.0
+    state_read = 16.0 if wide else 8.0   # the mixed mode's inverse z pass reads hi only
     # assembly per mode: 12 products + state + history read, state + history written
-    asm = (12 * 16 + 4 * 7 * 16) if precision == "fp64" else (12 + 7 * 2 + 7 + 7 * 3) * 8
+    asm = (12 * 16 + 4 * 7 * 16) if wide else (12 + 7 * 2 + 7 + 7 * 3) * 8
     fft = 5.0 * n * math.log2(n)
     m = {
         "inverse_z": (7 * (spec * state_read + n * nk * nx * c), 7 * nk * nx * fft),
@@ -286,7 +288,7 @@ def run_ours(args, name, cfg):
     from paper_1810_12707_gb300 import mhd
 
     n, batch, K, W = cfg["n"], cfg["batch"], args.steps, args.warmup
-    prec = mhd.MHD_FP64 if cfg["precision"] == "fp64" else mhd.MHD_FP32_MIXED
+    prec = {"fp64": mhd.MHD_FP64, "fp64df": mhd.MHD_FP64_DF}.get(cfg["precision"], mhd.MHD_FP32_MIXED)
     ics = workload(n, cfg["ic"], batch)
     phys = [(ic.nu, ic.eta, ic.cs) for ic in ics]
     ctx = mhd.mhd_init(n, phys, dt=cfg["dt"], precision=prec)
@@ -352,7 +354,7 @@ def run_ours(args, name, cfg):
         for opt, t in zip((mhd.MHD_OPT_TILE_INV_Z, mhd.MHD_OPT_TILE_INV_Y, mhd.MHD_OPT_TILE_FWD_Y,
                            mhd.MHD_OPT_TILE_FWD_Z), tuned["tiles"]):
             mhd.mhd_set_option(ectx, opt, t)
-        if prec != mhd.MHD_FP64:
+        if prec == mhd.MHD_FP32_MIXED:
             for opt, r in zip((mhd.MHD_OPT_RADIX_INV_Z, mhd.MHD_OPT_RADIX_INV_Y, mhd.MHD_OPT_RADIX_FWD_Y,
                                mhd.MHD_OPT_RADIX_FWD_Z), tuned["radix"]):
                 mhd.mhd_set_option(ectx, opt, r)
@@ -419,7 +421,8 @@ def run_ours(args, name, cfg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / (world * PAPER_256_V100) if (n == 256 and batch == 1) else None,
-            "dtype": "f64" if prec == mhd.MHD_FP64 else "f32 (double-float state)", "data": "synthetic",
+            "dtype": {mhd.MHD_FP64: "f64", mhd.MHD_FP64_DF: "f32x2 double-float (48-bit significand)"}.get(
+                prec, "f32 (double-float state)"), "data": "synthetic",
             "config": dict(config_block(name, cfg, world),
                            col_tiles=tiles if tiles else "library default (autotuner off)",
                            col_radix=tuned["radix"] if tuned else "library default"),
@@ -529,7 +532,7 @@ def main():
     ap.add_argument("--config", choices=sorted(CONFIGS), default="abc256")
     ap.add_argument("--n", type=int)
     ap.add_argument("--batch", type=int)
-    ap.add_argument("--precision", choices=("fp64", "fp32"))
+    ap.add_argument("--precision", choices=("fp64", "fp64df", "fp32"))
     ap.add_argument("--ic", choices=("abc", "tg", "ot", "ens"))
     ap.add_argument("--impl", choices=("ours", "reference", "cufft"), default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)

@@ -60,12 +60,21 @@ typedef enum {
 
 typedef enum {
   MHD_FP64 = 0,       /* IEEE double everywhere */
-  MHD_FP32_MIXED = 1  /* FFT passes, grid products and the RHS assembly in FP32; the state kept
+  MHD_FP32_MIXED = 1, /* FFT passes, grid products and the RHS assembly in FP32; the state kept
                          as a double-float pair of FP32 arrays (hi + lo, a 48-bit significand)
                          and advanced with an error-free two-sum; history and RK stage states in
                          FP32; dt computed in FP64 (from an FP32 CFL maximum); the k = 0 modes,
                          whose RHS is exactly zero, held exactly; diagnostics, spectra and
                          set/get of the state in FP64 */
+  MHD_FP64_DF = 2     /* FP64-tolerance mode without FP64 arithmetic in the step: every value of
+                         the step -- state, history, stage state, the intermediate spectra and the
+                         grid products -- is a double-float pair (hi + lo FP32, a 48-bit
+                         significand), and every transform, product, RHS term and update is done
+                         in double-float arithmetic on the FP32 pipe with error-free
+                         transformations (Knuth's TwoSum, an FMA-based TwoProd); the CFL maximum
+                         is taken exactly in FP64 at the few grid points that can reach it, and dt
+                         is computed in FP64 as in MHD_FP64; diagnostics, spectra and set/get of
+                         the state in FP64.  Same memory footprint as MHD_FP64. */
 } mhd_precision;
 
 /* Explicit time solvers (paper, section "Code G-MHD3D", Table I; its results use

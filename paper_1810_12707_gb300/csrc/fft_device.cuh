@@ -6,6 +6,7 @@
 // with DIR = -1 for the forward and +1 for the inverse transform.
 #pragma once
 
+#include "dfloat.cuh"
 #include "mhd_internal.h"
 
 #include <type_traits>
@@ -39,6 +40,15 @@ __device__ __forceinline__ CT c_cvt(CF a) {
   using R = typename CT::value_type;
   return CT{(R)a.re, (R)a.im};
 }
+
+// Double-float complex values use the generic forms above through the dfr operators (lazy sums
+// and products).  A pass scales its output by a power of two only, given as an FP32 number.
+__device__ __forceinline__ cdf c_scale(cdf a, float s) { return cdf{s * a.re, s * a.im}; }
+
+// What a pass stores to global memory: double-float values renormalised, others as they are.
+template <typename C>
+__device__ __forceinline__ C c_store(C a) { return a; }
+__device__ __forceinline__ cdf c_store(cdf a) { return cdf_norm(a); }
 
 // NaN-propagating maximum (a non-finite CFL speed must reach the step-size kernel).
 __device__ __forceinline__ double nan_max(double a, double b) {
@@ -146,6 +156,34 @@ __device__ __forceinline__ void dft16(C *v) {
   }
 }
 
+// Length 8 in double-float: the same split as above; W8 = h (1 + DIR i) with h = sqrt(2)/2 in
+// double-float.
+template <int DIR>
+__device__ __forceinline__ void dft8(cdf *v) {
+  constexpr dfr h = dfr_const(0.70710678118654752440);
+  cdf b[4], c[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    b[j] = c_add(v[j], v[j + 4]);
+    c[j] = c_sub(v[j], v[j + 4]);
+  }
+  if constexpr (DIR > 0) {
+    c[1] = cdf{h * (c[1].re - c[1].im), h * (c[1].im + c[1].re)};
+    c[3] = cdf{h * (-c[3].re - c[3].im), h * (c[3].re - c[3].im)};
+  } else {
+    c[1] = cdf{h * (c[1].re + c[1].im), h * (c[1].im - c[1].re)};
+    c[3] = cdf{h * (c[3].im - c[3].re), h * (-c[3].im - c[3].re)};
+  }
+  c[2] = c_mul_i<DIR>(c[2]);
+  dft4<DIR>(b);
+  dft4<DIR>(c);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[2 * m] = b[m];
+    v[2 * m + 1] = c[m];
+  }
+}
+
 template <int R, int DIR, typename C>
 __device__ __forceinline__ void dft_small(C *v) {
   if constexpr (R == 16) dft16<DIR>(v);
@@ -156,6 +194,13 @@ __device__ __forceinline__ void dft_small(C *v) {
 
 // Twiddle load that the compiler may not hoist out of loops: kernels that transform many pencils
 // in a loop would otherwise keep every stage's twiddles live in registers across the loop.
+__device__ __forceinline__ cdf tw_load(const cdf *p) {
+  cdf v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.re.hi), "=f"(v.re.lo), "=f"(v.im.hi), "=f"(v.im.lo)
+               : "l"(p));
+  return v;
+}
 __device__ __forceinline__ cplx64 tw_load(const cplx64 *p) {
   cplx64 v;
   asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.re), "=d"(v.im) : "l"(p));
@@ -355,6 +400,17 @@ __device__ __forceinline__ void dft8_first_fma(C *v) {
   // (X0, X4, X2, X6, X1, X5, X3, X7) -> natural order
   const C x0 = v[0], x4 = v[1], x2 = v[2], x6 = v[3], x1 = v[4], x5 = v[5], x3 = v[6], x7 = v[7];
   v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
+}
+
+// The first radix-8 stage in double-float: the plain length-8 DFT (inputs 3 and 4 are zeros
+// when the pencil is zero-padded and were not loaded).
+template <int DIR, bool ZP>
+__device__ __forceinline__ void dft8_first_fma(cdf *v) {
+  if constexpr (ZP) {
+    v[3] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+    v[4] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+  }
+  dft8<DIR>(v);
 }
 
 // ---- values per thread ----

@@ -24,7 +24,7 @@ namespace mhd {
 // VPT: values per thread of the transform (8, or 16 for FP32), so N / VPT threads per column.
 template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
 __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
-                               int cols, typename CC::value_type scale, const CC *__restrict__ tw) {
+                               int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CC *sm = reinterpret_cast<CC *>(smem_raw);
   constexpr int TPP = tpp_for<N, VPT>();
@@ -73,8 +73,8 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
     CO *dst = out + slab * (size_t)LOUT * cols + col;
     for (int l = l0; l < LOUT; l += TPP) {
       CC v = pen[sm_idx<CC>(DIR > 0 ? l : kept_to_fft(l, K, N))];
-      if (DIR < 0 && scale != (typename CC::value_type)1) v = c_scale(v, scale);
-      dst[(size_t)l * cols] = c_cvt<CO>(v);
+      if (DIR < 0 && scale != (typename scale_of<CC>::type)1) v = c_scale(v, scale);
+      dst[(size_t)l * cols] = c_store(c_cvt<CO>(v));
     }
   }
 }
@@ -130,7 +130,7 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   col_fft_kernel<N, DIR, CI, CO, CO, VPT><<<(unsigned)blocks, tc * TPP, smem, s>>>(
-      in, out, ntiles, tsh, cols, (typename CO::value_type)scale, tw);
+      in, out, ntiles, tsh, cols, (typename scale_of<CO>::type)scale, tw);
   return cudaGetLastError();
 }
 
@@ -162,6 +162,26 @@ cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double
 }
 
 }  // namespace
+
+int col_max_tile_df(int n, int dir) {
+  auto pick = [&](auto tag_n) -> int {
+    constexpr int N = decltype(tag_n)::value;
+    const int t = dir > 0 ? col_max_threads<N, +1, cdf, cdf, 8>() : col_max_threads<N, -1, cdf, cdf, 8>();
+    int tc = 1;
+    while (tc * 2 * tpp_for<N, 8>() <= t && tc < 64) tc *= 2;
+    return tc;
+  };
+  switch (n) {
+    case 16: return pick(std::integral_constant<int, 16>());
+    case 32: return pick(std::integral_constant<int, 32>());
+    case 64: return pick(std::integral_constant<int, 64>());
+    case 128: return pick(std::integral_constant<int, 128>());
+    case 256: return pick(std::integral_constant<int, 256>());
+    case 512: return pick(std::integral_constant<int, 512>());
+    case 1024: return pick(std::integral_constant<int, 1024>());
+    default: return 1;
+  }
+}
 
 int col_max_tile(int n, int dir, bool fp64, bool mixed_in, int vpt) {
   const bool r16 = !fp64 && vpt == 16;
@@ -208,6 +228,14 @@ cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, 
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
                                double scale, const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
   return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, vpt);
+}
+cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
+                               int tile, int) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
+}
+cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
+                               cudaStream_t s, int tile, int) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8);
 }
 
 }  // namespace mhd

@@ -35,8 +35,9 @@ __device__ __forceinline__ CT rho_at(const CT *rho, int kx, int ky, int kz, int 
 // density spectrum by +-kf along s, (rho sin)^(k) = [rho(k - kf s) - rho(k + kf s)] / 2i and
 // (rho cos)^(k) = [rho(k - kf s) + rho(k + kf s)] / 2.  The product is band-limited (no aliasing),
 // so this equals the transform of the product on the grid.
-template <typename CT>
-__device__ __forceinline__ void abc_force(const CT *rho, int kx, int ky, int kz, int K, const PhysDev &ph, CT f[3]) {
+// `rho(kx, ky, kz)` returns the density spectrum at a wavevector (as rho_at does).
+template <typename CT, typename RhoAt>
+__device__ __forceinline__ void abc_force(RhoAt rho, int kx, int ky, int kz, const PhysDev &ph, CT f[3]) {
   using R = typename CT::value_type;
   const int q = ph.fkf;
   const R a = (R)ph.fa, b = (R)ph.fb, c = (R)ph.fc, amp = (R)ph.famp, h = (R)0.5;
@@ -44,8 +45,8 @@ __device__ __forceinline__ void abc_force(const CT *rho, int kx, int ky, int kz,
   const int d[3][3] = {{q, 0, 0}, {0, q, 0}, {0, 0, q}};
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    const CT m = rho_at(rho, kx - d[s][0], ky - d[s][1], kz - d[s][2], K);
-    const CT p = rho_at(rho, kx + d[s][0], ky + d[s][1], kz + d[s][2], K);
+    const CT m = rho(kx - d[s][0], ky - d[s][1], kz - d[s][2]);
+    const CT p = rho(kx + d[s][0], ky + d[s][1], kz + d[s][2]);
     S[s] = CT{h * (m.im - p.im), -h * (m.re - p.re)};  // (m - p) / 2i
     Co[s] = CT{h * (m.re + p.re), h * (m.im + p.im)};
   }
@@ -301,10 +302,39 @@ __global__ void force_kernel(const CT *__restrict__ y_in, CT *__restrict__ force
     const int kxi = (int)(m % NX);
     const size_t t = m / NX;
     CT fo[3];
-    abc_force(y_in + (size_t)inst * 7 * spec, kxi, kept_wave((int)(t % NK), K), kept_wave((int)(t / NK), K), K, ph,
-              fo);
+    const CT *rho = y_in + (size_t)inst * 7 * spec;
+    abc_force<CT>([&](int x, int y, int z) { return rho_at(rho, x, y, z, K); }, kxi, kept_wave((int)(t % NK), K),
+                  kept_wave((int)(t / NK), K), ph, fo);
 #pragma unroll
     for (int a = 0; a < 3; ++a) force[((size_t)inst * 3 + a) * spec + m] = fo[a];
+  }
+}
+
+// The same force in the double-float mode: formed in FP64 from the double-float density spectrum
+// (a pass of its own, only for instances with the force on), stored as double-float values.
+__global__ void force_dfloat_kernel(const cdf *__restrict__ y_in, cdf *__restrict__ force,
+                                    const PhysDev *__restrict__ phys, int K, int batch) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const size_t total = spec * batch;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(idx / spec);
+    const size_t m = idx - (size_t)inst * spec;
+    const PhysDev ph = phys[inst];
+    if (ph.famp == 0.0) continue;
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    cplx64 fo[3];
+    const cdf *rho = y_in + (size_t)inst * 7 * spec;
+    abc_force<cplx64>(
+        [&](int x, int y, int z) {
+          const cdf v = rho_at(rho, x, y, z, K);
+          return cplx64{dfr_to_double(v.re), dfr_to_double(v.im)};
+        },
+        kxi, kept_wave((int)(t % NK), K), kept_wave((int)(t / NK), K), ph, fo);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) force[((size_t)inst * 3 + a) * spec + m] = cdf_from_c64(fo[a].re, fo[a].im);
   }
 }
 
@@ -323,6 +353,127 @@ __global__ void combine_state_kernel(const cplx32 *__restrict__ hi, const cplx32
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     const cplx32 a = hi[i], b = lo[i];
     out[i] = cplx64{(double)a.re + (double)b.re, (double)a.im + (double)b.im};
+  }
+}
+
+__global__ void split_cdf_kernel(const cplx64 *__restrict__ in, cdf *__restrict__ out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx64 v = in[i];
+    out[i] = cdf_from_c64(v.re, v.im);
+  }
+}
+
+__global__ void combine_cdf_kernel(const cdf *__restrict__ in, cplx64 *__restrict__ out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const cdf v = in[i];
+    out[i] = cplx64{dfr_to_double(v.re), dfr_to_double(v.im)};
+  }
+}
+
+// Double-float mode: the RHS of the FP64 assembly above, term by term in the same order, and the
+// update of the double-float state, in double-float arithmetic (no FP64 operation per mode).  The
+// wavenumbers, k^2 and the product spectra's factor 1/(2 N^3) are exact FP32 numbers.
+__global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *y_in, cdf *state,
+                                       cdf *__restrict__ hist, cdf *ystage, cplx64 *__restrict__ rhs_out,
+                                       const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
+                                       const cdf *__restrict__ force, int op, int stage, int K, int batch,
+                                       float inv_n3) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const size_t total = spec * batch;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int inst = (int)(idx / spec);
+    const size_t m = idx - (size_t)inst * spec;
+    if (op != ASM_RHS && coef[inst].skip) continue;
+    const int kxi = (int)(m % NX);
+    const size_t t = m / NX;
+    const int jy = (int)(t % NK), jz = (int)(t / NK);
+    const float kx = (float)kxi, ky = (float)kept_wave(jy, K), kz = (float)kept_wave(jz, K);
+    const float k2 = __fadd_rn(__fadd_rn(__fmul_rn(kx, kx), __fmul_rn(ky, ky)), __fmul_rn(kz, kz));  // exact
+    const dfr nu = phys[inst].nu_df, eta = phys[inst].eta_df, cs2 = phys[inst].cs2_df;
+    const float skx = __fmul_rn(kx, inv_n3), sky = __fmul_rn(ky, inv_n3), skz = __fmul_rn(kz, inv_n3);
+    const dfr nuk2s = dfr_scale2(k2 * nu, inv_n3);
+
+    const cdf *S = y_in + (size_t)inst * 7 * spec + m;
+    const cdf *F = flux + (size_t)inst * 12 * spec + m;
+    cdf y[7], f[12];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) f[q] = F[q * spec];
+    const cdf Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+    const cdf Ex = f[6], Ey = f[7], Ez = f[8];
+
+    cdf r[7];
+    {  // continuity: -i k . m
+      const cdf s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+      r[0] = cdf{s.im, -s.re};
+    }
+    {  // momentum
+      const float kk[3] = {kx, ky, kz};
+      const cdf T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cdf divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
+                          skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
+        const dfr kc = kk[a] * cs2;
+        const cdf g = {divT.re + kc * y[0].re, divT.im + kc * y[0].im};
+        const cdf u = f[9 + a];
+        r[1 + a] = cdf{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
+      }
+      if (force != nullptr && phys[inst].famp != 0.0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const cdf fo = force[((size_t)inst * 3 + a) * spec + m];
+          r[1 + a] = cdf{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+        }
+      }
+    }
+    {  // induction: i k x E - eta k^2 B
+      const cdf c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
+                        {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
+                        {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
+      const dfr etak2 = k2 * eta;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[4 + a] = cdf{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
+    }
+
+    const size_t o7 = (size_t)inst * 7 * spec + m;
+    if (op == ASM_RHS) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = cplx64{dfr_to_double(r[q].re), dfr_to_double(r[q].im)};
+      continue;
+    }
+    const StepCoef cf = coef[inst];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const size_t i = o7 + q * spec;
+      const cdf rq = r[q];
+      if (op == ASM_AB2 || op == ASM_PC_PRED) {
+        // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
+        cdf y0 = state[i];
+        if (cf.a0 != 0.0) {
+          const cdf h = hist[i];
+          y0 = cdf{y0.re + cf.dta0_df * h.re, y0.im + cf.dta0_df * h.im};
+        }
+        const cdf yn = cdf_norm(cdf{y0.re + cf.dta1_df * rq.re, y0.im + cf.dta1_df * rq.im});
+        if (op == ASM_AB2) state[i] = yn;
+        else ystage[i] = yn;
+        hist[i] = cdf_norm(rq);
+      } else if (op == ASM_RK_STAGE) {
+        const cdf acc = cdf_norm(stage == 1 ? rq : cdf{hist[i].re + dfr_scale2(rq.re, 2.f), hist[i].im + dfr_scale2(rq.im, 2.f)});
+        hist[i] = acc;
+        const dfr w = stage < 3 ? dfr_scale2(cf.dt_df, 0.5f) : cf.dt_df;
+        const cdf y0 = state[i];
+        ystage[i] = cdf_norm(cdf{y0.re + w * rq.re, y0.im + w * rq.im});
+      } else {  // ASM_RK_FINAL, ASM_PC_CORR
+        const dfr w = op == ASM_RK_FINAL ? cf.dt6_df : dfr_scale2(cf.dt_df, 0.5f);
+        const cdf h = hist[i], y0 = state[i];
+        const cdf acc = {h.re + rq.re, h.im + rq.im};
+        state[i] = cdf_norm(cdf{y0.re + w * acc.re, y0.im + w * acc.im});
+      }
+    }
   }
 }
 
@@ -366,6 +517,10 @@ __global__ void step_dt_kernel(unsigned long long *__restrict__ smax_bits, const
       c.fdt = (float)c.dt;
       c.fa1 = (float)c.a1;
       c.fa0 = (float)c.a0;
+      c.dt_df = dfr_from_double(c.dt);
+      c.dta1_df = dfr_from_double(c.dt * c.a1);
+      c.dta0_df = dfr_from_double(c.dt * c.a0);
+      c.dt6_df = dfr_from_double(c.dt / 6.0);
       s.t += dt;
       s.dt_prev = dt;
       s.dt_last = dt;
@@ -497,6 +652,31 @@ cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s
   const float inv_n3 = (float)(0.5 / ((double)d.n * d.n * d.n));  // with the split's 1/2
   assemble_df_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, s_hi, s_lo, hist, ystage, rhs_out, phys, coef,
                                                           force, op, stage, d.k, d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const cdf *flux, const cdf *y_in, cdf *state, cdf *hist, cdf *ystage, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int op, int stage, const Dims &d,
+                            cudaStream_t s, const cdf *force) {
+  const size_t total = d.spec * d.batch;
+  const float inv_n3 = (float)(0.5 / ((double)d.n * d.n * d.n));  // a power of two, with the split's 1/2
+  assemble_dfloat_kernel<<<grid_for(total, 256), 256, 0, s>>>(flux, y_in, state, hist, ystage, rhs_out, phys, coef,
+                                                              force, op, stage, d.k, d.batch, inv_n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force(const cdf *y_in, cdf *force, const PhysDev *phys, const Dims &d, cudaStream_t s) {
+  force_dfloat_kernel<<<grid_for(d.spec * d.batch, 256), 256, 0, s>>>(y_in, force, phys, d.k, d.batch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_state(const cplx64 *in, cdf *out, size_t count, cudaStream_t s) {
+  split_cdf_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_state(const cdf *in, cplx64 *out, size_t count, cudaStream_t s) {
+  combine_cdf_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, out, count);
   return cudaGetLastError();
 }
 

@@ -87,7 +87,7 @@ template <int N, typename C>
 __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
                               int K, int blocks_per_inst, const C *__restrict__ tw,
-                              typename C::value_type *__restrict__ bgrid) {
+                              typename grid_of<C>::type *__restrict__ bgrid) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -136,19 +136,77 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
   fft_pencils<N, +1, (flux_vpt<N, C>())>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
 
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
-  const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
-  R smax = 0;
-  // FP64: the maximum that blocks of this pass have already published is a lower bound of the
-  // pass's maximum.  A point whose FP32 estimate of |u| + c_f lies below `screen` (that bound
-  // less 1e-6 relative and 1e-18 absolute, above the estimate's worst error of about 3e-7
-  // relative) cannot raise it, so its exact speed (two FP64 square roots) is not formed.  The
-  // pass still yields the exact maximum, whichever blocks ran first; a NaN or an infinite
-  // estimate always takes the exact path.
+  constexpr bool kDF = std::is_same<C, cdf>::value;
+  using SM = typename std::conditional<kDF, double, R>::type;  // type of the CFL maximum
+  SM smax = 0;
+  // FP64 and double-float: the maximum that blocks of this pass have already published is a
+  // lower bound of the pass's maximum.  A point whose FP32 estimate of |u| + c_f lies below
+  // `screen` (that bound less 1e-6 relative and 1e-18 absolute, above the estimate's worst error
+  // of about 3e-7 relative) cannot raise it, so its exact speed (two FP64 square roots) is not
+  // formed.  The pass still yields the exact maximum, whichever blocks ran first; a NaN or an
+  // infinite estimate always takes the exact path.
   float screen = 0.f;
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (sizeof(SM) == 8) {
     const double lb = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long *>(smax_bits + inst));
     screen = (float)(lb * (1.0 - 1e-6) - 1e-18);
   }
+  if constexpr (kDF) {
+    // double-float products; the speed's squares are renormalised, so their high parts are the
+    // FP32 roundings the screening estimate assumes, and the exact speed is taken in FP64 from
+    // the double-float squares
+    const double csd = phys[inst].cs;
+    const dfr cs2 = dfr_from_double(csd * csd);
+    for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
+      const int p = q / N, j = q - p * N;
+      C *b = sm + p * 12 * P + sm_idx<C>(j);
+      dfr v[2][7];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        const C c = b[f * P];
+        v[0][f] = c.re;
+        v[1][f] = c.im;
+      }
+      if (bgrid != nullptr) {
+        constexpr size_t N3 = NN * N;
+        double *g = bgrid + (size_t)inst * 3 * N3 + (row0 + 2 * p) * N + j;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          g[c * N3] = dfr_to_double(v[0][4 + c]);
+          g[c * N3 + N] = dfr_to_double(v[1][4 + c]);
+        }
+      }
+      dfr *bd = reinterpret_cast<dfr *>(b);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const dfr rho = v[h][0];
+        const dfr mx = v[h][1], my = v[h][2], mz = v[h][3];
+        const dfr bx = v[h][4], by = v[h][5], bz = v[h][6];
+        const dfr ir = dfr_rcp(rho);
+        const dfr ux = mx * ir, uy = my * ir, uz = mz * ir;
+        const dfr bxx = bx * bx, byy = by * by, bzz = bz * bz;
+        const dfr b2 = bxx + byy + bzz;
+        const dfr hb = dfr_scale2(b2, 0.5f);
+        bd[2 * 0 * P + h] = mx * ux + hb - bxx;   // T_xx
+        bd[2 * 1 * P + h] = my * uy + hb - byy;   // T_yy
+        bd[2 * 2 * P + h] = mz * uz + hb - bzz;   // T_zz
+        bd[2 * 3 * P + h] = mx * uy - bx * by;    // T_xy
+        bd[2 * 4 * P + h] = mx * uz - bx * bz;    // T_xz
+        bd[2 * 5 * P + h] = my * uz - by * bz;    // T_yz
+        bd[2 * 6 * P + h] = uy * bz - uz * by;    // E_x
+        bd[2 * 7 * P + h] = uz * bx - ux * bz;    // E_y
+        bd[2 * 8 * P + h] = ux * by - uy * bx;    // E_z
+        bd[2 * 9 * P + h] = ux;
+        bd[2 * 10 * P + h] = uy;
+        bd[2 * 11 * P + h] = uz;
+        const dfr u2 = dfr_norm(ux * ux + uy * uy + uz * uz), c2 = dfr_norm(cs2 + b2 * ir);
+        if (!(sqrtf(u2.hi) + sqrtf(c2.hi) < screen)) {
+          const double s = sqrt(dfr_to_double(u2)) + sqrt(dfr_to_double(c2));
+          smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
+        }
+      }
+    }
+  } else {
+  const R cs2 = (R)(phys[inst].cs * phys[inst].cs);
   for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
     const int p = q / N, j = q - p * N;
     C *b = sm + p * 12 * P + sm_idx<C>(j);
@@ -203,6 +261,7 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
       }
     }
   }
+  }
   __syncthreads();
 
   // 4. forward transforms of the 12 products
@@ -216,11 +275,11 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
     const C *pen = sm + (p * 12 + f) * P;
     const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
     C *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
-    dst[k] = C{z.re + zc.re, z.im - zc.im};
-    dst[NX + k] = C{z.im + zc.im, zc.re - z.re};
+    dst[k] = c_store(C{z.re + zc.re, z.im - zc.im});
+    dst[NX + k] = c_store(C{z.im + zc.im, zc.re - z.re});
   }
 
-  const R m = block_nan_max(smax, reinterpret_cast<R *>(red));
+  const SM m = block_nan_max(smax, reinterpret_cast<SM *>(red));
   if (threadIdx.x == 0) atomicMax(smax_bits + inst, max_bits((double)m));
 }
 
@@ -566,7 +625,7 @@ namespace {
 
 template <int N, typename C>
 cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
-                   cudaStream_t s, int *err, typename C::value_type *bgrid, uint32_t wait_polls) {
+                   cudaStream_t s, int *err, typename grid_of<C>::type *bgrid, uint32_t wait_polls) {
   constexpr int PAIRS = pairs_for(N);
   if constexpr (PAIRS == 1 && sizeof(C) == 8) {
     if (bgrid != nullptr) err = nullptr;  // the pipelined variant does not write the grid field
@@ -678,6 +737,11 @@ cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, un
                           const Dims &d, const cplx32 *tw, cudaStream_t s, int *err, float *bgrid,
                           uint32_t wait_polls) {
   MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls)));
+}
+
+cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
+                          const cdf *tw, cudaStream_t s, int *, double *bgrid, uint32_t) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, nullptr, bgrid, kWaitPolls)));
 }
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,

@@ -24,6 +24,7 @@
 #include "mhd.h"
 #include "mhd_internal.h"
 
+using mhd::cdf;
 using mhd::cplx32;
 using mhd::cplx64;
 
@@ -39,7 +40,8 @@ struct mhd_ctx {
   int precision = MHD_FP64;
   cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
   cplx32 *tw32 = nullptr;
-  cplx64 *S64 = nullptr;  // mixed precision: FP64 copy of one instance's state for set/get/diagnostics
+  cdf *twdf = nullptr;    // double-float mode: W_N^m as double-float values
+  cplx64 *S64 = nullptr;  // mixed and double-float modes: FP64 copy of one instance's state for set/get/diagnostics
   int integrator = MHD_AB2;
   void *Y = nullptr;      // stage state of RK4 / predictor-corrector ([b][7][spec], working precision)
   size_t w1_len = 0, w2_len = 0;  // bytes / 16
@@ -136,7 +138,7 @@ struct Sizes {
 
 Sizes sizes_for(const mhd::Dims &d, int precision) {
   const size_t n = d.n, nx = d.nx, nk = d.nk, b = d.batch;
-  const size_t elem = precision == MHD_FP64 ? 16 : 8;
+  const size_t elem = precision == MHD_FP32_MIXED ? 8 : 16;
   Sizes s;
   s.S = b * 7 * d.spec;
   // step (all instances, working precision)
@@ -157,6 +159,7 @@ Sizes sizes_for(const mhd::Dims &d, int precision) {
 size_t footprint(const mhd::Dims &d, int precision) {
   const Sizes s = sizes_for(d, precision);
   return (2 * s.S + s.W1 + s.W2) * sizeof(cplx64) + mhd::fp64_twiddle_size(d.n) + d.n * sizeof(cplx32) +
+         (precision == MHD_FP64_DF ? d.n * sizeof(cdf) : 0) +
          s.part * sizeof(double) +
          (precision == MHD_FP64 ? 0 : 7 * d.spec * sizeof(cplx64)) +
          d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) +
@@ -214,6 +217,12 @@ cplx32 *state_lo(mhd_ctx *c, int inst) {
   return reinterpret_cast<cplx32 *>(c->S) + ((size_t)c->d.batch + inst) * 7 * c->d.spec;
 }
 cplx32 *hist32(mhd_ctx *c, int inst) { return reinterpret_cast<cplx32 *>(c->H) + (size_t)inst * 7 * c->d.spec; }
+// Double-float mode: S, H (and the stage state) hold [b][7][spec] double-float complex values, the
+// same bytes per value as FP64.
+cdf *statedf(mhd_ctx *c, int inst) { return reinterpret_cast<cdf *>(c->S) + (size_t)inst * 7 * c->d.spec; }
+cdf *histdf(mhd_ctx *c, int inst) { return reinterpret_cast<cdf *>(c->H) + (size_t)inst * 7 * c->d.spec; }
+
+bool valid_precision(int p) { return p == MHD_FP64 || p == MHD_FP32_MIXED || p == MHD_FP64_DF; }
 
 void drop_graphs(mhd_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -230,7 +239,10 @@ mhd_status state_fp64(mhd_ctx *c, int inst, const cplx64 **out) {
     *out = state64(c, inst);
     return MHD_OK;
   }
-  CK(mhd::launch_combine_state(state_hi(c, inst), state_lo(c, inst), c->S64, 7 * c->d.spec, c->stream));
+  if (c->precision == MHD_FP64_DF)
+    CK(mhd::launch_combine_state(statedf(c, inst), c->S64, 7 * c->d.spec, c->stream));
+  else
+    CK(mhd::launch_combine_state(state_hi(c, inst), state_lo(c, inst), c->S64, 7 * c->d.spec, c->stream));
   *out = c->S64;
   return MHD_OK;
 }
@@ -267,7 +279,7 @@ mhd_status spectra_to_real(mhd_ctx *c, const cplx64 *src, double *a, double *b3,
 extern "C" {
 
 size_t mhd_footprint_bytes(int32_t n, int32_t precision, int32_t batch) {
-  if (!valid_n(n) || batch < 1 || (precision != MHD_FP64 && precision != MHD_FP32_MIXED)) return 0;
+  if (!valid_n(n) || batch < 1 || !valid_precision(precision)) return 0;
   return footprint(mhd::make_dims(n, batch), precision);
 }
 
@@ -295,7 +307,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (!p || !phys) return MHD_EINVAL;
   if (!valid_n(p->n) || p->batch < 1) return MHD_EINVAL;
   if (p->integrator < MHD_AB2 || p->integrator > MHD_PC) return MHD_EINVAL;
-  if (p->precision != MHD_FP64 && p->precision != MHD_FP32_MIXED) return MHD_EINVAL;
+  if (!valid_precision(p->precision)) return MHD_EINVAL;
   if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return MHD_EINVAL;
   for (int i = 0; i < p->batch; ++i) {
     if (!(phys[i].nu >= 0.0) || !(phys[i].eta >= 0.0) || !(phys[i].cs > 0.0) || !isfinite(phys[i].nu) ||
@@ -332,8 +344,9 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->tw = (cplx64 *)dalloc(c, mhd::fp64_twiddle_size(c->d.n))) != nullptr;
   ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
   if (c->precision != MHD_FP64) ok = ok && (c->S64 = (cplx64 *)dalloc(c, 7 * c->d.spec * sizeof(cplx64))) != nullptr;
+  if (c->precision == MHD_FP64_DF) ok = ok && (c->twdf = (cdf *)dalloc(c, (size_t)c->d.n * sizeof(cdf))) != nullptr;
   if (c->integrator != MHD_AB2)
-    ok = ok && (c->Y = dalloc(c, s.S * (c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32)))) != nullptr;
+    ok = ok && (c->Y = dalloc(c, s.S * (c->precision == MHD_FP32_MIXED ? sizeof(cplx32) : sizeof(cplx64)))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
   ok = ok && (c->smax_bits = (unsigned long long *)dalloc(c, 2 * p->batch * sizeof(unsigned long long))) != nullptr;
   ok = ok && (c->d_err = (int *)dalloc(c, 4 * sizeof(int))) != nullptr;
@@ -348,14 +361,18 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
     return MHD_ENOMEM;
   }
   std::vector<mhd::PhysDev> pd(p->batch);
-  for (int i = 0; i < p->batch; ++i) pd[i] = mhd::PhysDev{phys[i].nu, phys[i].eta, phys[i].cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
+  for (int i = 0; i < p->batch; ++i) pd[i] = mhd::make_phys(phys[i].nu, phys[i].eta, phys[i].cs);
   const std::vector<cplx64> w = mhd::twiddle_table(c->d.n);
   const std::vector<unsigned char> w64 = mhd::fp64_twiddle_bytes(c->d.n);
   std::vector<cplx32> w32(w.size());
   for (size_t i = 0; i < w.size(); ++i) w32[i] = cplx32{(float)w[i].re, (float)w[i].im};
+  std::vector<cdf> wdf(w.size());
+  for (size_t i = 0; i < w.size(); ++i) wdf[i] = cdf{mhd::dfr_const(w[i].re), mhd::dfr_const(w[i].im)};
   cudaError_t e = cudaMemcpyAsync(c->phys, pd.data(), pd.size() * sizeof(mhd::PhysDev), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w64.data(), w64.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw32, w32.data(), w32.size() * sizeof(cplx32), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && c->twdf)
+    e = cudaMemcpyAsync(c->twdf, wdf.data(), wdf.size() * sizeof(cdf), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
@@ -526,6 +543,9 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
   }
   if (fp64) {
     CK(cudaMemsetAsync(c->H + (size_t)inst * 7 * d.spec, 0, 7 * d.spec * sizeof(cplx64), c->stream));
+  } else if (c->precision == MHD_FP64_DF) {
+    CK(mhd::launch_split_state(c->S64, statedf(c, inst), 7 * d.spec, c->stream));
+    CK(cudaMemsetAsync(histdf(c, inst), 0, 7 * d.spec * sizeof(cdf), c->stream));
   } else {
     CK(mhd::launch_split_state(c->S64, state_hi(c, inst), state_lo(c, inst), 7 * d.spec, c->stream));
     CK(cudaMemsetAsync(hist32(c, inst), 0, 7 * d.spec * sizeof(cplx32), c->stream));
@@ -602,7 +622,7 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 template <typename CF, typename CS>
 static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, const CS *S, const mhd::PhysDev *phys,
                                  mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw,
-                                 typename CF::value_type *bgrid) {
+                                 typename mhd::grid_of<CF>::type *bgrid) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
@@ -642,6 +662,16 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
     LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
                                    c->stream, force));
+  } else if (c->precision == MHD_FP64_DF) {
+    const cdf *yi = static_cast<const cdf *>(y_in);
+    if ((st = flux_spectra_t<cdf>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->twdf,
+                                  static_cast<double *>(bgrid))))
+      return st;
+    cdf *Y = c->Y ? static_cast<cdf *>(c->Y) + off : nullptr;
+    cdf *force = c->forced ? reinterpret_cast<cdf *>(c->W2) : nullptr;  // W2 is free after the forward z pass
+    if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
+    LAUNCH(6, mhd::launch_assemble(reinterpret_cast<const cdf *>(c->W1), yi, statedf(c, inst0), histdf(c, inst0), Y,
+                                   rhs_out, phys, coef, op, stage, d, c->stream, force));
   } else {
     const cplx32 *yi = static_cast<const cplx32 *>(y_in);
     if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32,
@@ -662,10 +692,12 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
 static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 *rhs_out,
                               const mhd::PhysDev *phys, mhd::TimeState *ts, mhd::StepCoef *coef, int mode) {
   const size_t off = (size_t)inst0 * 7 * d.spec;
-  const void *y = c->precision == MHD_FP64 ? (const void *)state64(c, inst0) : (const void *)state_hi(c, inst0);
+  const void *y = c->precision == MHD_FP64      ? (const void *)state64(c, inst0)
+                  : c->precision == MHD_FP64_DF ? (const void *)statedf(c, inst0)
+                                                : (const void *)state_hi(c, inst0);
   const void *Y = nullptr;
-  if (c->Y) Y = c->precision == MHD_FP64 ? (const void *)(static_cast<cplx64 *>(c->Y) + off)
-                                         : (const void *)(static_cast<cplx32 *>(c->Y) + off);
+  if (c->Y) Y = c->precision == MHD_FP32_MIXED ? (const void *)(static_cast<cplx32 *>(c->Y) + off)
+                                               : (const void *)(static_cast<cplx64 *>(c->Y) + off);
   if (mode == 0) return eval_and_assemble(c, d, inst0, y, rhs_out, phys, ts, coef, true, mhd::ASM_RHS, 0);
   // tracers: the first evaluation (at y^n) also writes the grid field; the push follows the step
   void *bg = nullptr;
@@ -692,7 +724,7 @@ static mhd_status rhs_or_step(mhd_ctx *c, const mhd::Dims &d, int inst0, cplx64 
   for (int i = inst0; i < inst0 + d.batch; ++i) {
     if (c->ntr[i] == 0) continue;
     const size_t goff = (size_t)(i - inst0) * 3 * n3;
-    if (c->precision == MHD_FP64)
+    if (c->precision != MHD_FP32_MIXED)
       LAUNCH(7, mhd::launch_tracer_push(static_cast<const double *>(c->bgrid) + goff, c->tr[i], c->ntr[i], coef + i,
                                         d.n, c->stream));
     else
@@ -835,6 +867,15 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, int32_t *radix
   // one launch of column pass `kind` with tile width `tile` and radix `vpt`, on the step's
   // buffers and shapes
   auto run = [&](int kind, int tile, int vpt) -> cudaError_t {
+    if (c->precision == MHD_FP64_DF) {
+      cdf *w1 = reinterpret_cast<cdf *>(c->W1), *w2 = reinterpret_cast<cdf *>(c->W2);
+      switch (kind) {
+        case 0: return mhd::launch_col_inverse(statedf(c, 0), w1, d.n, b * 7, d.nk * d.nx, c->twdf, c->stream, tile);
+        case 1: return mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, c->twdf, c->stream, tile);
+        case 2: return mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, c->twdf, c->stream, tile);
+        default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->twdf, c->stream, tile);
+      }
+    }
     if (c->precision == MHD_FP64) {
       cplx64 *w1 = c->W1, *w2 = c->W2;
       switch (kind) {
@@ -852,18 +893,19 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, int32_t *radix
       default: return mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, c->tw32, c->stream, tile, vpt);
     }
   };
-  const size_t elem = c->precision == MHD_FP64 ? sizeof(cplx64) : sizeof(cplx32);
+  const size_t elem = c->precision == MHD_FP32_MIXED ? sizeof(cplx32) : sizeof(cplx64);
   const size_t pitch = (size_t)(d.n + d.n / (128 / (int)elem)) | 1;  // pencil pitch, as the kernels lay it out
   int best[4], best_vpt[4];
   double best_ms[4];
   cudaError_t err = cudaSuccess;
-  const bool fp64 = c->precision == MHD_FP64;
+  const bool fp64 = c->precision != MHD_FP32_MIXED;  // radix 8 only
   for (int kind = 0; kind < 4 && err == cudaSuccess; ++kind) {
     best[kind] = 0;
     best_vpt[kind] = 0;
     best_ms[kind] = 1e300;
     for (int vpt = 8; vpt <= (fp64 ? 8 : 16) && err == cudaSuccess; vpt *= 2) {
-      const int max_tc = mhd::col_max_tile(d.n, kind < 2 ? +1 : -1, fp64, false, vpt);
+      const int max_tc = c->precision == MHD_FP64_DF ? mhd::col_max_tile_df(d.n, kind < 2 ? +1 : -1)
+                                                     : mhd::col_max_tile(d.n, kind < 2 ? +1 : -1, fp64, false, vpt);
       for (int tc = 1; tc <= max_tc && err == cudaSuccess; tc *= 2) {
         if (tc * pitch * elem > 227 * 1024) break;
         if ((err = run(kind, tc, vpt)) != cudaSuccess) break;  // warm-up (raises the shared-memory limit)
@@ -929,7 +971,8 @@ mhd_status mhd_set_forcing(mhd_ctx *c, int32_t inst, double amp, double a, doubl
   if (!isfinite(amp) || !isfinite(a) || !isfinite(b) || !isfinite(cc)) return fail(c, MHD_EINVAL, "non-finite forcing");
   if (kf < 1 || kf > c->d.k) return fail(c, MHD_EINVAL, "forcing wavenumber %d outside 1..%d", kf, c->d.k);
   DeviceGuard g(c->device);
-  const mhd::PhysDev pd{c->phys_host[inst].nu, c->phys_host[inst].eta, c->phys_host[inst].cs, amp, a, b, cc, kf, 0};
+  const mhd::PhysDev pd = mhd::make_phys(c->phys_host[inst].nu, c->phys_host[inst].eta, c->phys_host[inst].cs, amp, a,
+                                         b, cc, kf);
   CK(cudaMemcpyAsync(c->phys + inst, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (amp != 0.0 && !c->forced) {
@@ -968,7 +1011,7 @@ mhd_status mhd_tracers_set(mhd_ctx *c, int32_t inst, int64_t count, const double
   const mhd::Dims d = one(c);
   const size_t n3 = (size_t)d.n * d.n * d.n;
   if (!c->bgrid) {
-    const size_t elem = c->precision == MHD_FP64 ? sizeof(double) : sizeof(float);
+    const size_t elem = c->precision == MHD_FP32_MIXED ? sizeof(float) : sizeof(double);
     if (!(c->bgrid = dalloc(c, (size_t)c->d.batch * 3 * n3 * elem))) return fail(c, MHD_ENOMEM, "tracer grid buffer");
   }
   double *t = static_cast<double *>(dalloc(c, (size_t)count * 6 * sizeof(double)));
@@ -1144,7 +1187,7 @@ mhd_status mhd_checkpoint(mhd_ctx *c, int32_t inst, double *buf, int32_t on_devi
   DeviceGuard g(c->device);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (c->precision == MHD_FP64) {
+  if (c->precision != MHD_FP32_MIXED) {  // FP64, or double-float values in the same bytes
     CK(cudaMemcpyAsync(buf, state64(c, inst), sp * sizeof(cplx64), k, c->stream));
     CK(cudaMemcpyAsync(buf + 2 * sp, c->H + (size_t)inst * sp, sp * sizeof(cplx64), k, c->stream));
   } else {
@@ -1175,7 +1218,7 @@ mhd_status mhd_restore(mhd_ctx *c, int32_t inst, const double *buf, int32_t on_d
   DeviceGuard g(c->device);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (c->precision == MHD_FP64) {
+  if (c->precision != MHD_FP32_MIXED) {  // FP64, or double-float values in the same bytes
     CK(cudaMemcpyAsync(state64(c, inst), buf, sp * sizeof(cplx64), k, c->stream));
     CK(cudaMemcpyAsync(c->H + (size_t)inst * sp, buf + 2 * sp, sp * sizeof(cplx64), k, c->stream));
   } else {
@@ -1204,7 +1247,7 @@ struct mhd_pool {
 static mhd_status move_instance(mhd_ctx *c, int from, int to) {
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-  if (c->precision == MHD_FP64) {
+  if (c->precision != MHD_FP32_MIXED) {  // FP64, or double-float values in the same bytes
     CK(cudaMemcpyAsync(state64(c, to), state64(c, from), sp * sizeof(cplx64), k, c->stream));
     CK(cudaMemcpyAsync(c->H + (size_t)to * sp, c->H + (size_t)from * sp, sp * sizeof(cplx64), k, c->stream));
   } else {
@@ -1277,7 +1320,7 @@ mhd_status mhd_pool_admit(mhd_pool *p, const mhd_phys *phys, const double *rho, 
   if (handle < 0) return MHD_EBUSY;
   DeviceGuard g(c->device);
   const int pos = c->live;
-  const mhd::PhysDev pd{phys->nu, phys->eta, phys->cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
+  const mhd::PhysDev pd = mhd::make_phys(phys->nu, phys->eta, phys->cs);
   CK(cudaMemcpyAsync(c->phys + pos, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
   c->phys_host[pos] = *phys;
   mhd_status st = mhd_set_state(c, pos, rho, u, b, on_device);

@@ -19,6 +19,8 @@
 
 #include <vector>
 
+#include "dfloat.cuh"
+
 namespace mhd {
 
 constexpr int kStateFields = 7;  // rho, m_x, m_y, m_z, B_x, B_y, B_z
@@ -49,6 +51,8 @@ struct StepCoef {
   double dt, a1, a0;
   float fdt, fa1, fa0;  // the same, rounded once, for the mixed-precision update
   int32_t skip;
+  // the double-float update's weights, split from their FP64 values: dt, dt a1, dt a0, dt / 6
+  dfr dt_df, dta1_df, dta0_df, dt6_df;
 };
 
 // Per-instance physical parameters in device memory; famp != 0 switches on the ABC body force
@@ -57,6 +61,31 @@ struct PhysDev {
   double nu, eta, cs;
   double famp, fa, fb, fc;
   int fkf, pad;
+  dfr nu_df, eta_df, cs2_df;  // nu, eta and cs^2 split into double-float (the double-float assembly)
+};
+
+__host__ __device__ inline PhysDev make_phys(double nu, double eta, double cs, double famp = 0.0, double fa = 0.0,
+                                             double fb = 0.0, double fc = 0.0, int kf = 1) {
+  return PhysDev{nu, eta, cs, famp, fa, fb, fc, kf, 0, dfr_const(nu), dfr_const(eta), dfr_const(cs * cs)};
+}
+
+// Element type a pass scales its output by (a power of two in the double-float passes), and of a
+// grid field written out for the tracers (FP64 for the double-float passes).
+template <typename C>
+struct scale_of {
+  using type = typename C::value_type;
+};
+template <>
+struct scale_of<cdf> {
+  using type = float;
+};
+template <typename C>
+struct grid_of {
+  using type = typename C::value_type;
+};
+template <>
+struct grid_of<cdf> {
+  using type = double;
 };
 
 struct Dims {
@@ -111,6 +140,13 @@ cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, 
                                double scale, const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
                                double scale, const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
+// Double-float passes (MHD_FP64_DF): data, twiddles (W_N^m as hi + lo pairs) and arithmetic in
+// double-float, radix 8; `scale` must be a power of two.
+cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
+                               int tile = 0, int vpt = 0);
+cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
+                               cudaStream_t s, int tile = 0, int vpt = 0);
+int col_max_tile_df(int n, int dir);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
 // grid, forward real transforms of the 12 product fields (kx <= K kept), and the maximum of
@@ -127,6 +163,11 @@ cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, un
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr,
                           float *bgrid = nullptr, uint32_t wait_polls = kWaitPolls);
+// Double-float flux pass (MHD_FP64_DF): products in double-float, exact FP64 CFL maximum as in
+// the FP64 pass, grid magnetic field for the tracers in FP64.
+cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
+                          const cdf *tw, cudaStream_t s, int *err = nullptr, double *bgrid = nullptr,
+                          uint32_t wait_polls = kWaitPolls);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
@@ -189,6 +230,17 @@ cudaError_t launch_assemble_df(const cplx32 *flux, const cplx32 *y_in, cplx32 *s
 // FP64 spectra <-> (hi, lo) pairs of `count` complex values.
 cudaError_t launch_split_state(const cplx64 *in, cplx32 *hi, cplx32 *lo, size_t count, cudaStream_t s);
 cudaError_t launch_combine_state(const cplx32 *hi, const cplx32 *lo, cplx64 *out, size_t count, cudaStream_t s);
+
+// Double-float mode (MHD_FP64_DF): state, history and stage state as double-float complex values
+// [inst][7][spec]; the RHS, the update and the force spectra in double-float arithmetic; ASM_RHS
+// writes the RHS in FP64 to `rhs_out`.
+cudaError_t launch_assemble(const cdf *flux, const cdf *y_in, cdf *state, cdf *hist, cdf *ystage, cplx64 *rhs_out,
+                            const PhysDev *phys, const StepCoef *coef, int op, int stage, const Dims &d,
+                            cudaStream_t s, const cdf *force = nullptr);
+cudaError_t launch_force(const cdf *y_in, cdf *force, const PhysDev *phys, const Dims &d, cudaStream_t s);
+// FP64 spectra <-> double-float complex values.
+cudaError_t launch_split_state(const cplx64 *in, cdf *out, size_t count, cudaStream_t s);
+cudaError_t launch_combine_state(const cdf *in, cplx64 *out, size_t count, cudaStream_t s);
 
 // Final reduction of the diagnostic partials of one instance plus the spectral terms; writes
 // 24 doubles to `out` (see mhd_api.cu for the order).

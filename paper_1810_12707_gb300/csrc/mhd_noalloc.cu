@@ -109,7 +109,7 @@ cudaError_t setup_device(unsigned char **base) {
 
 // The instance's parameters, written on the caller's stream from kernel arguments.
 __global__ void set_phys_kernel(mhd::PhysDev *pd, double nu, double eta, double cs) {
-  *pd = mhd::PhysDev{nu, eta, cs, 0.0, 0.0, 0.0, 0.0, 1, 0};
+  *pd = mhd::make_phys(nu, eta, cs);
 }
 
 }  // namespace

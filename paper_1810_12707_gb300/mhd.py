@@ -23,6 +23,7 @@ LIBRARY = os.path.join(_PKG, "libmhd_gb300.so")
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ESTATE, MHD_ENONFINITE, MHD_ETIMEOUT, MHD_EBUSY = range(8)
 MHD_FP64 = 0
 MHD_FP32_MIXED = 1
+MHD_FP64_DF = 2
 MHD_AB2, MHD_RK4, MHD_PC = 0, 1, 2
 (MHD_OPT_CUDA_GRAPH, MHD_OPT_TILE_INV_Z, MHD_OPT_TILE_INV_Y, MHD_OPT_TILE_FWD_Y, MHD_OPT_TILE_FWD_Z,
  MHD_OPT_FLUX_PIPELINE, MHD_OPT_RADIX_INV_Z, MHD_OPT_RADIX_INV_Y, MHD_OPT_RADIX_FWD_Y,

@@ -36,9 +36,14 @@ def test_footprint_is_pure_host_arithmetic():
     assert mhd.mhd_footprint_bytes(8, 0, 1) == 0           # below the smallest grid, 16
     assert mhd.mhd_footprint_bytes(2048, 0, 1) == 0        # above the largest, 1024
     assert mhd.mhd_footprint_bytes(256, 0, 0) == 0         # no instance
-    assert mhd.mhd_footprint_bytes(256, 2, 1) == 0         # no such precision
+    assert mhd.mhd_footprint_bytes(256, 3, 1) == 0         # no such precision
     f256 = mhd.mhd_footprint_bytes(256, 0, 1)
     assert 2e9 < f256 < 3e9
+    # the double-float mode stores FP64-sized values: FP64's footprint plus its twiddle table
+    # and the FP64 copy of one instance's state
+    k = (256 - 1) // 3
+    spec = (2 * k + 1) ** 2 * (k + 1)
+    assert mhd.mhd_footprint_bytes(256, 2, 1) == f256 + 256 * 16 + 7 * spec * 16
     assert mhd.mhd_footprint_bytes(1024, 0, 1) < 200e9     # the largest grid fits in HBM
 
 
