@@ -151,9 +151,13 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
     screen = (float)(lb * (1.0 - 1e-6) - 1e-18);
   }
   if constexpr (kDF) {
-    // double-float products; the speed's squares are renormalised, so their high parts are the
-    // FP32 roundings the screening estimate assumes, and the exact speed is taken in FP64 from
-    // the double-float squares
+    // double-float products.  The grid values leave the inverse transforms unnormalised; near a
+    // zero of a field (a stagnation point) their low part can exceed the high part, and the
+    // square of such a pair, which drops lo^2, can come out negative.  So they are renormalised
+    // first (then |lo| <= ulp(hi) / 2 and every square is >= 0), as are the velocity components
+    // before the speed is formed; the speed's squares are renormalised too, so their high parts
+    // are the FP32 roundings the screening estimate assumes, and the exact speed is taken in FP64
+    // from the double-float squares.
     const double csd = phys[inst].cs;
     const dfr cs2 = dfr_from_double(csd * csd);
     for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
@@ -163,8 +167,8 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
 #pragma unroll
       for (int f = 0; f < 7; ++f) {
         const C c = b[f * P];
-        v[0][f] = c.re;
-        v[1][f] = c.im;
+        v[0][f] = dfr_norm(c.re);
+        v[1][f] = dfr_norm(c.im);
       }
       if (bgrid != nullptr) {
         constexpr size_t N3 = NN * N;
@@ -198,7 +202,8 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
         bd[2 * 9 * P + h] = ux;
         bd[2 * 10 * P + h] = uy;
         bd[2 * 11 * P + h] = uz;
-        const dfr u2 = dfr_norm(ux * ux + uy * uy + uz * uz), c2 = dfr_norm(cs2 + b2 * ir);
+        const dfr nx = dfr_norm(ux), ny = dfr_norm(uy), nz = dfr_norm(uz);
+        const dfr u2 = dfr_norm(nx * nx + ny * ny + nz * nz), c2 = dfr_norm(cs2 + b2 * ir);
         if (!(sqrtf(u2.hi) + sqrtf(c2.hi) < screen)) {
           const double s = sqrt(dfr_to_double(u2)) + sqrt(dfr_to_double(c2));
           smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
