@@ -41,38 +41,9 @@ __device__ __forceinline__ CT c_cvt(CF a) {
   return CT{(R)a.re, (R)a.im};
 }
 
-// Complex double-float values (packed pairs, dfloat.cuh).  A pass scales its output by a power
-// of two only, given as an FP32 number.
-__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return a + b; }
-__device__ __forceinline__ cdf c_sub(cdf a, cdf b) { return a - b; }
-__device__ __forceinline__ cdf c_scale(cdf a, float s) { return cdf_scale2(a, s); }
-template <int DIR>
-__device__ __forceinline__ cdf c_mul_i(cdf a) { return DIR > 0 ? cdf_mul_i(a) : cdf_mul_negi(a); }
-__device__ __forceinline__ cdf c_mul(cdf a, cdftw w) { return cdf_cmul(a, w.wr, w.wi); }
-__device__ __forceinline__ cdf c_mulc(cdf a, cdftw w) { return a * w.wr - cdf_swap(a) * w.wi; }
-template <typename CT>
-__device__ __forceinline__ CT c_cvt(cdf a) { return a; }
-
-// The two real rows z = row0 + i row1 of an x pass, from and to their truncated half spectra
-// X0, X1 (see kernels_x.cu): inverse Z[k] = X0 + i X1, Z[N - k] = conj(X0) + i conj(X1),
-// Z[0] = (Re X0, Re X1); forward 2 X0 = Z[k] + conj Z[N - k], 2 X1 = -i (Z[k] - conj Z[N - k]).
-template <typename C>
-__device__ __forceinline__ C pair_lo(C x0, C x1) { return C{x0.re - x1.im, x0.im + x1.re}; }
-template <typename C>
-__device__ __forceinline__ C pair_hi(C x0, C x1) { return C{x0.re + x1.im, x1.re - x0.im}; }
-template <typename C>
-__device__ __forceinline__ C pair_dc(C x0, C x1) { return C{x0.re, x1.re}; }
-template <typename C>
-__device__ __forceinline__ C split0(C z, C zc) { return C{z.re + zc.re, z.im - zc.im}; }
-template <typename C>
-__device__ __forceinline__ C split1(C z, C zc) { return C{z.im + zc.im, zc.re - z.re}; }
-__device__ __forceinline__ cdf pair_lo(cdf x0, cdf x1) { return x0 + cdf_mul_i(x1); }
-__device__ __forceinline__ cdf pair_hi(cdf x0, cdf x1) { return cdf_conj(x0) + cdf_swap(x1); }
-__device__ __forceinline__ cdf pair_dc(cdf x0, cdf x1) {
-  return cdf{make_float2(x0.hi.x, x1.hi.x), make_float2(x0.lo.x, x1.lo.x)};
-}
-__device__ __forceinline__ cdf split0(cdf z, cdf zc) { return z + cdf_conj(zc); }
-__device__ __forceinline__ cdf split1(cdf z, cdf zc) { return cdf_swap(zc) + cdf_mul_negi(z); }
+// Double-float complex values use the generic forms above through the dfr operators (lazy sums
+// and products).  A pass scales its output by a power of two only, given as an FP32 number.
+__device__ __forceinline__ cdf c_scale(cdf a, float s) { return cdf{s * a.re, s * a.im}; }
 
 // What a pass stores to global memory: double-float values renormalised, others as they are.
 template <typename C>
@@ -185,8 +156,8 @@ __device__ __forceinline__ void dft16(C *v) {
   }
 }
 
-// Length 8 in double-float: the same split as above; W8 = h (1 + DIR i) and W8^3 = h (-1 + DIR i)
-// with h = sqrt(2)/2 in double-float: c1 W8 = h (c1 + DIR i c1), c3 W8^3 = h (DIR i c3 - c3).
+// Length 8 in double-float: the same split as above; W8 = h (1 + DIR i) with h = sqrt(2)/2 in
+// double-float.
 template <int DIR>
 __device__ __forceinline__ void dft8(cdf *v) {
   constexpr dfr h = dfr_const(0.70710678118654752440);
@@ -196,8 +167,13 @@ __device__ __forceinline__ void dft8(cdf *v) {
     b[j] = c_add(v[j], v[j + 4]);
     c[j] = c_sub(v[j], v[j + 4]);
   }
-  c[1] = h * (c[1] + c_mul_i<DIR>(c[1]));
-  c[3] = h * (c_mul_i<DIR>(c[3]) - c[3]);
+  if constexpr (DIR > 0) {
+    c[1] = cdf{h * (c[1].re - c[1].im), h * (c[1].im + c[1].re)};
+    c[3] = cdf{h * (-c[3].re - c[3].im), h * (c[3].re - c[3].im)};
+  } else {
+    c[1] = cdf{h * (c[1].re + c[1].im), h * (c[1].im - c[1].re)};
+    c[3] = cdf{h * (c[3].im - c[3].re), h * (-c[3].im - c[3].re)};
+  }
   c[2] = c_mul_i<DIR>(c[2]);
   dft4<DIR>(b);
   dft4<DIR>(c);
@@ -218,14 +194,11 @@ __device__ __forceinline__ void dft_small(C *v) {
 
 // Twiddle load that the compiler may not hoist out of loops: kernels that transform many pencils
 // in a loop would otherwise keep every stage's twiddles live in registers across the loop.
-__device__ __forceinline__ cdftw tw_load(const cdftw *p) {
-  cdftw v;
+__device__ __forceinline__ cdf tw_load(const cdf *p) {
+  cdf v;
   asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.wr.hi.x), "=f"(v.wr.hi.y), "=f"(v.wr.lo.x), "=f"(v.wr.lo.y)
+               : "=f"(v.re.hi), "=f"(v.re.lo), "=f"(v.im.hi), "=f"(v.im.lo)
                : "l"(p));
-  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.wi.hi.x), "=f"(v.wi.hi.y), "=f"(v.wi.lo.x), "=f"(v.wi.lo.y)
-               : "l"(reinterpret_cast<const char *>(p) + 16));
   return v;
 }
 __device__ __forceinline__ cplx64 tw_load(const cplx64 *p) {
@@ -434,8 +407,8 @@ __device__ __forceinline__ void dft8_first_fma(C *v) {
 template <int DIR, bool ZP>
 __device__ __forceinline__ void dft8_first_fma(cdf *v) {
   if constexpr (ZP) {
-    v[3] = cdf_zero();
-    v[4] = cdf_zero();
+    v[3] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+    v[4] = cdf{{0.f, 0.f}, {0.f, 0.f}};
   }
   dft8<DIR>(v);
 }
@@ -468,8 +441,7 @@ __host__ __device__ constexpr int fft_tpp() { return tpp_for<N, fft_vpt<C>()>();
 // `active == false` only take part in the barriers.  The caller separates the transform from the
 // preceding writes and the following reads of the pencil with a block barrier.
 template <int N, int DIR, int NS, typename C, int VPT, bool ZP>
-__device__ __forceinline__ void stockham_stages(C *buf, int t, bool active,
-                                                const typename twiddle_of<C>::type *__restrict__ tw) {
+__device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
     static_assert(VPT == 8 || (VPT == 16 && sizeof(C) == 8), "radix 16 is an FP32 option");
     constexpr int R = (N / NS >= VPT) ? VPT : N / NS;
@@ -500,7 +472,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active,
           if (kFirst16 && r >= 6 && r <= 9) continue;
           C x = buf[sm_idx<C>(j + r * (N / R))];
           if (!kFma && NS > 1 && r > 0) {
-            const auto w = tw_load(tw + r * k * TWSTEP);
+            const C w = tw_load(tw + r * k * TWSTEP);
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
           }
           v[b * R + r] = x;
@@ -538,8 +510,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active,
 // transform of a truncated spectrum is; the FP64 first stage then skips the inputs it knows are
 // zero (they need not even be written).
 template <int N, int DIR, typename C, int VPT = fft_vpt<C>(), bool ZP = false>
-__device__ __forceinline__ void pencil_fft(C *buf, int t, bool active,
-                                           const typename twiddle_of<C>::type *__restrict__ tw) {
+__device__ __forceinline__ void pencil_fft(C *buf, int t, bool active, const C *__restrict__ tw) {
   stockham_stages<N, DIR, 1, C, VPT, ZP>(buf, t, active, tw);
 }
 

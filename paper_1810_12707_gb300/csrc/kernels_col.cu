@@ -24,8 +24,7 @@ namespace mhd {
 // VPT: values per thread of the transform (8, or 16 for FP32), so N / VPT threads per column.
 template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
 __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
-                               int cols, typename scale_of<CC>::type scale,
-                               const typename twiddle_of<CC>::type *__restrict__ tw) {
+                               int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CC *sm = reinterpret_cast<CC *>(smem_raw);
   constexpr int TPP = tpp_for<N, VPT>();
@@ -112,8 +111,8 @@ int col_max_threads() {
 }
 
 template <int N, int DIR, typename CI, typename CO, int VPT>
-cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scale,
-                         const typename twiddle_of<CO>::type *tw, cudaStream_t s, int tile) {
+cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
+                         cudaStream_t s, int tile) {
   constexpr int TPP = tpp_for<N, VPT>();
   int tc = tile > 0 ? tile : pick_tc(TPP, cols);
   const int max_threads = col_max_threads<N, DIR, CI, CO, VPT>();
@@ -138,8 +137,8 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
 // Radix of a column pass: `vpt` 8 or 16 (FP32 only); 0 picks the library default (radix 8, and
 // radix 16 for FP32 at N >= 512, where it measured faster).
 template <int N, int DIR, typename CI, typename CO>
-cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale,
-                         const typename twiddle_of<CO>::type *tw, cudaStream_t s, int tile, int vpt) {
+cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
+                         cudaStream_t s, int tile, int vpt) {
   if constexpr (sizeof(CO) == 8) {
     if (vpt == 16 || (vpt == 0 && N >= 512))
       return launch_col_v<N, DIR, CI, CO, 16>(in, out, nslab, cols, scale, tw, s, tile);
@@ -148,8 +147,8 @@ cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scal
 }
 
 template <int DIR, typename CI, typename CO>
-cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale,
-                       const typename twiddle_of<CO>::type *tw, cudaStream_t s, int tile, int vpt) {
+cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale, const CO *tw,
+                       cudaStream_t s, int tile, int vpt) {
   switch (n) {
     case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
     case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
@@ -230,11 +229,11 @@ cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, 
                                double scale, const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
   return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, vpt);
 }
-cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdftw *tw,
-                               cudaStream_t s, int tile, int) {
+cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
+                               int tile, int) {
   return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
 }
-cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdftw *tw,
+cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
                                cudaStream_t s, int tile, int) {
   return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8);
 }

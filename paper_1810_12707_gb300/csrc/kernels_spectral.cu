@@ -15,10 +15,6 @@
 
 namespace mhd {
 
-template <typename CT>
-__device__ __forceinline__ CT c_conj(CT v) { return CT{v.re, -v.im}; }
-__device__ __forceinline__ cdf c_conj(cdf v) { return cdf_conj(v); }
-
 // rho_hat at wavevector (kx, ky, kz) of one instance's truncated density spectrum (zero outside
 // the kept set; kx < 0 through Hermitian symmetry).
 template <typename CT>
@@ -32,7 +28,7 @@ __device__ __forceinline__ CT rho_at(const CT *rho, int kx, int ky, int kz, int 
     kz = -kz;
   }
   const CT v = rho[((size_t)(kz >= 0 ? kz : kz + NK) * NK + (ky >= 0 ? ky : ky + NK)) * NX + kx];
-  return cj ? c_conj(v) : v;
+  return cj ? CT{v.re, -v.im} : v;
 }
 
 // Spectrum of rho f_ABC at (kx, ky, kz): the product with sin(kf s) and cos(kf s) shifts the
@@ -334,7 +330,7 @@ __global__ void force_dfloat_kernel(const cdf *__restrict__ y_in, cdf *__restric
     abc_force<cplx64>(
         [&](int x, int y, int z) {
           const cdf v = rho_at(rho, x, y, z, K);
-          return cplx64{dfr_to_double(cdf_x(v)), dfr_to_double(cdf_y(v))};
+          return cplx64{dfr_to_double(v.re), dfr_to_double(v.im)};
         },
         kxi, kept_wave((int)(t % NK), K), kept_wave((int)(t / NK), K), ph, fo);
 #pragma unroll
@@ -370,16 +366,13 @@ __global__ void split_cdf_kernel(const cplx64 *__restrict__ in, cdf *__restrict_
 __global__ void combine_cdf_kernel(const cdf *__restrict__ in, cplx64 *__restrict__ out, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     const cdf v = in[i];
-    out[i] = cplx64{dfr_to_double(cdf_x(v)), dfr_to_double(cdf_y(v))};
+    out[i] = cplx64{dfr_to_double(v.re), dfr_to_double(v.im)};
   }
 }
 
 // Double-float mode: the RHS of the FP64 assembly above, term by term in the same order, and the
-// update of the double-float state, in double-float arithmetic on packed (re, im) pairs (no FP64
-// operation per mode).  The wavenumbers, k^2 and the product spectra's factor 1/(2 N^3) are exact
-// FP32 numbers.
-__device__ __forceinline__ dfr dfr_half(dfr a) { return dfr{__fmul_rn(a.hi, 0.5f), __fmul_rn(a.lo, 0.5f)}; }
-
+// update of the double-float state, in double-float arithmetic (no FP64 operation per mode).  The
+// wavenumbers, k^2 and the product spectra's factor 1/(2 N^3) are exact FP32 numbers.
 __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *y_in, cdf *state,
                                        cdf *__restrict__ hist, cdf *ystage, cplx64 *__restrict__ rhs_out,
                                        const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
@@ -398,9 +391,9 @@ __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *
     const int jy = (int)(t % NK), jz = (int)(t / NK);
     const float kx = (float)kxi, ky = (float)kept_wave(jy, K), kz = (float)kept_wave(jz, K);
     const float k2 = __fadd_rn(__fadd_rn(__fmul_rn(kx, kx), __fmul_rn(ky, ky)), __fmul_rn(kz, kz));  // exact
-    const cdf nu = cdf_bc(phys[inst].nu_df), eta = cdf_bc(phys[inst].eta_df), cs2 = cdf_bc(phys[inst].cs2_df);
+    const dfr nu = phys[inst].nu_df, eta = phys[inst].eta_df, cs2 = phys[inst].cs2_df;
     const float skx = __fmul_rn(kx, inv_n3), sky = __fmul_rn(ky, inv_n3), skz = __fmul_rn(kz, inv_n3);
-    const cdf nuk2s = cdf_scale2(k2 * nu, inv_n3);
+    const dfr nuk2s = dfr_scale2(k2 * nu, inv_n3);
 
     const cdf *S = y_in + (size_t)inst * 7 * spec + m;
     const cdf *F = flux + (size_t)inst * 12 * spec + m;
@@ -413,34 +406,43 @@ __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *
     const cdf Ex = f[6], Ey = f[7], Ez = f[8];
 
     cdf r[7];
-    // continuity: -i k . m
-    r[0] = cdf_mul_negi(kx * y[1] + ky * y[2] + kz * y[3]);
-    {  // momentum: -i k_j T_ij - i k_i cs^2 rho - nu k^2 u_i
+    {  // continuity: -i k . m
+      const cdf s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+      r[0] = cdf{s.im, -s.re};
+    }
+    {  // momentum
       const float kk[3] = {kx, ky, kz};
       const cdf T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const cdf divT = skx * T[a][0] + sky * T[a][1] + skz * T[a][2];
-        const cdf g = divT + (kk[a] * cs2) * y[0];
-        r[1 + a] = cdf_mul_negi(g) - nuk2s * f[9 + a];
+        const cdf divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
+                          skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
+        const dfr kc = kk[a] * cs2;
+        const cdf g = {divT.re + kc * y[0].re, divT.im + kc * y[0].im};
+        const cdf u = f[9 + a];
+        r[1 + a] = cdf{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
       }
       if (force != nullptr && phys[inst].famp != 0.0) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) r[1 + a] = r[1 + a] + force[((size_t)inst * 3 + a) * spec + m];
+        for (int a = 0; a < 3; ++a) {
+          const cdf fo = force[((size_t)inst * 3 + a) * spec + m];
+          r[1 + a] = cdf{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+        }
       }
     }
     {  // induction: i k x E - eta k^2 B
-      const cdf c[3] = {sky * Ez - skz * Ey, skz * Ex - skx * Ez, skx * Ey - sky * Ex};
-      const cdf etak2 = k2 * eta;
+      const cdf c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
+                        {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
+                        {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
+      const dfr etak2 = k2 * eta;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) r[4 + a] = cdf_mul_i(c[a]) - etak2 * y[4 + a];
+      for (int a = 0; a < 3; ++a) r[4 + a] = cdf{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
     }
 
     const size_t o7 = (size_t)inst * 7 * spec + m;
     if (op == ASM_RHS) {
 #pragma unroll
-      for (int q = 0; q < 7; ++q)
-        rhs_out[o7 + q * spec] = cplx64{dfr_to_double(cdf_x(r[q])), dfr_to_double(cdf_y(r[q]))};
+      for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = cplx64{dfr_to_double(r[q].re), dfr_to_double(r[q].im)};
       continue;
     }
     const StepCoef cf = coef[inst];
@@ -451,19 +453,25 @@ __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *
       if (op == ASM_AB2 || op == ASM_PC_PRED) {
         // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
         cdf y0 = state[i];
-        if (cf.a0 != 0.0) y0 = y0 + cf.dta0_df * hist[i];
-        const cdf yn = cdf_norm(y0 + cf.dta1_df * rq);
+        if (cf.a0 != 0.0) {
+          const cdf h = hist[i];
+          y0 = cdf{y0.re + cf.dta0_df * h.re, y0.im + cf.dta0_df * h.im};
+        }
+        const cdf yn = cdf_norm(cdf{y0.re + cf.dta1_df * rq.re, y0.im + cf.dta1_df * rq.im});
         if (op == ASM_AB2) state[i] = yn;
         else ystage[i] = yn;
         hist[i] = cdf_norm(rq);
       } else if (op == ASM_RK_STAGE) {
-        const cdf acc = cdf_norm(stage == 1 ? rq : hist[i] + cdf_scale2(rq, 2.f));
+        const cdf acc = cdf_norm(stage == 1 ? rq : cdf{hist[i].re + dfr_scale2(rq.re, 2.f), hist[i].im + dfr_scale2(rq.im, 2.f)});
         hist[i] = acc;
-        const dfr w = stage < 3 ? dfr_half(cf.dt_df) : cf.dt_df;
-        ystage[i] = cdf_norm(state[i] + w * rq);
+        const dfr w = stage < 3 ? dfr_scale2(cf.dt_df, 0.5f) : cf.dt_df;
+        const cdf y0 = state[i];
+        ystage[i] = cdf_norm(cdf{y0.re + w * rq.re, y0.im + w * rq.im});
       } else {  // ASM_RK_FINAL, ASM_PC_CORR
-        const dfr w = op == ASM_RK_FINAL ? cf.dt6_df : dfr_half(cf.dt_df);
-        state[i] = cdf_norm(state[i] + w * (hist[i] + rq));
+        const dfr w = op == ASM_RK_FINAL ? cf.dt6_df : dfr_scale2(cf.dt_df, 0.5f);
+        const cdf h = hist[i], y0 = state[i];
+        const cdf acc = {h.re + rq.re, h.im + rq.im};
+        state[i] = cdf_norm(cdf{y0.re + w * acc.re, y0.im + w * acc.im});
       }
     }
   }

@@ -61,9 +61,8 @@ constexpr int flux_min_blocks() {
 // so the stages synchronise per group; one block barrier closes the whole transform.
 // Every inverse (DIR = +1) transform here starts from a truncated half spectrum, so its pencil is
 // zero-padded by the 2/3 rule (see pencil_fft).
-template <int N, int DIR, int VPT, typename Ptr, typename TW>
-__device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const TW *__restrict__ tw) {
-  using C = typename std::remove_pointer<decltype(ptr(0))>::type;
+template <int N, int DIR, int VPT, typename Ptr, typename C>
+__device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
   constexpr int TPP = tpp_for<N, VPT>();
   const int G = blockDim.x / TPP;
   const int g = threadIdx.x / TPP, t = threadIdx.x - g * TPP;
@@ -87,7 +86,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const TW *__restric
 template <int N, typename C>
 __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
                               const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
-                              int K, int blocks_per_inst, const typename twiddle_of<C>::type *__restrict__ tw,
+                              int K, int blocks_per_inst, const C *__restrict__ tw,
                               typename grid_of<C>::type *__restrict__ bgrid) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
@@ -118,10 +117,10 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
       C *pen = sm + (p * 12 + f) * P;
       const C x0 = src[k], x1 = src[NX + k];
       if (k == 0) {
-        pen[0] = pair_dc(x0, x1);
+        pen[0] = C{x0.re, x1.re};
       } else {
-        pen[sm_idx<C>(k)] = pair_lo(x0, x1);
-        pen[sm_idx<C>(N - k)] = pair_hi(x0, x1);
+        pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
+        pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
       }
     }
   }
@@ -152,58 +151,63 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
     screen = (float)(lb * (1.0 - 1e-6) - 1e-18);
   }
   if constexpr (kDF) {
-    // double-float products, the point's two rows (real and imaginary parts of the pencil
-    // element) side by side in the packed lanes.  The grid values leave the inverse transforms
-    // unnormalised; near a zero of a field (a stagnation point) their low part can exceed the
-    // high part, and the square of such a pair, which drops lo^2, can come out negative.  So they
-    // are renormalised first (then |lo| <= ulp(hi) / 2 and every square is >= 0), as are the
-    // velocity components before the speed is formed; the speed's squares are renormalised too,
-    // so their high parts are the FP32 roundings the screening estimate assumes, and the exact
-    // speed is taken in FP64 from the double-float squares.
+    // double-float products.  The grid values leave the inverse transforms unnormalised; near a
+    // zero of a field (a stagnation point) their low part can exceed the high part, and the
+    // square of such a pair, which drops lo^2, can come out negative.  So they are renormalised
+    // first (then |lo| <= ulp(hi) / 2 and every square is >= 0), as are the velocity components
+    // before the speed is formed; the speed's squares are renormalised too, so their high parts
+    // are the FP32 roundings the screening estimate assumes, and the exact speed is taken in FP64
+    // from the double-float squares.
     const double csd = phys[inst].cs;
-    const cdf cs2 = cdf_bc(dfr_from_double(csd * csd));
+    const dfr cs2 = dfr_from_double(csd * csd);
     for (int q = threadIdx.x; q < PAIRS * N; q += nthr) {
       const int p = q / N, j = q - p * N;
       C *b = sm + p * 12 * P + sm_idx<C>(j);
-      const cdf rho = cdf_norm(b[0]);
-      const cdf mx = cdf_norm(b[P]), my = cdf_norm(b[2 * P]), mz = cdf_norm(b[3 * P]);
-      const cdf bx = cdf_norm(b[4 * P]), by = cdf_norm(b[5 * P]), bz = cdf_norm(b[6 * P]);
+      dfr v[2][7];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        const C c = b[f * P];
+        v[0][f] = dfr_norm(c.re);
+        v[1][f] = dfr_norm(c.im);
+      }
       if (bgrid != nullptr) {
         constexpr size_t N3 = NN * N;
         double *g = bgrid + (size_t)inst * 3 * N3 + (row0 + 2 * p) * N + j;
-        const cdf bb[3] = {bx, by, bz};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          g[c * N3] = dfr_to_double(cdf_x(bb[c]));
-          g[c * N3 + N] = dfr_to_double(cdf_y(bb[c]));
+          g[c * N3] = dfr_to_double(v[0][4 + c]);
+          g[c * N3 + N] = dfr_to_double(v[1][4 + c]);
         }
       }
-      const cdf ir = cdf_rcp(rho);
-      const cdf ux = mx * ir, uy = my * ir, uz = mz * ir;
-      const cdf bxx = bx * bx, byy = by * by, bzz = bz * bz;
-      const cdf b2 = bxx + byy + bzz;
-      const cdf hb = cdf_scale2(b2, 0.5f);
-      b[0 * P] = mx * ux + hb - bxx;   // T_xx
-      b[1 * P] = my * uy + hb - byy;   // T_yy
-      b[2 * P] = mz * uz + hb - bzz;   // T_zz
-      b[3 * P] = mx * uy - bx * by;    // T_xy
-      b[4 * P] = mx * uz - bx * bz;    // T_xz
-      b[5 * P] = my * uz - by * bz;    // T_yz
-      b[6 * P] = uy * bz - uz * by;    // E_x
-      b[7 * P] = uz * bx - ux * bz;    // E_y
-      b[8 * P] = ux * by - uy * bx;    // E_z
-      b[9 * P] = ux;
-      b[10 * P] = uy;
-      b[11 * P] = uz;
-      const cdf nx = cdf_norm(ux), ny = cdf_norm(uy), nz = cdf_norm(uz);
-      const cdf u2 = cdf_norm(nx * nx + ny * ny + nz * nz), c2 = cdf_norm(cs2 + b2 * ir);
-      if (!(sqrtf(u2.hi.x) + sqrtf(c2.hi.x) < screen)) {
-        const double sp = sqrt(dfr_to_double(cdf_x(u2))) + sqrt(dfr_to_double(cdf_x(c2)));
-        smax = (sp != sp || sp > smax) ? sp : smax;  // keeps a NaN once seen
-      }
-      if (!(sqrtf(u2.hi.y) + sqrtf(c2.hi.y) < screen)) {
-        const double sp = sqrt(dfr_to_double(cdf_y(u2))) + sqrt(dfr_to_double(cdf_y(c2)));
-        smax = (sp != sp || sp > smax) ? sp : smax;
+      dfr *bd = reinterpret_cast<dfr *>(b);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const dfr rho = v[h][0];
+        const dfr mx = v[h][1], my = v[h][2], mz = v[h][3];
+        const dfr bx = v[h][4], by = v[h][5], bz = v[h][6];
+        const dfr ir = dfr_rcp(rho);
+        const dfr ux = mx * ir, uy = my * ir, uz = mz * ir;
+        const dfr bxx = bx * bx, byy = by * by, bzz = bz * bz;
+        const dfr b2 = bxx + byy + bzz;
+        const dfr hb = dfr_scale2(b2, 0.5f);
+        bd[2 * 0 * P + h] = mx * ux + hb - bxx;   // T_xx
+        bd[2 * 1 * P + h] = my * uy + hb - byy;   // T_yy
+        bd[2 * 2 * P + h] = mz * uz + hb - bzz;   // T_zz
+        bd[2 * 3 * P + h] = mx * uy - bx * by;    // T_xy
+        bd[2 * 4 * P + h] = mx * uz - bx * bz;    // T_xz
+        bd[2 * 5 * P + h] = my * uz - by * bz;    // T_yz
+        bd[2 * 6 * P + h] = uy * bz - uz * by;    // E_x
+        bd[2 * 7 * P + h] = uz * bx - ux * bz;    // E_y
+        bd[2 * 8 * P + h] = ux * by - uy * bx;    // E_z
+        bd[2 * 9 * P + h] = ux;
+        bd[2 * 10 * P + h] = uy;
+        bd[2 * 11 * P + h] = uz;
+        const dfr nx = dfr_norm(ux), ny = dfr_norm(uy), nz = dfr_norm(uz);
+        const dfr u2 = dfr_norm(nx * nx + ny * ny + nz * nz), c2 = dfr_norm(cs2 + b2 * ir);
+        if (!(sqrtf(u2.hi) + sqrtf(c2.hi) < screen)) {
+          const double s = sqrt(dfr_to_double(u2)) + sqrt(dfr_to_double(c2));
+          smax = (s != s || s > smax) ? s : smax;  // keeps a NaN once seen
+        }
       }
     }
   } else {
@@ -276,8 +280,8 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
     const C *pen = sm + (p * 12 + f) * P;
     const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
     C *dst = out + ((size_t)(inst * 12 + f) * NN + row0 + 2 * p) * NX;
-    dst[k] = c_store(split0(z, zc));
-    dst[NX + k] = c_store(split1(z, zc));
+    dst[k] = c_store(C{z.re + zc.re, z.im - zc.im});
+    dst[NX + k] = c_store(C{z.im + zc.im, zc.re - z.re});
   }
 
   const SM m = block_nan_max(smax, reinterpret_cast<SM *>(red));
@@ -625,9 +629,8 @@ __global__ void __launch_bounds__(kMaxThreads) diag_x_kernel(const cplx64 *__res
 namespace {
 
 template <int N, typename C>
-cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d,
-                   const typename twiddle_of<C>::type *tw, cudaStream_t s, int *err, typename grid_of<C>::type *bgrid,
-                   uint32_t wait_polls) {
+cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
+                   cudaStream_t s, int *err, typename grid_of<C>::type *bgrid, uint32_t wait_polls) {
   constexpr int PAIRS = pairs_for(N);
   if constexpr (PAIRS == 1 && sizeof(C) == 8) {
     if (bgrid != nullptr) err = nullptr;  // the pipelined variant does not write the grid field
@@ -742,7 +745,7 @@ cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, un
 }
 
 cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
-                          const cdftw *tw, cudaStream_t s, int *, double *bgrid, uint32_t) {
+                          const cdf *tw, cudaStream_t s, int *, double *bgrid, uint32_t) {
   MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, nullptr, bgrid, kWaitPolls)));
 }
 

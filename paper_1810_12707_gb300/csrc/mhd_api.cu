@@ -40,7 +40,7 @@ struct mhd_ctx {
   int precision = MHD_FP64;
   cplx64 *S = nullptr, *H = nullptr, *W1 = nullptr, *W2 = nullptr, *tw = nullptr;
   cplx32 *tw32 = nullptr;
-  mhd::cdftw *twdf = nullptr;  // double-float mode: W_N^m as double-float pairs
+  cdf *twdf = nullptr;    // double-float mode: W_N^m as double-float values
   cplx64 *S64 = nullptr;  // mixed and double-float modes: FP64 copy of one instance's state for set/get/diagnostics
   int integrator = MHD_AB2;
   void *Y = nullptr;      // stage state of RK4 / predictor-corrector ([b][7][spec], working precision)
@@ -159,7 +159,7 @@ Sizes sizes_for(const mhd::Dims &d, int precision) {
 size_t footprint(const mhd::Dims &d, int precision) {
   const Sizes s = sizes_for(d, precision);
   return (2 * s.S + s.W1 + s.W2) * sizeof(cplx64) + mhd::fp64_twiddle_size(d.n) + d.n * sizeof(cplx32) +
-         (precision == MHD_FP64_DF ? d.n * sizeof(mhd::cdftw) : 0) +
+         (precision == MHD_FP64_DF ? d.n * sizeof(cdf) : 0) +
          s.part * sizeof(double) +
          (precision == MHD_FP64 ? 0 : 7 * d.spec * sizeof(cplx64)) +
          d.batch * (sizeof(mhd::TimeState) + sizeof(mhd::StepCoef) + sizeof(mhd::PhysDev)) +
@@ -344,8 +344,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->tw = (cplx64 *)dalloc(c, mhd::fp64_twiddle_size(c->d.n))) != nullptr;
   ok = ok && (c->tw32 = (cplx32 *)dalloc(c, (size_t)c->d.n * sizeof(cplx32))) != nullptr;
   if (c->precision != MHD_FP64) ok = ok && (c->S64 = (cplx64 *)dalloc(c, 7 * c->d.spec * sizeof(cplx64))) != nullptr;
-  if (c->precision == MHD_FP64_DF)
-    ok = ok && (c->twdf = (mhd::cdftw *)dalloc(c, (size_t)c->d.n * sizeof(mhd::cdftw))) != nullptr;
+  if (c->precision == MHD_FP64_DF) ok = ok && (c->twdf = (cdf *)dalloc(c, (size_t)c->d.n * sizeof(cdf))) != nullptr;
   if (c->integrator != MHD_AB2)
     ok = ok && (c->Y = dalloc(c, s.S * (c->precision == MHD_FP32_MIXED ? sizeof(cplx32) : sizeof(cplx64)))) != nullptr;
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
@@ -367,14 +366,13 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   const std::vector<unsigned char> w64 = mhd::fp64_twiddle_bytes(c->d.n);
   std::vector<cplx32> w32(w.size());
   for (size_t i = 0; i < w.size(); ++i) w32[i] = cplx32{(float)w[i].re, (float)w[i].im};
-  std::vector<mhd::cdftw> wdf(w.size());  // (Re W, Re W) and (-Im W, Im W) in double-float
-  for (size_t i = 0; i < w.size(); ++i)
-    wdf[i] = mhd::cdftw{mhd::cdf_const(w[i].re, w[i].re), mhd::cdf_const(-w[i].im, w[i].im)};
+  std::vector<cdf> wdf(w.size());
+  for (size_t i = 0; i < w.size(); ++i) wdf[i] = cdf{mhd::dfr_const(w[i].re), mhd::dfr_const(w[i].im)};
   cudaError_t e = cudaMemcpyAsync(c->phys, pd.data(), pd.size() * sizeof(mhd::PhysDev), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw, w64.data(), w64.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw32, w32.data(), w32.size() * sizeof(cplx32), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && c->twdf)
-    e = cudaMemcpyAsync(c->twdf, wdf.data(), wdf.size() * sizeof(mhd::cdftw), cudaMemcpyHostToDevice, c->stream);
+    e = cudaMemcpyAsync(c->twdf, wdf.data(), wdf.size() * sizeof(cdf), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, s.S * sizeof(cplx64), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
@@ -623,8 +621,8 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 // `bgrid` (nullable) receives the grid magnetic field for the tracers.
 template <typename CF, typename CS>
 static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, const CS *S, const mhd::PhysDev *phys,
-                                 mhd::TimeState *ts, mhd::StepCoef *coef, bool advance,
-                                 const typename mhd::twiddle_of<CF>::type *tw, typename mhd::grid_of<CF>::type *bgrid) {
+                                 mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw,
+                                 typename mhd::grid_of<CF>::type *bgrid) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);

@@ -88,20 +88,6 @@ struct grid_of<cdf> {
   using type = double;
 };
 
-// Twiddle of the double-float passes: W = wr + i wi stored as the pairs (Re W, Re W) and
-// (-Im W, Im W), so that a W = a (Re W) + swap(a) (-Im W, Im W) is two packed products and one sum.
-struct alignas(16) cdftw {
-  cdf wr, wi;
-};
-template <typename C>
-struct twiddle_of {
-  using type = C;
-};
-template <>
-struct twiddle_of<cdf> {
-  using type = cdftw;
-};
-
 struct Dims {
   int n;      // grid points per axis
   int k;      // K = floor((n-1)/3)
@@ -156,9 +142,9 @@ cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, 
                                double scale, const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
 // Double-float passes (MHD_FP64_DF): data, twiddles (W_N^m as hi + lo pairs) and arithmetic in
 // double-float, radix 8; `scale` must be a power of two.
-cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdftw *tw,
-                               cudaStream_t s, int tile = 0, int vpt = 0);
-cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdftw *tw,
+cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
+                               int tile = 0, int vpt = 0);
+cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
                                cudaStream_t s, int tile = 0, int vpt = 0);
 int col_max_tile_df(int n, int dir);
 
@@ -180,7 +166,7 @@ cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, un
 // Double-float flux pass (MHD_FP64_DF): products in double-float, exact FP64 CFL maximum as in
 // the FP64 pass, grid magnetic field for the tracers in FP64.
 cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
-                          const cdftw *tw, cudaStream_t s, int *err = nullptr, double *bgrid = nullptr,
+                          const cdf *tw, cudaStream_t s, int *err = nullptr, double *bgrid = nullptr,
                           uint32_t wait_polls = kWaitPolls);
 int flux_x_blocks_per_instance(int n);
 

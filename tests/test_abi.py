@@ -43,7 +43,7 @@ def test_footprint_is_pure_host_arithmetic():
     # and the FP64 copy of one instance's state
     k = (256 - 1) // 3
     spec = (2 * k + 1) ** 2 * (k + 1)
-    assert mhd.mhd_footprint_bytes(256, 2, 1) == f256 + 256 * 32 + 7 * spec * 16
+    assert mhd.mhd_footprint_bytes(256, 2, 1) == f256 + 256 * 16 + 7 * spec * 16
     assert mhd.mhd_footprint_bytes(1024, 0, 1) < 200e9     # the largest grid fits in HBM
 
 
