@@ -1,16 +1,25 @@
-"""Serving many independent MHD runs with continuous batching.
+"""Serving many independent MHD runs with continuous batching, admitted by free device memory.
 
 Requests (grid size N, initial condition, nu, eta, Mach, step budget) arrive as a Poisson stream.
-Each grid size has one `mhd_pool` (C ABI) whose slots hold device-resident runs; the number of
-slots per size is set once from the free device memory and the request mix (admission by free
-HBM).  A scheduler round admits every arrived request that has a free slot (H2D of its initial
-state), advances every pool by k steps -- pools of different sizes on their own CUDA streams, so
-their work overlaps on the device -- and retires the runs that reached their budget (D2H of the
-final state).  Runs never interact, so a run's result is bitwise the same alone and in the mix.
+Runs of one grid size are batched in "slabs": fixed-capacity `mhd_pool`s (C ABI) whose slots hold
+device-resident runs stepped together in one launch per kernel.  Slabs are not planned ahead:
 
-Reported: per-step latency (round wall time / k, one sample per live run and round), per-run
-latency (retirement time - arrival time), p50 and p99 of both, and aggregate throughput in
-grid-point-steps/s.
+  * admission: a waiting request goes to an idle slab of its size with a free slot; if there is
+    none, a new slab is created when the device's free memory at that moment (the driver's free
+    memory plus what PyTorch's caching allocator holds unused, less a reserve) covers its
+    footprint (mhd_footprint_bytes), with as many slots as fit, up to a per-size cap;
+  * retirement: a run that has reached its step budget is copied out (D2H) and its slot freed; a
+    slab with no live run left is destroyed at once, so the memory a retired 32^3 run frees can
+    admit a waiting 256^3 run;
+  * each slab advances k steps at a time on its own CUDA stream and is polled through its own
+    events, so slabs of different sizes overlap on the device and a run's per-step latency is the
+    device time of its own slab's steps (event to event, divided by k), not a global round's.
+
+Runs never interact, so a run's result is bitwise the same alone and in the mix.
+
+Reported: per-step latency (one sample per live run and slab batch), per-run latency
+(retirement time - arrival time), queueing time, p50 and p99 of each overall and per grid size,
+and aggregate throughput in grid-point-steps/s.
 """
 from __future__ import annotations
 
@@ -25,6 +34,8 @@ from . import inputs, mhd
 SIZES = (32, 64, 128, 256)
 WEIGHTS = (0.4, 0.3, 0.2, 0.1)
 IC_SEEDS = 4  # initial states per (N, kind); requests pick one, the host caches them
+# most slots one slab of a size gets (larger N: fewer instances already fill the device)
+SLAB_CAP = {16: 64, 32: 64, 64: 32, 128: 8, 256: 4, 512: 1, 1024: 1}
 
 
 @dataclass
@@ -79,34 +90,18 @@ class ICCache:
         return self._c[key]
 
 
-def plan_slots(free_bytes: float, precision: int = mhd.MHD_FP32_MIXED, sizes=SIZES, weights=WEIGHTS,
-               fraction: float = 0.8, max_slots: int = 64) -> dict:
-    """Slots per grid size, at least one each, total footprint (mhd_footprint_bytes of every pool)
-    within `fraction` of the free device memory.  Every live run advances the same k steps per
-    scheduler round, so by Little's law the runs of size N in flight are proportional to that
-    size's arrival share: slots are given in proportion to the request weights."""
-    share = np.array(weights, dtype=np.float64)
-    share /= share.sum()
-    budget = free_bytes * fraction
-    slots = {n: 1 for n in sizes}
-    used = sum(mhd.mhd_footprint_bytes(n, precision, 1) for n in sizes)
-    # grow the size whose slots are furthest below its work share, while memory lasts
-    while True:
-        total = sum(slots.values())
-        best = None
-        for i, n in enumerate(sizes):
-            if slots[n] >= max_slots:
-                continue
-            extra = mhd.mhd_footprint_bytes(n, precision, slots[n] + 1) - mhd.mhd_footprint_bytes(n, precision, slots[n])
-            if used + extra > budget:
-                continue
-            key = (share[i] * (total + 1) - slots[n], n, extra)
-            if best is None or key > best:
-                best = key
-        if best is None:
-            return slots
-        slots[best[1]] += 1
-        used += best[2]
+def slab_capacity(n: int, precision: int, available_bytes: float, cap: int | None = None) -> int:
+    """Slots of a new slab of size n: the most, up to `cap` (SLAB_CAP[n] by default), whose
+    footprint fits in `available_bytes`; 0 if not even one slot fits."""
+    cap = SLAB_CAP.get(n, 1) if cap is None else cap
+    c = cap
+    while c > 0 and mhd.mhd_footprint_bytes(n, precision, c) > available_bytes:
+        c -= 1
+    return c
+
+
+def pct(a, q):
+    return float(np.percentile(a, q)) if len(a) else None
 
 
 @dataclass
@@ -118,94 +113,215 @@ class ServeStats:
     run_latency_s: list = field(default_factory=list)
     queue_s: list = field(default_factory=list)
     outputs: dict = field(default_factory=dict)
+    by_size: dict = field(default_factory=dict)  # n -> {"step_ms": [...], "run_s": [...]}
+    admitted_at: dict = field(default_factory=dict)  # request id -> seconds from the start
+    retired_at: dict = field(default_factory=dict)
+    slabs_created: int = 0
+    peak_bytes: float = 0.0
 
     def summary(self) -> dict:
-        pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-        return {"completed": self.completed, "wall_s": self.wall,
-                "throughput": self.work / self.wall if self.wall > 0 else 0.0,
-                "step_latency_ms_p50": pct(self.step_latency_ms, 50), "step_latency_ms_p99": pct(self.step_latency_ms, 99),
-                "run_latency_s_p50": pct(self.run_latency_s, 50), "run_latency_s_p99": pct(self.run_latency_s, 99),
-                "queue_s_p50": pct(self.queue_s, 50), "queue_s_p99": pct(self.queue_s, 99)}
+        out = {"completed": self.completed, "wall_s": self.wall,
+               "throughput": self.work / self.wall if self.wall > 0 else 0.0,
+               "step_latency_ms_p50": pct(self.step_latency_ms, 50), "step_latency_ms_p99": pct(self.step_latency_ms, 99),
+               "run_latency_s_p50": pct(self.run_latency_s, 50), "run_latency_s_p99": pct(self.run_latency_s, 99),
+               "queue_s_p50": pct(self.queue_s, 50), "queue_s_p99": pct(self.queue_s, 99)}
+        if self.by_size:
+            out["per_size"] = {str(n): {"runs": len(v["run_s"]), "step_latency_ms_p50": pct(v["step_ms"], 50),
+                                        "step_latency_ms_p99": pct(v["step_ms"], 99),
+                                        "run_latency_s_p50": pct(v["run_s"], 50), "run_latency_s_p99": pct(v["run_s"], 99)}
+                               for n, v in sorted(self.by_size.items())}
+            out["slabs_created"] = self.slabs_created
+            out["peak_slab_bytes"] = self.peak_bytes
+        return out
+
+
+class Slab:
+    """One pool of a grid size on a stream of its own."""
+
+    def __init__(self, torch, n: int, capacity: int, precision: int):
+        self.n, self.capacity = n, capacity
+        self.stream = torch.cuda.Stream()
+        with torch.cuda.stream(self.stream):
+            self.pool = mhd.mhd_pool_create(n, capacity, precision=precision)
+        self.footprint = mhd.mhd_footprint_bytes(n, precision, capacity)
+        self.live = {}  # slot -> request
+        self.busy = False
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev1 = torch.cuda.Event(enable_timing=True)
+
+    def close(self):
+        mhd.mhd_pool_destroy(self.pool)
 
 
 class Server:
-    def __init__(self, slots: dict, precision: int = mhd.MHD_FP32_MIXED, k: int = 10, cache: ICCache | None = None):
+    """Continuous-batching scheduler over slabs (see the module docstring).
+
+    `memory_limit` (bytes, optional) caps the slabs' total footprint below what the device has
+    free, so that admission by memory can be exercised at any device size; `reserve` bytes of
+    device memory are always left free."""
+
+    def __init__(self, precision: int = mhd.MHD_FP32_MIXED, k: int = 10, cache: ICCache | None = None,
+                 memory_limit: float | None = None, reserve: float = 2e9, slab_cap: dict | None = None):
         import torch
         self.torch = torch
         self.k = k
         self.precision = precision
         self.cache = cache or ICCache()
-        self.pools, self.streams = {}, {}
-        for n, s in slots.items():
-            st = torch.cuda.Stream()
-            with torch.cuda.stream(st):
-                self.pools[n] = mhd.mhd_pool_create(n, s, precision=precision)
-            self.streams[n] = st
-        self.slots = dict(slots)
+        self.memory_limit = memory_limit
+        self.reserve = reserve
+        self.slab_cap = dict(SLAB_CAP)
+        self.slab_cap.update(slab_cap or {})
+        self.slabs = []
 
     def close(self):
-        for p in self.pools.values():
-            mhd.mhd_pool_destroy(p)
-        self.pools.clear()
+        for s in self.slabs:
+            s.close()
+        self.slabs.clear()
 
-    def _admit(self, req: Request) -> int | None:
+    def used_bytes(self) -> float:
+        return float(sum(s.footprint for s in self.slabs))
+
+    def available_bytes(self) -> float:
+        t = self.torch
+        free, _ = t.cuda.mem_get_info()
+        cached = t.cuda.memory_reserved() - t.cuda.memory_allocated()
+        avail = free + cached - self.reserve
+        if self.memory_limit is not None:
+            avail = min(avail, self.memory_limit - self.used_bytes())
+        return avail
+
+    def _admit_into(self, slab: Slab, req: Request) -> bool:
         rho, u, b = self.cache.get(req)
-        pool = self.pools[req.n]
-        with self.torch.cuda.stream(self.streams[req.n]):
-            return mhd.mhd_pool_admit(pool, (req.nu, req.eta, 1.0 / req.mach), rho, u, b, req.nsteps)
+        with self.torch.cuda.stream(slab.stream):
+            slot = mhd.mhd_pool_admit(slab.pool, (req.nu, req.eta, 1.0 / req.mach), rho, u, b, req.nsteps)
+        if slot is None:
+            return False
+        slab.live[slot] = req
+        return True
 
-    def run(self, requests: list, keep_outputs=()) -> ServeStats:
+    def _place(self, req: Request, stats: ServeStats) -> str:
+        """Admit `req` into an idle slab of its size with a free slot ("admitted"); if a slab of
+        its size has a free slot but is stepping, wait for it, at most one batch of k steps
+        ("wait"); else open a new slab if the free memory allows, or report "memory"."""
+        room = [s for s in self.slabs if s.n == req.n and len(s.live) < s.capacity]
+        for s in room:
+            if not s.busy:
+                return "admitted" if self._admit_into(s, req) else "wait"
+        if room:
+            return "wait"
+        cap = slab_capacity(req.n, self.precision, self.available_bytes(), self.slab_cap.get(req.n, 1))
+        if cap < 1:
+            return "memory"
+        slab = Slab(self.torch, req.n, cap, self.precision)
+        self.slabs.append(slab)
+        stats.slabs_created += 1
+        stats.peak_bytes = max(stats.peak_bytes, self.used_bytes())
+        return "admitted" if self._admit_into(slab, req) else "wait"
+
+    def _issue(self, slab: Slab):
+        with self.torch.cuda.stream(slab.stream):
+            slab.ev0.record(slab.stream)
+            mhd.mhd_pool_step(slab.pool, self.k)
+            slab.ev1.record(slab.stream)
+        slab.busy = True
+
+    def _finish(self, slab: Slab, stats: ServeStats, t0: float, keep: set, stop: bool) -> float:
+        """Collect a completed batch of steps; returns the grid-point-steps it advanced."""
+        step_ms = slab.ev0.elapsed_time(slab.ev1) / self.k
+        bucket = stats.by_size.setdefault(slab.n, {"step_ms": [], "run_s": []})
+        stats.step_latency_ms += [step_ms] * len(slab.live)
+        bucket["step_ms"] += [step_ms] * len(slab.live)
+        steps, _, fin = mhd.mhd_pool_progress(slab.pool)
+        advanced = 0.0
+        for s in list(slab.live):
+            req = slab.live[s]
+            done_before = getattr(req, "_counted", 0)
+            advanced += float(req.n) ** 3 * (int(steps[s]) - done_before)
+            req._counted = int(steps[s])
+            if fin[s] or stop:
+                out = mhd.mhd_pool_retire(slab.pool, s, copy_out=(req.rid in keep) and fin[s])
+                slab.live.pop(s)
+                if out is not None:
+                    stats.outputs[req.rid] = out
+                if fin[s]:
+                    t = time.perf_counter() - t0
+                    stats.completed += 1
+                    stats.work += req.work
+                    stats.run_latency_s.append(t - req.arrival)
+                    bucket["run_s"].append(t - req.arrival)
+                    stats.retired_at[req.rid] = t
+        slab.busy = False
+        return advanced
+
+    def run(self, requests: list, keep_outputs=(), stop_after_s: float | None = None) -> ServeStats:
         """Serve `requests` in real time (arrival times relative to the start).  Outputs of the
-        request ids in `keep_outputs` are returned in stats.outputs."""
+        request ids in `keep_outputs` are returned in stats.outputs.  With `stop_after_s`, no
+        request is admitted after that many seconds and the runs in flight are dropped once their
+        current steps complete; stats.work then counts the steps actually taken (a closed-loop
+        capacity measurement)."""
         keep = set(keep_outputs)
         stats = ServeStats()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
-        live = {n: {} for n in self.pools}  # slot -> request
-        admitted_at = {}
+        for r in requests:
+            r._counted = 0
         t0 = time.perf_counter()
-        while pending or waiting or any(live[n] for n in live):
+        steps_work = 0.0
+        while True:
             now = time.perf_counter() - t0
+            stop = stop_after_s is not None and now >= stop_after_s
+            # completed batches: progress, retirements, empty slabs destroyed
+            for slab in list(self.slabs):
+                if slab.busy and slab.ev1.query():
+                    steps_work += self._finish(slab, stats, t0, keep, stop)
+                    if not slab.live:
+                        slab.close()
+                        self.slabs.remove(slab)
+            if stop:
+                pending.clear()
+                waiting.clear()
+                if not any(s.busy for s in self.slabs):
+                    for slab in list(self.slabs):
+                        for s in list(slab.live):
+                            mhd.mhd_pool_retire(slab.pool, s, copy_out=False)
+                            slab.live.pop(s)
+                        slab.close()
+                        self.slabs.remove(slab)
+                    break
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            # admission in arrival order.  A request whose slab is stepping waits for it while
+            # later ones go ahead; a request that no free memory can take stops admission for
+            # the round, so that the slabs of smaller runs drain and free the memory it needs
+            # (a large run is not starved by a stream of small ones)
             still = collections.deque()
             while waiting:
                 req = waiting.popleft()
-                slot = self._admit(req) if len(live[req.n]) < self.slots[req.n] else None
-                if slot is None:
-                    still.append(req)
-                else:
-                    live[req.n][slot] = req
-                    admitted_at[req.rid] = time.perf_counter() - t0
+                verdict = self._place(req, stats)
+                if verdict == "admitted":
+                    stats.admitted_at[req.rid] = time.perf_counter() - t0
+                    stats.queue_s.append(stats.admitted_at[req.rid] - req.arrival)
+                    continue
+                still.append(req)
+                if verdict == "memory":
+                    still.extend(waiting)
+                    waiting.clear()
             waiting = still
-            if not any(live[n] for n in live):
+            for slab in self.slabs:
+                if not slab.busy and slab.live and not stop:
+                    self._issue(slab)
+            if not pending and not waiting and not self.slabs:
+                break
+            if not any(s.busy for s in self.slabs):
                 if pending:
                     time.sleep(max(0.0, min(0.002, pending[0].arrival - (time.perf_counter() - t0))))
-                continue
-            tr = time.perf_counter()
-            for n, pool in self.pools.items():
-                if live[n]:
-                    with self.torch.cuda.stream(self.streams[n]):
-                        mhd.mhd_pool_step(pool, self.k)
-            done = []
-            for n, pool in self.pools.items():
-                if live[n]:
-                    steps, status, fin = mhd.mhd_pool_progress(pool)
-                    done += [(n, s) for s in list(live[n]) if fin[s]]
-            round_ms = (time.perf_counter() - tr) * 1e3
-            nlive = sum(len(live[n]) for n in live)
-            stats.step_latency_ms += [round_ms / self.k] * nlive
-            for n, s in done:
-                req = live[n].pop(s)
-                out = mhd.mhd_pool_retire(self.pools[n], s, copy_out=req.rid in keep)
-                if out is not None:
-                    stats.outputs[req.rid] = out
-                t = time.perf_counter() - t0
-                stats.completed += 1
-                stats.work += req.work
-                stats.run_latency_s.append(t - req.arrival)
-                stats.queue_s.append(admitted_at[req.rid] - req.arrival)
+                elif waiting:
+                    raise RuntimeError("a waiting request fits no slab even with the device idle")
+            else:
+                time.sleep(0.0002)
         stats.wall = time.perf_counter() - t0
+        if stop_after_s is not None:
+            stats.work = steps_work
         return stats
 
 
@@ -226,33 +342,9 @@ def run_alone(req: Request, precision: int = mhd.MHD_FP32_MIXED, cache: ICCache 
 
 
 def measure_capacity(server: Server, requests: list, duration_s: float = 10.0) -> float:
-    """Closed-loop throughput (grid-point-steps/s) with every slot kept busy by requests admitted
-    back to back; the work counted is the steps the runs actually took."""
-    queue = {n: collections.deque(r for r in requests if r.n == n) for n in server.pools}
-    live = {n: {} for n in server.pools}   # slot -> steps already counted
-    work, t0 = 0.0, time.perf_counter()
-    while time.perf_counter() - t0 < duration_s:
-        for n in server.pools:
-            while len(live[n]) < server.slots[n] and queue[n]:
-                r = queue[n].popleft()
-                live[n][server._admit(r)] = 0
-                queue[n].append(r)
-        for n, pool in server.pools.items():
-            if live[n]:
-                with server.torch.cuda.stream(server.streams[n]):
-                    mhd.mhd_pool_step(pool, server.k)
-        for n, pool in server.pools.items():
-            if not live[n]:
-                continue
-            steps, _, fin = mhd.mhd_pool_progress(pool)
-            for s in list(live[n]):
-                work += float(n) ** 3 * (steps[s] - live[n][s])
-                live[n][s] = steps[s]
-                if fin[s]:
-                    live[n].pop(s)
-                    mhd.mhd_pool_retire(pool, s, copy_out=False)
-    wall = time.perf_counter() - t0
-    for n, pool in server.pools.items():
-        for s in list(live[n]):
-            mhd.mhd_pool_retire(pool, s, copy_out=False)
-    return work / wall
+    """Closed-loop throughput (grid-point-steps/s): every request available at once, admission
+    as fast as memory and slabs allow, for `duration_s`; the work counted is the steps the runs
+    actually took."""
+    closed = [Request(r.rid, 0.0, r.n, r.ic, r.seed, r.nu, r.eta, r.mach, r.nsteps) for r in requests]
+    stats = server.run(closed, stop_after_s=duration_s)
+    return stats.work / stats.wall

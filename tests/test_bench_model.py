@@ -56,3 +56,21 @@ def test_traffic_is_dropped_when_sources_change(monkeypatch):
     assert nbytes is None and "changed" in why
     nbytes, why = bench.measured_traffic("flux_x", 48, 1, "fp64")
     assert nbytes is None and "no capture" in why
+
+
+def test_double_float_model():
+    """The double-float mode moves FP64-sized values, so its bytes are the FP64 model's; its
+    operation count per transform follows the radix plan: N = 8 one untwiddled radix-8 DFT (432
+    FP32 operations), N = 16 two of them and eight twiddled radix-2 butterflies (64 each), N = 32
+    four and eight twiddled radix-4 butterflies (224 each), N = 64 eight untwiddled and eight
+    twiddled radix-8 DFTs (656 each)."""
+    assert bench.dfloat_fft_ops(8) == 432
+    assert bench.dfloat_fft_ops(16) == 2 * 432 + 8 * 64
+    assert bench.dfloat_fft_ops(32) == 4 * 432 + 8 * 224
+    assert bench.dfloat_fft_ops(64) == 8 * 432 + 8 * 656
+    assert bench.dfloat_fft_ops(512) == 64 * 432 + 2 * 64 * 656
+    fp64, df = bench.kernel_model(N, 1, "fp64"), bench.kernel_model(N, 1, "fp64df")
+    for kernel in fp64:
+        assert df[kernel][0] == fp64[kernel][0]
+    ops = bench.dfloat_ops(N)
+    assert df["inverse_y"][1] == ops["inverse_y"] == 7 * N * NX * (bench.dfloat_fft_ops(N) + 6 * N)

@@ -54,7 +54,7 @@ def test_pool_budgets_compaction_and_alone_vs_mix(lib, precision):
 def test_serving_loop_small(lib):
     from paper_1810_12707_gb300 import serving
     reqs = serving.make_requests(12, rate=200.0, seed=5, sizes=(16, 32), weights=(0.5, 0.5), steps=(20, 60))
-    srv = serving.Server({16: 3, 32: 2}, k=5)
+    srv = serving.Server(k=5, slab_cap={16: 3, 32: 2})
     keep = [r.rid for r in reqs[:4]]
     stats = srv.run(reqs, keep_outputs=keep)
     srv.close()
@@ -68,9 +68,30 @@ def test_serving_loop_small(lib):
             assert np.array_equal(g, e)
 
 
-def test_plan_slots_respects_memory(lib):
+def test_largest_run_is_admitted_once_smaller_runs_free_the_memory(lib):
+    """No slot is set aside for the largest grid: with a memory budget that holds either the
+    slab of small runs or one large run but not both, the large request (arriving while the small
+    runs are on the device) waits, is admitted once the small runs have retired and their slab
+    has been destroyed, and completes; later small requests do not overtake it."""
     from paper_1810_12707_gb300 import serving
-    slots = serving.plan_slots(40e9)
-    used = sum(lib.mhd_footprint_bytes(n, 1, s) for n, s in slots.items())
-    assert used <= 0.8 * 40e9 * 1.01 and all(s >= 1 for s in slots.values())
-    assert slots[32] >= slots[64] >= slots[128] >= slots[256]
+    prec = lib.MHD_FP32_MIXED
+    small, big = 16, 64
+    cap = 4
+    limit = max(lib.mhd_footprint_bytes(small, prec, cap), lib.mhd_footprint_bytes(big, prec, 1)) * 1.05
+    assert lib.mhd_footprint_bytes(small, prec, cap) + lib.mhd_footprint_bytes(big, prec, 1) > limit
+    mk = lambda rid, t, n, steps: serving.Request(rid, t, n, "ot", rid % serving.IC_SEEDS, 5e-3, 5e-3, 0.2, steps)
+    reqs = [mk(i, 0.0, small, 30) for i in range(4)] + [mk(4, 0.001, big, 20)] + \
+           [mk(5 + i, 0.002, small, 10) for i in range(3)]
+    srv = serving.Server(precision=prec, k=5, memory_limit=limit, slab_cap={small: cap, big: 1})
+    stats = srv.run(reqs, keep_outputs=[4])
+    srv.close()
+    assert stats.completed == len(reqs)
+    assert stats.peak_bytes <= limit
+    first_small_done = max(stats.retired_at[i] for i in range(4))
+    assert stats.admitted_at[4] >= first_small_done
+    assert all(stats.admitted_at[5 + i] >= stats.admitted_at[4] for i in range(3))
+    alone = serving.run_alone(reqs[4], precision=prec)
+    for g, e in zip(stats.outputs[4], alone):
+        assert np.array_equal(g, e)
+    per = stats.summary()["per_size"]
+    assert set(per) == {str(small), str(big)} and per[str(big)]["runs"] == 1

@@ -1,4 +1,4 @@
-"""Host-side logic of the serving loop, no GPU: the Poisson request stream, slot planning by free
+"""Host-side logic of the serving loop, no GPU: the Poisson request stream, slab sizing by free
 device memory (through the library's host-only footprint arithmetic) and the latency summary."""
 import numpy as np
 import pytest
@@ -33,35 +33,24 @@ def test_request_stream_is_seeded_and_has_the_stated_mix(serving):
     assert a[0].work == float(a[0].n) ** 3 * a[0].nsteps
 
 
-@pytest.mark.parametrize("free_gb", [2, 40, 250])
-def test_slot_plan_fits_memory_and_follows_the_mix(serving, free_gb):
+@pytest.mark.parametrize("free_gb", [0.001, 2, 40, 250])
+def test_slab_capacity_fits_the_free_memory(serving, free_gb):
+    """A new slab takes as many slots as fit in the memory free at that moment (the library's
+    host-only footprint arithmetic), up to the per-size cap; none when one slot does not fit."""
     from paper_1810_12707_gb300 import mhd
     free = free_gb * 1e9
-    slots = serving.plan_slots(free)
-    used = sum(mhd.mhd_footprint_bytes(n, mhd.MHD_FP32_MIXED, s) for n, s in slots.items())
-    assert all(s >= 1 for s in slots.values())
-    assert all(s <= 64 for s in slots.values())
-    ones = sum(mhd.mhd_footprint_bytes(n, mhd.MHD_FP32_MIXED, 1) for n in slots)
-    assert used <= max(0.8 * free, ones)
-    # no size can take one more slot without leaving the budget, unless it is at the cap or
-    # already at or above its share
-    total = sum(slots.values())
-    for n, w in zip(serving.SIZES, serving.WEIGHTS):
-        extra = mhd.mhd_footprint_bytes(n, mhd.MHD_FP32_MIXED, slots[n] + 1) - \
-            mhd.mhd_footprint_bytes(n, mhd.MHD_FP32_MIXED, slots[n])
-        if slots[n] < 64 and slots[n] < w * total:
-            assert used + extra > 0.8 * free, (n, slots)
-    assert slots[32] >= slots[64] >= slots[128] >= slots[256]
-
-
-def test_slot_plan_is_proportional_when_memory_allows(serving):
-    """With memory for every size's cap, each size gets the cap; below it, the slot counts follow
-    the weights 0.4 : 0.3 : 0.2 : 0.1 to within one slot of the largest-remainder split."""
-    big = serving.plan_slots(10e12)
-    assert big == {n: 64 for n in serving.SIZES}
-    small = serving.plan_slots(10e12, max_slots=10 ** 6, sizes=(32, 64), weights=(0.75, 0.25), fraction=1e-3)
-    total = sum(small.values())
-    assert abs(small[32] - 0.75 * total) <= 1 and abs(small[64] - 0.25 * total) <= 1
+    for n in serving.SIZES:
+        for prec in (mhd.MHD_FP32_MIXED, mhd.MHD_FP64, mhd.MHD_FP64_DF):
+            c = serving.slab_capacity(n, prec, free)
+            cap = serving.SLAB_CAP[n]
+            assert 0 <= c <= cap
+            if c > 0:
+                assert mhd.mhd_footprint_bytes(n, prec, c) <= free
+            if c < cap:
+                assert mhd.mhd_footprint_bytes(n, prec, c + 1) > free
+    assert serving.slab_capacity(256, mhd.MHD_FP32_MIXED, 1e6) == 0
+    assert serving.slab_capacity(32, mhd.MHD_FP32_MIXED, 1e12) == serving.SLAB_CAP[32]
+    assert serving.slab_capacity(32, mhd.MHD_FP32_MIXED, 1e12, cap=3) == 3
 
 
 def test_latency_summary(serving):
@@ -74,3 +63,7 @@ def test_latency_summary(serving):
     assert s["run_latency_s_p50"] == 2.0
     empty = serving.ServeStats().summary()
     assert empty["throughput"] == 0.0 and empty["step_latency_ms_p50"] is None
+    st.by_size = {32: {"step_ms": [1.0, 3.0], "run_s": [2.0]}, 256: {"step_ms": [9.0], "run_s": [4.0, 6.0]}}
+    per = st.summary()["per_size"]
+    assert per["32"]["step_latency_ms_p50"] == 2.0 and per["256"]["run_latency_s_p50"] == 5.0
+    assert per["256"]["runs"] == 2
