@@ -77,7 +77,7 @@ def test_largest_run_is_admitted_once_smaller_runs_free_the_memory(lib):
     prec = lib.MHD_FP32_MIXED
     small, big = 16, 64
     cap = 4
-    limit = max(lib.mhd_footprint_bytes(small, prec, cap), lib.mhd_footprint_bytes(big, prec, 1)) * 1.05
+    limit = lib.mhd_footprint_bytes(big, prec, 1) + 0.5 * lib.mhd_footprint_bytes(small, prec, cap)
     assert lib.mhd_footprint_bytes(small, prec, cap) + lib.mhd_footprint_bytes(big, prec, 1) > limit
     mk = lambda rid, t, n, steps: serving.Request(rid, t, n, "ot", rid % serving.IC_SEEDS, 5e-3, 5e-3, 0.2, steps)
     reqs = [mk(i, 0.0, small, 30) for i in range(4)] + [mk(4, 0.001, big, 20)] + \
