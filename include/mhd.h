@@ -269,7 +269,12 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *                          record the failure, wait (up to 4194304 polls each) for the copies it
  *                          still has in flight, and return; mhd_synchronize then reports
  *                          MHD_ETIMEOUT and the context may only be destroyed.  0 gives up at
- *                          once, so that a caller can exercise that path without a fault. */
+ *                          once, so that a caller can exercise that path without a fault.
+ *   MHD_OPT_PERSISTENT     1: the four column passes and the flux pass run as persistent
+ *                          kernels, one grid of resident blocks per pass taking tiles from a work
+ *                          counter (for batches of small grids: no per-block launch cost, no
+ *                          tail); 0 (default): one block per tile.  No block waits on another.
+ *                          Results are identical. */
 enum {
   MHD_OPT_CUDA_GRAPH = 0,
   MHD_OPT_TILE_INV_Z = 1,
@@ -281,7 +286,8 @@ enum {
   MHD_OPT_RADIX_INV_Y = 7,
   MHD_OPT_RADIX_FWD_Y = 8,
   MHD_OPT_RADIX_FWD_Z = 9,
-  MHD_OPT_WAIT_POLLS = 10
+  MHD_OPT_WAIT_POLLS = 10,
+  MHD_OPT_PERSISTENT = 11
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
 

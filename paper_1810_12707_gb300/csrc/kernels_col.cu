@@ -22,11 +22,11 @@ namespace mhd {
 // moves rows l0, l0 + N/VPT, ... of column c, so consecutive threads touch consecutive columns of a
 // row (coalesced) and no index needs a division.
 // VPT: values per thread of the transform (8, or 16 for FP32), so N / VPT threads per column.
+// One tile (TC columns of one slab): work item w = slab * ntiles + tile.
 template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
-__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
-                               int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CC *sm = reinterpret_cast<CC *>(smem_raw);
+__device__ __forceinline__ void col_fft_tile(const CI *__restrict__ in, CO *__restrict__ out, unsigned w, int ntiles,
+                                             int tsh, int cols, typename scale_of<CC>::type scale,
+                                             const CC *__restrict__ tw, CC *sm) {
   constexpr int TPP = tpp_for<N, VPT>();
   constexpr int P = pencil_pitch<CC>(N);
   constexpr int K = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
@@ -34,8 +34,8 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   constexpr int LIN = DIR > 0 ? NK : N;
   constexpr int LOUT = DIR > 0 ? N : NK;
   const int tc = 1 << tsh;
-  const int tile = blockIdx.x % ntiles;
-  const size_t slab = blockIdx.x / ntiles;
+  const int tile = (int)(w % (unsigned)ntiles);
+  const size_t slab = w / (unsigned)ntiles;
   const int c = threadIdx.x & (tc - 1);
   const int l0 = threadIdx.x >> tsh;  // 0 .. TPP-1
   const int col = tile * tc + c;
@@ -79,14 +79,51 @@ __global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, 
   }
 }
 
+template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
+__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
+                               int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  col_fft_tile<N, DIR, CI, CO, CC, VPT>(in, out, blockIdx.x, ntiles, tsh, cols, scale, tw,
+                                        reinterpret_cast<CC *>(smem_raw));
+}
+
+// The same pass as a persistent kernel: a grid of (SMs x resident blocks) takes tiles from the
+// work counter ctr[0] until all `total` are done; ctr[1] counts the blocks that have finished, and
+// the last one resets both for the next launch (every block has taken its last tile by then; no
+// block waits on another).  Each tile's arithmetic is the one col_fft_kernel does.
+template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
+__global__ void col_fft_persistent_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
+                                          int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw,
+                                          unsigned total, unsigned *ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const unsigned w = next;
+    if (w >= total) break;
+    col_fft_tile<N, DIR, CI, CO, CC, VPT>(in, out, w, ntiles, tsh, cols, scale, tw, reinterpret_cast<CC *>(smem_raw));
+    __syncthreads();  // the tile's shared memory and `next` are free again
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+    }
+  }
+}
+
 namespace {
 
 // Columns per block: enough that a tile row is at least 128 bytes and a block at least 128
-// threads, but not more than the columns there are.
-int pick_tc(int tpp, int cols) {
+// threads, but not more than the columns there are; 16-byte values (FP64 and double-float) at most
+// 256 threads a block (the width the autotuner picks for them at N >= 512 on GB300).
+int pick_tc(int tpp, int cols, size_t elem) {
   int tc = 8;
   while (tc * tpp < 128 && tc < 64) tc *= 2;
   while (tc * tpp > 1024) tc /= 2;
+  while (elem >= 16 && tc > 1 && tc * tpp > 256) tc /= 2;
   while (tc > 1 && tc / 2 >= cols) tc /= 2;  // no more than one power of two above `cols`
   return tc;
 }
@@ -110,11 +147,39 @@ int col_max_threads() {
   return cached;
 }
 
+// Resident blocks per SM of a persistent launch (per instantiation and block shape).
+template <auto Fn>
+int resident_blocks(int threads, size_t smem) {
+  static int cached_threads = -1, cached = 1;
+  static size_t cached_smem = 0;
+  if (threads != cached_threads || smem != cached_smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Fn, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cached = per_sm > 0 ? per_sm : 1;
+    cached_threads = threads;
+    cached_smem = smem;
+  }
+  return cached;
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    sms = (cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 1;
+  }
+  return sms;
+}
+
 template <int N, int DIR, typename CI, typename CO, int VPT>
 cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
-                         cudaStream_t s, int tile) {
+                         cudaStream_t s, int tile, unsigned *ctr) {
   constexpr int TPP = tpp_for<N, VPT>();
-  int tc = tile > 0 ? tile : pick_tc(TPP, cols);
+  int tc = tile > 0 ? tile : pick_tc(TPP, cols, sizeof(CO));
   const int max_threads = col_max_threads<N, DIR, CI, CO, VPT>();
   while (tc > 1 && tc * TPP > max_threads) tc /= 2;
   if (tc < 1) tc = 1;
@@ -122,13 +187,25 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
   tc = 1 << tsh;
   const int ntiles = (cols + tc - 1) / tc;
   const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
+  const long long blocks = (long long)nslab * ntiles;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (ctr != nullptr) {
+    constexpr auto kfn = col_fft_persistent_kernel<N, DIR, CI, CO, CO, VPT>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = ensure_smem<kfn>((int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    long long grid = (long long)sm_count() * resident_blocks<kfn>(tc * TPP, smem);
+    if (grid > blocks) grid = blocks;
+    kfn<<<(unsigned)grid, tc * TPP, smem, s>>>(in, out, ntiles, tsh, cols, (typename scale_of<CO>::type)scale, tw,
+                                               (unsigned)blocks, ctr);
+    return cudaGetLastError();
+  }
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO, VPT>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  const long long blocks = (long long)nslab * ntiles;
-  if (blocks <= 0) return cudaSuccess;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   col_fft_kernel<N, DIR, CI, CO, CO, VPT><<<(unsigned)blocks, tc * TPP, smem, s>>>(
       in, out, ntiles, tsh, cols, (typename scale_of<CO>::type)scale, tw);
   return cudaGetLastError();
@@ -138,25 +215,25 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
 // radix 16 for FP32 at N >= 512, where it measured faster).
 template <int N, int DIR, typename CI, typename CO>
 cudaError_t launch_col_n(const CI *in, CO *out, int nslab, int cols, double scale, const CO *tw,
-                         cudaStream_t s, int tile, int vpt) {
+                         cudaStream_t s, int tile, int vpt, unsigned *ctr) {
   if constexpr (sizeof(CO) == 8) {
     if (vpt == 16 || (vpt == 0 && N >= 512))
-      return launch_col_v<N, DIR, CI, CO, 16>(in, out, nslab, cols, scale, tw, s, tile);
+      return launch_col_v<N, DIR, CI, CO, 16>(in, out, nslab, cols, scale, tw, s, tile, ctr);
   }
-  return launch_col_v<N, DIR, CI, CO, 8>(in, out, nslab, cols, scale, tw, s, tile);
+  return launch_col_v<N, DIR, CI, CO, 8>(in, out, nslab, cols, scale, tw, s, tile, ctr);
 }
 
 template <int DIR, typename CI, typename CO>
 cudaError_t launch_col(const CI *in, CO *out, int n, int nslab, int cols, double scale, const CO *tw,
-                       cudaStream_t s, int tile, int vpt) {
+                       cudaStream_t s, int tile, int vpt, unsigned *ctr = nullptr) {
   switch (n) {
-    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
-    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt);
+    case 16: return launch_col_n<16, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 32: return launch_col_n<32, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 64: return launch_col_n<64, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 128: return launch_col_n<128, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 256: return launch_col_n<256, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 512: return launch_col_n<512, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
+    case 1024: return launch_col_n<1024, DIR>(in, out, nslab, cols, scale, tw, s, tile, vpt, ctr);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -210,32 +287,32 @@ int col_max_tile(int n, int dir, bool fp64, bool mixed_in, int vpt) {
 }
 
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s, int tile, int) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
+                               const cplx64 *tw, cudaStream_t s, int tile, int, unsigned *ctr) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8, ctr);
 }
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
                                const cplx32 *tw, cudaStream_t s, int tile) {
   return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
 }
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, vpt);
+                               const cplx32 *tw, cudaStream_t s, int tile, int vpt, unsigned *ctr) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, vpt, ctr);
 }
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s, int tile, int) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile, int, unsigned *ctr) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8, ctr);
 }
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s, int tile, int vpt) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, vpt);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile, int vpt, unsigned *ctr) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, vpt, ctr);
 }
 cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
-                               int tile, int) {
-  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8);
+                               int tile, int, unsigned *ctr) {
+  return launch_col<+1>(in, out, n, nslab, cols, 1.0, tw, s, tile, 8, ctr);
 }
 cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
-                               cudaStream_t s, int tile, int) {
-  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8);
+                               cudaStream_t s, int tile, int, unsigned *ctr) {
+  return launch_col<-1>(in, out, n, nslab, cols, scale, tw, s, tile, 8, ctr);
 }
 
 }  // namespace mhd

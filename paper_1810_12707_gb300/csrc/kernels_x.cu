@@ -83,22 +83,22 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
 // combined in FP64.
 // bgrid (nullable): the grid magnetic field is also written out, [inst][3][N^3] in the data's
 // precision, for the tracer push.
+// One work item w = (instance, block of PAIRS row pairs); `sm` the block's dynamic shared memory,
+// `red` 32 doubles of shared scratch for the block maximum.
 template <int N, typename C>
-__global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>())) flux_x_kernel(const C *__restrict__ in, C *__restrict__ out,
-                              const PhysDev *__restrict__ phys, unsigned long long *__restrict__ smax_bits,
-                              int K, int blocks_per_inst, const C *__restrict__ tw,
-                              typename grid_of<C>::type *__restrict__ bgrid) {
+__device__ __forceinline__ void flux_x_item(const C *__restrict__ in, C *__restrict__ out,
+                                            const PhysDev *__restrict__ phys,
+                                            unsigned long long *__restrict__ smax_bits, int K, int blocks_per_inst,
+                                            const C *__restrict__ tw, typename grid_of<C>::type *__restrict__ bgrid,
+                                            unsigned w, C *sm, double *red) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   using R = typename C::value_type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *sm = reinterpret_cast<C *>(smem_raw);
-  __shared__ double red[32];
   constexpr int P = pencil_pitch<C>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
   constexpr int NX = KT + 1;
-  const int inst = blockIdx.x / blocks_per_inst;
-  const int bl = blockIdx.x - inst * blocks_per_inst;
+  const int inst = (int)(w / (unsigned)blocks_per_inst);
+  const int bl = (int)(w - (unsigned)inst * (unsigned)blocks_per_inst);
   const size_t row0 = (size_t)bl * PAIRS * 2;
   // the launch uses exactly this many threads, so every loop below has a constant trip count
   constexpr int nthr = flux_threads<N, C>();
@@ -286,6 +286,47 @@ __global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>
 
   const SM m = block_nan_max(smax, reinterpret_cast<SM *>(red));
   if (threadIdx.x == 0) atomicMax(smax_bits + inst, max_bits((double)m));
+}
+
+template <int N, typename C>
+__global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>()))
+    flux_x_kernel(const C *__restrict__ in, C *__restrict__ out, const PhysDev *__restrict__ phys,
+                  unsigned long long *__restrict__ smax_bits, int K, int blocks_per_inst, const C *__restrict__ tw,
+                  typename grid_of<C>::type *__restrict__ bgrid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  flux_x_item<N, C>(in, out, phys, smax_bits, K, blocks_per_inst, tw, bgrid, blockIdx.x,
+                    reinterpret_cast<C *>(smem_raw), red);
+}
+
+// The same pass as a persistent kernel (batched small grids): a grid of resident blocks takes
+// work items from ctr[0] until all `total` are done; ctr[1] counts finished blocks and the last
+// one resets both (no block waits on another).  Each item computes what flux_x_kernel computes.
+template <int N, typename C>
+__global__ void __launch_bounds__((flux_threads<N, C>()), (flux_min_blocks<N, C>()))
+    flux_x_persistent_kernel(const C *__restrict__ in, C *__restrict__ out, const PhysDev *__restrict__ phys,
+                             unsigned long long *__restrict__ smax_bits, int K, int blocks_per_inst,
+                             const C *__restrict__ tw, typename grid_of<C>::type *__restrict__ bgrid, unsigned total,
+                             unsigned *ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ unsigned next;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const unsigned w = next;
+    if (w >= total) break;
+    flux_x_item<N, C>(in, out, phys, smax_bits, K, blocks_per_inst, tw, bgrid, w, reinterpret_cast<C *>(smem_raw),
+                      red);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -630,7 +671,7 @@ namespace {
 
 template <int N, typename C>
 cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long *part, const Dims &d, const C *tw,
-                   cudaStream_t s, int *err, typename grid_of<C>::type *bgrid, uint32_t wait_polls) {
+                   cudaStream_t s, int *err, typename grid_of<C>::type *bgrid, uint32_t wait_polls, unsigned *ctr) {
   constexpr int PAIRS = pairs_for(N);
   if constexpr (PAIRS == 1 && sizeof(C) == 8) {
     if (bgrid != nullptr) err = nullptr;  // the pipelined variant does not write the grid field
@@ -662,6 +703,22 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (long long)bpi * d.batch;
+  if (ctr != nullptr) {
+    constexpr auto kfn = flux_x_persistent_kernel<N, C>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = ensure_smem<kfn>((int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > blocks) grid = blocks;
+    kfn<<<(unsigned)grid, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw, bgrid, (unsigned)blocks, ctr);
+    return cudaGetLastError();
+  }
   flux_x_kernel<N, C><<<(unsigned)blocks, threads, smem, s>>>(in, out, phys, part, d.k, bpi, tw, bgrid);
   return cudaGetLastError();
 }
@@ -734,19 +791,19 @@ int diag_x_blocks(int n) { return n * n / (2 * pairs_for(n)); }
 
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx64 *tw, cudaStream_t s, int *err, double *bgrid,
-                          uint32_t wait_polls) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls)));
+                          uint32_t wait_polls, unsigned *ctr) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls, ctr)));
 }
 
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx32 *tw, cudaStream_t s, int *err, float *bgrid,
-                          uint32_t wait_polls) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls)));
+                          uint32_t wait_polls, unsigned *ctr) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, err, bgrid, wait_polls, ctr)));
 }
 
 cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
-                          const cdf *tw, cudaStream_t s, int *, double *bgrid, uint32_t) {
-  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, nullptr, bgrid, kWaitPolls)));
+                          const cdf *tw, cudaStream_t s, int *, double *bgrid, uint32_t, unsigned *ctr) {
+  MHD_DISPATCH_N(d.n, (flux_n<N>(in, out, phys, smax_bits, d, tw, s, nullptr, bgrid, kWaitPolls, ctr)));
 }
 
 cudaError_t launch_set_x(const double *rho, const double *u, const double *b, cplx64 *out,

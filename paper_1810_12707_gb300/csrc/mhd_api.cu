@@ -61,6 +61,8 @@ struct mhd_ctx {
   bool use_graph = true;
   bool flux_pipeline = false;
   uint32_t wait_polls = mhd::kWaitPolls;  // poll limit of the pipelined flux pass's copy waits
+  bool persistent = false;    // column and flux passes as persistent work-queue kernels
+  unsigned *work_ctr = nullptr;  // two zeroed words per pass of the step (persistent kernels)
   bool forced = false;  // some instance has the ABC body force on
   // tracer particles: per instance a count and device data tr[6][count]; the grid magnetic field
   // the step's flux pass writes for them ([batch][3][N^3], working precision)
@@ -350,6 +352,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   ok = ok && (c->part = (double *)dalloc(c, s.part * sizeof(double))) != nullptr;
   ok = ok && (c->smax_bits = (unsigned long long *)dalloc(c, 2 * p->batch * sizeof(unsigned long long))) != nullptr;
   ok = ok && (c->d_err = (int *)dalloc(c, 4 * sizeof(int))) != nullptr;
+  ok = ok && (c->work_ctr = (unsigned *)dalloc(c, 16 * sizeof(unsigned))) != nullptr;
   ok = ok && (c->ts = (mhd::TimeState *)dalloc(c, p->batch * sizeof(mhd::TimeState))) != nullptr;
   ok = ok && (c->coef = (mhd::StepCoef *)dalloc(c, p->batch * sizeof(mhd::StepCoef))) != nullptr;
   ok = ok && (c->phys = (mhd::PhysDev *)dalloc(c, p->batch * sizeof(mhd::PhysDev))) != nullptr;
@@ -378,6 +381,7 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ts, 0, p->batch * sizeof(mhd::TimeState), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->smax_bits, 0, 2 * p->batch * sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->work_ctr, 0, 16 * sizeof(unsigned), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_all(c);
@@ -627,20 +631,24 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
   CF *w2 = reinterpret_cast<CF *>(c->W2);
-  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0]));
-  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1], c->radix[1]));
+  unsigned *ctr = c->persistent ? c->work_ctr : nullptr;  // two words per pass: 0, 2, 4, 6, 8
+  auto wc = [&](int pass) { return ctr ? ctr + 2 * pass : nullptr; };
+  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0], wc(0)));
+  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1], c->radix[1], wc(1)));
   // The CFL maximum of an advancing pass goes to the first slot (zero at the pass's start: the
   // dt kernel resets it after reading).  Evaluations that take no step (later RK stages, the
   // corrector, mhd_rhs) write to a second slot that nothing reads; its maxima are not exact
   // (the flux pass screens against the slot's earlier content), which changes no result.
   unsigned long long *bits = c->smax_bits + (advance ? 0 : c->d.batch) + inst0;
   LAUNCH(2, mhd::launch_flux_x(w2, w1, phys, bits, d, tw, c->stream, c->flux_pipeline ? c->d_err : nullptr, bgrid,
-                               c->wait_polls));
+                               c->wait_polls, wc(2)));
   if (advance) {
     LAUNCH(3, mhd::launch_step_dt(bits, phys, ts, coef, d, c->dt_fixed, c->cfl_adv, c->cfl_visc, c->stream));
   }
-  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2], c->radix[2]));
-  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3], c->radix[3]));
+  LAUNCH(4, mhd::launch_col_forward(w1, w2, d.n, b * 12 * d.n, d.nx, 1.0, tw, c->stream, c->tile[2], c->radix[2],
+                                    wc(3)));
+  LAUNCH(5, mhd::launch_col_forward(w2, w1, d.n, b * 12, d.nk * d.nx, 1.0, tw, c->stream, c->tile[3], c->radix[3],
+                                    wc(4)));
   return MHD_OK;
 }
 
@@ -947,6 +955,9 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   } else if (option == MHD_OPT_FLUX_PIPELINE) {
     if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "pipeline option must be 0 or 1");
     c->flux_pipeline = value != 0;
+  } else if (option == MHD_OPT_PERSISTENT) {
+    if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "persistent option must be 0 or 1");
+    c->persistent = value != 0;
   } else if (option == MHD_OPT_WAIT_POLLS) {
     if (value < 0 || value > (int64_t)mhd::kWaitPolls)
       return fail(c, MHD_EINVAL, "wait poll limit must be 0..%u", (unsigned)mhd::kWaitPolls);

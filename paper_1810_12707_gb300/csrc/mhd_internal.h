@@ -125,27 +125,32 @@ std::vector<cplx64> twiddle_table(int n);
 std::vector<unsigned char> fp64_twiddle_bytes(int n);
 constexpr size_t fp64_twiddle_size(int n) { return (size_t)n * (2 * sizeof(cplx64) + 1); }
 
+// `ctr` (nullable): two zeroed unsigned words of device memory owned by the caller; when given,
+// the pass runs as a persistent kernel (one grid of resident blocks taking tiles from ctr[0]) and
+// leaves the words zeroed again.  Results are the same bits either way.
 cudaError_t launch_col_inverse(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
+                               const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0, unsigned *ctr = nullptr);
 cudaError_t launch_col_inverse(const cplx64 *in, cplx32 *out, int n, int nslab, int cols,
                                const cplx32 *tw, cudaStream_t s, int tile = 0);
 // vpt (FP32 passes): values per thread of the transform, 8 (radix 8) or 16 (radix 16); 0 = the
 // library's default for the grid size.
 cudaError_t launch_col_inverse(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
+                               const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0, unsigned *ctr = nullptr);
 // Largest power-of-two tile width (columns per block, <= 64) a column pass can launch with:
 // dir +1 inverse, -1 forward; fp64 the transform type; mixed_in an FP64 input to an FP32 inverse.
 int col_max_tile(int n, int dir, bool fp64, bool mixed_in = false, int vpt = 8);
 cudaError_t launch_col_forward(const cplx64 *in, cplx64 *out, int n, int nslab, int cols,
-                               double scale, const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
+                               double scale, const cplx64 *tw, cudaStream_t s, int tile = 0, int vpt = 0,
+                               unsigned *ctr = nullptr);
 cudaError_t launch_col_forward(const cplx32 *in, cplx32 *out, int n, int nslab, int cols,
-                               double scale, const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0);
+                               double scale, const cplx32 *tw, cudaStream_t s, int tile = 0, int vpt = 0,
+                               unsigned *ctr = nullptr);
 // Double-float passes (MHD_FP64_DF): data, twiddles (W_N^m as hi + lo pairs) and arithmetic in
 // double-float, radix 8; `scale` must be a power of two.
 cudaError_t launch_col_inverse(const cdf *in, cdf *out, int n, int nslab, int cols, const cdf *tw, cudaStream_t s,
-                               int tile = 0, int vpt = 0);
+                               int tile = 0, int vpt = 0, unsigned *ctr = nullptr);
 cudaError_t launch_col_forward(const cdf *in, cdf *out, int n, int nslab, int cols, double scale, const cdf *tw,
-                               cudaStream_t s, int tile = 0, int vpt = 0);
+                               cudaStream_t s, int tile = 0, int vpt = 0, unsigned *ctr = nullptr);
 int col_max_tile_df(int n, int dir);
 
 // Fused x pass: inverse real transforms of the 7 state fields row by row, the products on the
@@ -157,17 +162,19 @@ int col_max_tile_df(int n, int dir);
 // With `bgrid` non-null the grid magnetic field is written to bgrid[inst][3][N^3] as well (the
 // plain variant runs).
 constexpr uint32_t kWaitPolls = 1u << 22;
+// `ctr` (nullable, not with the pipelined variant): two zeroed unsigned words; the pass then runs
+// as a persistent kernel taking row-pair blocks from ctr[0] (same results).
 cudaError_t launch_flux_x(const cplx64 *in, cplx64 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx64 *tw, cudaStream_t s, int *err = nullptr,
-                          double *bgrid = nullptr, uint32_t wait_polls = kWaitPolls);
+                          double *bgrid = nullptr, uint32_t wait_polls = kWaitPolls, unsigned *ctr = nullptr);
 cudaError_t launch_flux_x(const cplx32 *in, cplx32 *out, const PhysDev *phys, unsigned long long *smax_bits,
                           const Dims &d, const cplx32 *tw, cudaStream_t s, int *err = nullptr,
-                          float *bgrid = nullptr, uint32_t wait_polls = kWaitPolls);
+                          float *bgrid = nullptr, uint32_t wait_polls = kWaitPolls, unsigned *ctr = nullptr);
 // Double-float flux pass (MHD_FP64_DF): products in double-float, exact FP64 CFL maximum as in
 // the FP64 pass, grid magnetic field for the tracers in FP64.
 cudaError_t launch_flux_x(const cdf *in, cdf *out, const PhysDev *phys, unsigned long long *smax_bits, const Dims &d,
                           const cdf *tw, cudaStream_t s, int *err = nullptr, double *bgrid = nullptr,
-                          uint32_t wait_polls = kWaitPolls);
+                          uint32_t wait_polls = kWaitPolls, unsigned *ctr = nullptr);
 int flux_x_blocks_per_instance(int n);
 
 // Forward real transform along x of 7 real fields given as rho, u (3), B (3) on the grid, with
