@@ -494,16 +494,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // ------------------------------------------------------------------------------------------
 // Forward x transform of an initial state (m = rho u formed first)
 // ------------------------------------------------------------------------------------------
-template <int N>
+// The real fields are FP64; C = cplx64 transforms in FP64, C = cdf splits each value (and the FP64
+// product rho u) into double-float pairs and transforms in double-float.
+__device__ __forceinline__ void x_load(double v, double &r) { r = v; }
+__device__ __forceinline__ void x_load(double v, dfr &r) { r = dfr_from_double(v); }
+__device__ __forceinline__ double x_store(double v) { return v; }
+__device__ __forceinline__ double x_store(dfr v) { return dfr_to_double(v); }
+
+template <int N, typename C>
 // Rows from `row_begin` on (a multiple of 2 PAIRS); the real arrays hold rows from `row_begin`
 // with field stride `fstride` (N^3 for whole fields, less for a slab of z-planes).
 __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__restrict__ rho, const double *__restrict__ u,
-                             const double *__restrict__ b, cplx64 *__restrict__ out, int K,
-                             const cplx64 *__restrict__ tw, size_t row_begin, size_t fstride) {
+                             const double *__restrict__ b, C *__restrict__ out, int K,
+                             const C *__restrict__ tw, size_t row_begin, size_t fstride) {
+  using R = typename C::value_type;
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
-  constexpr int P = pencil_pitch<cplx64>(N);
+  C *sm = reinterpret_cast<C *>(smem_raw);
+  constexpr int P = pencil_pitch<C>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
   constexpr int NX = KT + 1;
@@ -514,12 +522,19 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
     const int p = q / N, j = q - p * N;
     const size_t i0 = (row0 - row_begin + 2 * p) * N + j, i1 = i0 + N;
     const double r0 = rho[i0], r1 = rho[i1];
-    cplx64 *pen = sm + p * 7 * P + sm_idx<cplx64>(j);
-    pen[0] = cplx64{r0, r1};
+    C *pen = sm + p * 7 * P + sm_idx<C>(j);
+    R a, c;
+    x_load(r0, a);
+    x_load(r1, c);
+    pen[0] = C{a, c};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      pen[(1 + d) * P] = cplx64{r0 * u[d * fstride + i0], r1 * u[d * fstride + i1]};
-      pen[(4 + d) * P] = cplx64{b[d * fstride + i0], b[d * fstride + i1]};
+      x_load(r0 * u[d * fstride + i0], a);
+      x_load(r1 * u[d * fstride + i1], c);
+      pen[(1 + d) * P] = C{a, c};
+      x_load(b[d * fstride + i0], a);
+      x_load(b[d * fstride + i1], c);
+      pen[(4 + d) * P] = C{a, c};
     }
   }
   __syncthreads();
@@ -528,25 +543,25 @@ __global__ void __launch_bounds__(kMaxThreads) set_x_kernel(const double *__rest
     const int k = q % NX;
     const int r = q / NX;
     const int f = r % 7, p = r / 7;
-    const cplx64 *pen = sm + (p * 7 + f) * P;
-    const cplx64 z = pen[sm_idx<cplx64>(k)], zc = pen[sm_idx<cplx64>((N - k) & (N - 1))];
-    cplx64 *dst = out + ((size_t)f * NN + row0 + 2 * p) * NX;
-    dst[k] = cplx64{0.5 * (z.re + zc.re), 0.5 * (z.im - zc.im)};
-    dst[NX + k] = cplx64{0.5 * (z.im + zc.im), 0.5 * (zc.re - z.re)};
+    const C *pen = sm + (p * 7 + f) * P;
+    const C z = pen[sm_idx<C>(k)], zc = pen[sm_idx<C>((N - k) & (N - 1))];
+    C *dst = out + ((size_t)f * NN + row0 + 2 * p) * NX;
+    dst[k] = c_store(c_scale(C{z.re + zc.re, z.im - zc.im}, (typename scale_of<C>::type)0.5));
+    dst[NX + k] = c_store(c_scale(C{z.im + zc.im, zc.re - z.re}, (typename scale_of<C>::type)0.5));
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // Inverse x transform to real rows
 // ------------------------------------------------------------------------------------------
-template <int N>
+template <int N, typename C>
 // Rows from `row_begin` on; `out` holds rows from `row_begin` with field stride `fstride`.
-__global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__restrict__ in, double *__restrict__ out, int nf, int K,
-                             const cplx64 *__restrict__ tw, size_t row_begin, size_t fstride) {
+__global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const C *__restrict__ in, double *__restrict__ out, int nf, int K,
+                             const C *__restrict__ tw, size_t row_begin, size_t fstride) {
   constexpr int KT = (N - 1) / 3;  // the 2/3-rule cut-off, fixed by N
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx64 *sm = reinterpret_cast<cplx64 *>(smem_raw);
-  constexpr int P = pencil_pitch<cplx64>(N);
+  C *sm = reinterpret_cast<C *>(smem_raw);
+  constexpr int P = pencil_pitch<C>(N);
   constexpr int PAIRS = pairs_for(N);
   constexpr size_t NN = (size_t)N * N;
   constexpr int NX = KT + 1;
@@ -557,20 +572,20 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     const int k = q % NX;
     const int r = q / NX;
     const int f = r % nf, p = r / nf;
-    const cplx64 *src = in + ((size_t)f * NN + row0 + 2 * p) * NX;
-    cplx64 *pen = sm + (p * nf + f) * P;
-    const cplx64 x0 = src[k], x1 = src[NX + k];
+    const C *src = in + ((size_t)f * NN + row0 + 2 * p) * NX;
+    C *pen = sm + (p * nf + f) * P;
+    const C x0 = src[k], x1 = src[NX + k];
     if (k == 0) {
-      pen[0] = cplx64{x0.re, x1.re};
+      pen[0] = C{x0.re, x1.re};
     } else {
-      pen[sm_idx<cplx64>(k)] = cplx64{x0.re - x1.im, x0.im + x1.re};
-      pen[sm_idx<cplx64>(N - k)] = cplx64{x0.re + x1.im, x1.re - x0.im};
+      pen[sm_idx<C>(k)] = C{x0.re - x1.im, x0.im + x1.re};
+      pen[sm_idx<C>(N - k)] = C{x0.re + x1.im, x1.re - x0.im};
     }
   }
   for (int q = threadIdx.x; q < nf * PAIRS * (N - 2 * KT - 1); q += nthr) {
     const int z = q % (N - 2 * KT - 1);
     const int r = q / (N - 2 * KT - 1);
-    sm[r * P + sm_idx<cplx64>(KT + 1 + z)] = cplx64{0.0, 0.0};
+    sm[r * P + sm_idx<C>(KT + 1 + z)] = C{0, 0};
   }
   __syncthreads();
   fft_pencils<N, +1, 8>(nf * PAIRS, [&](int id) { return sm + id * P; }, tw);
@@ -578,10 +593,10 @@ __global__ void __launch_bounds__(kMaxThreads) get_x_kernel(const cplx64 *__rest
     const int j = q % N;
     const int r = q / N;
     const int f = r % nf, p = r / nf;
-    const cplx64 z = sm[(p * nf + f) * P + sm_idx<cplx64>(j)];
+    const C z = sm[(p * nf + f) * P + sm_idx<C>(j)];
     const size_t i0 = f * fstride + (row0 - row_begin + 2 * p) * N + j;
-    out[i0] = z.re;
-    out[i0 + N] = z.im;
+    out[i0] = x_store(z.re);
+    out[i0 + N] = x_store(z.im);
   }
 }
 
@@ -723,37 +738,37 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t set_n(const double *rho, const double *u, const double *b, cplx64 *out, const Dims &d,
-                  const cplx64 *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
+template <int N, typename C>
+cudaError_t set_n(const double *rho, const double *u, const double *b, C *out, const Dims &d,
+                  const C *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
   constexpr int PAIRS = pairs_for(N);
   if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
   const int blocks = (int)(nrows / (2 * PAIRS));
   if (blocks == 0) return cudaSuccess;
   const int threads = threads_for(tpp_for<N, 8>(), 7 * PAIRS);
-  const size_t smem = (size_t)7 * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
+  const size_t smem = (size_t)7 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<set_x_kernel<N>>((int)smem);
+    cudaError_t e = ensure_smem<set_x_kernel<N, C>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  set_x_kernel<N><<<blocks, threads, smem, s>>>(rho, u, b, out, d.k, tw, row_begin, fstride);
+  set_x_kernel<N, C><<<blocks, threads, smem, s>>>(rho, u, b, out, d.k, tw, row_begin, fstride);
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t get_n(const cplx64 *in, double *out, int nf, const Dims &d, const cplx64 *tw, cudaStream_t s,
+template <int N, typename C>
+cudaError_t get_n(const C *in, double *out, int nf, const Dims &d, const C *tw, cudaStream_t s,
                   size_t row_begin, size_t nrows, size_t fstride) {
   constexpr int PAIRS = pairs_for(N);
   if (row_begin % (2 * PAIRS) || nrows % (2 * PAIRS)) return cudaErrorInvalidValue;
   const int blocks = (int)(nrows / (2 * PAIRS));
   if (blocks == 0) return cudaSuccess;
   const int threads = threads_for(tpp_for<N, 8>(), nf * PAIRS);
-  const size_t smem = (size_t)nf * PAIRS * pencil_pitch<cplx64>(N) * sizeof(cplx64);
+  const size_t smem = (size_t)nf * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<get_x_kernel<N>>((int)smem);
+    cudaError_t e = ensure_smem<get_x_kernel<N, C>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  get_x_kernel<N><<<blocks, threads, smem, s>>>(in, out, nf, d.k, tw, row_begin, fstride);
+  get_x_kernel<N, C><<<blocks, threads, smem, s>>>(in, out, nf, d.k, tw, row_begin, fstride);
   return cudaGetLastError();
 }
 
@@ -825,6 +840,16 @@ cudaError_t launch_get_x(const cplx64 *in, double *out, int nfields, const Dims 
 
 cudaError_t launch_get_x_rows(const cplx64 *in, double *out, int nfields, const Dims &d, const cplx64 *tw,
                               cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
+  MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s, row_begin, nrows, fstride)));
+}
+
+cudaError_t launch_set_x_rows(const double *rho, const double *u, const double *b, cdf *out, const Dims &d,
+                              const cdf *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride) {
+  MHD_DISPATCH_N(d.n, (set_n<N>(rho, u, b, out, d, tw, s, row_begin, nrows, fstride)));
+}
+
+cudaError_t launch_get_x_rows(const cdf *in, double *out, int nfields, const Dims &d, const cdf *tw, cudaStream_t s,
+                              size_t row_begin, size_t nrows, size_t fstride) {
   MHD_DISPATCH_N(d.n, (get_n<N>(in, out, nfields, d, tw, s, row_begin, nrows, fstride)));
 }
 

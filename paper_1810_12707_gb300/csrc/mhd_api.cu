@@ -433,7 +433,10 @@ mhd_status ensure_copy_stream(mhd_ctx *c) {
 
 // Host rho, u, B -> truncated spectra `Si` (FP64) of one instance.  Returns MHD_EINVAL without
 // queueing anything when no staging plan fits (the caller then takes the unpipelined path).
-mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const double *b, cplx64 *Si) {
+// C = cplx64: FP64 transforms into FP64 spectra; C = cdf: double-float transforms into the
+// double-float state (the values are split at the x pass).
+template <typename C>
+mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const double *b, C *Si, const C *tw) {
   SlabPlan pl;
   if (!slab_plan(c, &pl)) return MHD_EINVAL;
   mhd_status st = ensure_copy_stream(c);
@@ -456,17 +459,19 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_full[k], c->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_full[k], 0);
+    C *w1 = reinterpret_cast<C *>(c->W1), *w2 = reinterpret_cast<C *>(c->W2);
     if (e == cudaSuccess)
-      e = mhd::launch_set_x_rows(slot, slot + cnt, slot + 4 * cnt, c->W2, d1, c->tw, c->stream, (size_t)z0 * n,
+      e = mhd::launch_set_x_rows(slot, slot + cnt, slot + 4 * cnt, w2, d1, tw, c->stream, (size_t)z0 * n,
                                  (size_t)dzc * n, cnt);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_free[k], c->stream);
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
-      e = mhd::launch_col_forward(c->W2 + slab0 * n * d.nx, c->W1 + slab0 * d.nk * d.nx, n, dzc, d.nx, 1.0, c->tw,
+      e = mhd::launch_col_forward(w2 + slab0 * n * d.nx, w1 + slab0 * d.nk * d.nx, n, dzc, d.nx, 1.0, tw,
                                   c->stream);
     }
   }
-  if (e == cudaSuccess) e = mhd::launch_col_forward(c->W1, Si, n, 7, d.nk * d.nx, 1.0 / (double)n3, c->tw, c->stream);
+  if (e == cudaSuccess)
+    e = mhd::launch_col_forward(reinterpret_cast<C *>(c->W1), Si, n, 7, d.nk * d.nx, 1.0 / (double)n3, tw, c->stream);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(c->copy_stream);  // the host buffers must outlive the copies in flight
     return fail(c, MHD_ECUDA, "set_state: %s", cudaGetErrorString(e));
@@ -476,7 +481,8 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
 
 // Truncated FP64 spectra `src` of one instance -> host rho, m, B.  MHD_EINVAL (nothing queued)
 // when no staging plan fits.
-mhd_status get_state_host(mhd_ctx *c, const cplx64 *src, double *rho, double *m, double *b) {
+template <typename C>
+mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, double *m, double *b) {
   SlabPlan pl;
   if (!slab_plan(c, &pl)) return MHD_EINVAL;
   mhd_status st = ensure_copy_stream(c);
@@ -485,7 +491,8 @@ mhd_status get_state_host(mhd_ctx *c, const cplx64 *src, double *rho, double *m,
   const mhd::Dims d1 = one(c);
   const int n = d.n;
   const size_t nn = (size_t)n * n, n3 = nn * n;
-  cudaError_t e = mhd::launch_col_inverse(src, c->W1, n, 7, d.nk * d.nx, c->tw, c->stream);  // z pass
+  C *w1 = reinterpret_cast<C *>(c->W1), *w2 = reinterpret_cast<C *>(c->W2);
+  cudaError_t e = mhd::launch_col_inverse(src, w1, n, 7, d.nk * d.nx, tw, c->stream);  // z pass
   int i = 0;
   for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
     const int dzc = std::min(pl.dz, n - z0), k = i & 1;
@@ -494,11 +501,10 @@ mhd_status get_state_host(mhd_ctx *c, const cplx64 *src, double *rho, double *m,
     if (i >= 2) e = cudaStreamWaitEvent(c->stream, c->ev_free[k], 0);  // slot copied out
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
-      e = mhd::launch_col_inverse(c->W1 + slab0 * d.nk * d.nx, c->W2 + slab0 * n * d.nx, n, dzc, d.nx, c->tw,
-                                  c->stream);
+      e = mhd::launch_col_inverse(w1 + slab0 * d.nk * d.nx, w2 + slab0 * n * d.nx, n, dzc, d.nx, tw, c->stream);
     }
     if (e == cudaSuccess)
-      e = mhd::launch_get_x_rows(c->W2, slot, 7, d1, c->tw, c->stream, (size_t)z0 * n, (size_t)dzc * n, cnt);
+      e = mhd::launch_get_x_rows(w2, slot, 7, d1, tw, c->stream, (size_t)z0 * n, (size_t)dzc * n, cnt);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_full[k], c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_full[k], 0);
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
@@ -527,8 +533,31 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
   const mhd::Dims &d = c->d;
   const size_t n3 = (size_t)d.n * d.n * d.n;
   const bool fp64 = c->precision == MHD_FP64;
+  const bool dfl = c->precision == MHD_FP64_DF;
   cplx64 *Si = fp64 ? state64(c, inst) : c->S64;
-  if (!on_device && (st = set_state_host(c, rho, u, b, Si)) != MHD_EINVAL) {
+  if (dfl) {
+    // double-float transforms straight into the double-float state; device inputs go through the
+    // same row kernels over all rows
+    cdf *Sd = statedf(c, inst);
+    if (on_device || (st = set_state_host(c, rho, u, b, Sd, c->twdf)) == MHD_EINVAL) {
+      const double *r = rho, *uu = u, *bb = b;
+      if (!on_device) {
+        double *real = reinterpret_cast<double *>(c->W1);
+        CK(cudaMemcpyAsync(real, rho, n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(real + n3, u, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(real + 4 * n3, b, 3 * n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        r = real;
+        uu = real + n3;
+        bb = real + 4 * n3;
+      }
+      cdf *w1 = reinterpret_cast<cdf *>(c->W1), *w2 = reinterpret_cast<cdf *>(c->W2);
+      CK(mhd::launch_set_x_rows(r, uu, bb, w2, one(c), c->twdf, c->stream, 0, (size_t)d.n * d.n, n3));
+      CK(mhd::launch_col_forward(w2, w1, d.n, 7 * d.n, d.nx, 1.0, c->twdf, c->stream));
+      CK(mhd::launch_col_forward(w1, Sd, d.n, 7, d.nk * d.nx, 1.0 / ((double)n3), c->twdf, c->stream));
+    } else if (st) {
+      return st;
+    }
+  } else if (!on_device && (st = set_state_host(c, rho, u, b, Si, c->tw)) != MHD_EINVAL) {
     if (st) return st;
   } else {
     const double *r = rho, *uu = u, *bb = b;
@@ -547,8 +576,7 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
   }
   if (fp64) {
     CK(cudaMemsetAsync(c->H + (size_t)inst * 7 * d.spec, 0, 7 * d.spec * sizeof(cplx64), c->stream));
-  } else if (c->precision == MHD_FP64_DF) {
-    CK(mhd::launch_split_state(c->S64, statedf(c, inst), 7 * d.spec, c->stream));
+  } else if (dfl) {
     CK(cudaMemsetAsync(histdf(c, inst), 0, 7 * d.spec * sizeof(cdf), c->stream));
   } else {
     CK(mhd::launch_split_state(c->S64, state_hi(c, inst), state_lo(c, inst), 7 * d.spec, c->stream));
@@ -566,9 +594,26 @@ mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, doubl
   if (st) return st;
   if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
   DeviceGuard g(c->device);
+  if (c->precision == MHD_FP64_DF) {
+    // double-float transforms straight from the double-float state
+    const cdf *Sd = statedf(c, inst);
+    if (!on_device && (st = get_state_host(c, Sd, c->twdf, rho, m, b)) != MHD_EINVAL) return st;
+    const mhd::Dims &d = c->d;
+    const size_t n3 = (size_t)d.n * d.n * d.n;
+    cdf *w1 = reinterpret_cast<cdf *>(c->W1), *w2 = reinterpret_cast<cdf *>(c->W2);
+    CK(mhd::launch_col_inverse(Sd, w1, d.n, 7, d.nk * d.nx, c->twdf, c->stream));
+    CK(mhd::launch_col_inverse(w1, w2, d.n, 7 * d.n, d.nx, c->twdf, c->stream));
+    double *real = reinterpret_cast<double *>(c->W1);
+    CK(mhd::launch_get_x_rows(w2, real, 7, one(c), c->twdf, c->stream, 0, (size_t)d.n * d.n, n3));
+    if ((st = copy_out(c, rho, real, n3 * sizeof(double), on_device))) return st;
+    if ((st = copy_out(c, m, real + n3, 3 * n3 * sizeof(double), on_device))) return st;
+    if ((st = copy_out(c, b, real + 4 * n3, 3 * n3 * sizeof(double), on_device))) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return MHD_OK;
+  }
   const cplx64 *src = nullptr;
   if ((st = state_fp64(c, inst, &src))) return st;
-  if (!on_device && (st = get_state_host(c, src, rho, m, b)) != MHD_EINVAL) return st;
+  if (!on_device && (st = get_state_host(c, src, c->tw, rho, m, b)) != MHD_EINVAL) return st;
   return spectra_to_real(c, src, rho, m, b, on_device);
 }
 

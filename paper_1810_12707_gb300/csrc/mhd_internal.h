@@ -193,6 +193,12 @@ cudaError_t launch_set_x_rows(const double *rho, const double *u, const double *
                               const cplx64 *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride);
 cudaError_t launch_get_x_rows(const cplx64 *in, double *out, int nfields, const Dims &d, const cplx64 *tw,
                               cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride);
+// The same in double-float: FP64 values (and the FP64 product rho u) split into double-float pairs
+// on the way in, double-float values summed into FP64 on the way out; transforms in double-float.
+cudaError_t launch_set_x_rows(const double *rho, const double *u, const double *b, cdf *out, const Dims &d,
+                              const cdf *tw, cudaStream_t s, size_t row_begin, size_t nrows, size_t fstride);
+cudaError_t launch_get_x_rows(const cdf *in, double *out, int nfields, const Dims &d, const cdf *tw, cudaStream_t s,
+                              size_t row_begin, size_t nrows, size_t fstride);
 // Inverse x pass of the 7 state fields of one instance with per-block partial sums of the grid
 // diagnostics: part[block][8] = (sum ke, me, eint, u.B, |u|, |B|, max s, unused).
 cudaError_t launch_diag_x(const cplx64 *in, const PhysDev *phys, double *part, const Dims &d,
