@@ -127,6 +127,9 @@ def kernel_model(n: int, batch: int = 1, precision: str = "fp64"):
         "forward_y": (12 * (n * n * nx + n * nk * nx) * c, 12 * n * nx * fft),
         "forward_z": (12 * (n * nk * nx + spec) * c, 12 * nk * nx * fft),
         "assemble_ab2": (asm * spec, 110.0 * spec),
+        # the fused assembly: the assembly's traffic plus the z pass's output (its state read is
+        # the assembly's own)
+        "assemble_iz": (asm * spec + 7 * n * nk * nx * c, 110.0 * spec + 7 * nk * nx * fft),
     }
     if precision == "fp64df":
         # the double-float kernels are bound by their FP32 arithmetic: "flops" become the FP32
@@ -176,6 +179,7 @@ def dfloat_ops(n: int) -> dict:
         "forward_y": 12 * n * nx * (f + nk * store),
         "forward_z": 12 * nk * nx * (f + nk * store),
         "assemble_ab2": 930.0 * spec,
+        "assemble_iz": 930.0 * spec + 7 * nk * nx * (f + n * store),
     }
 
 
@@ -391,6 +395,8 @@ def run_ours(args, name, cfg):
     stream = torch.cuda.current_stream()
     # tile widths of the column FFT passes from the library's autotuner (before any timing)
     tuned = None if args.no_autotune else mhd.mhd_autotune(ctx, reps=3)
+    if args.fused_update:
+        mhd.mhd_set_option(ctx, mhd.MHD_OPT_FUSED_UPDATE, 1)
     tiles = tuned["tiles"] if tuned else None
 
     # per-kernel device times from a profiled run (direct launches, events on the library's
@@ -487,6 +493,8 @@ def run_ours(args, name, cfg):
             per[kname] = {"avg_ms": avg, "share": tot / max(total_ms, 1e-30),
                           "gbs": b / (avg * 1e-3) / 1e9, "tflops": f / (avg * 1e-3) / 1e12}
     top = max(per, key=lambda k: per[k]["share"])
+    # algorithmic bytes of one step: each kernel's bytes times its launches per profiled step
+    step_bytes = sum(model[kname][0] * cnt / K for kname, (tot, cnt) in prof.items() if cnt)
     tb, tf = model[top]
     traffic, traffic_src = measured_traffic(top, n, batch, cfg["precision"])
     t_mem = tb / (hbm * 1e9)
@@ -506,8 +514,8 @@ def run_ours(args, name, cfg):
                 "frac": per[top]["gbs"] / hbm, "traffic": traffic, "peak_source": f"{hbm_src} copy"}
     roof.update({"kernel": top, "traffic_source": traffic_src, "algorithmic_bytes": tb, "algorithmic_flops": tf,
                  "achieved_gbs": per[top]["gbs"], "frac_hbm_of_measured": per[top]["gbs"] / hbm,
-                 "step_model_bytes": sum(v[0] for v in model.values()),
-                 "step_frac_hbm": sum(v[0] for v in model.values()) / (ms / K * 1e-3) / 1e9 / hbm})
+                 "step_model_bytes": step_bytes,
+                 "step_frac_hbm": step_bytes / (ms / K * 1e-3) / 1e9 / hbm})
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras and name == DEFAULT_CONFIG:
@@ -528,12 +536,13 @@ def run_ours(args, name, cfg):
             "dtype": DTYPES[cfg["precision"]], "data": "synthetic",
             "config": dict(config_block(name, cfg, world),
                            col_tiles=tiles if tiles else "library default (autotuner off)",
-                           col_radix=tuned["radix"] if tuned else "library default"),
+                           col_radix=tuned["radix"] if tuned else "library default",
+                           fused_update=bool(args.fused_update)),
             "roofline": roof,
             "kernels": per,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 7 * K,
+            "gpu_launches": (6 if args.fused_update else 7) * K,
             "clocks": clocks,
             "status": mhd.STATUS_NAMES.get(st, st),
             "final": {"t": diag["t"], "dt": diag["dt"], "step": diag["step"], "ke": diag["ke"], "me": diag["me"]},
@@ -741,6 +750,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the extra keys of the default line")
     ap.add_argument("--serve-segment", type=int, default=200, help="requests of the default line's served segment")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default FFT tile widths")
+    ap.add_argument("--fused-update", action="store_true",
+                    help="AB2 steps with the assembly fused into the next inverse z pass (MHD_OPT_FUSED_UPDATE)")
     ap.add_argument("--serve", action="store_true", help="run the serving configuration instead")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--serve-k", type=int, default=20)

@@ -274,7 +274,17 @@ MHD_API mhd_status mhd_restore(mhd_ctx *ctx, int32_t inst, const double *buf, in
  *                          kernels, one grid of resident blocks per pass taking tiles from a work
  *                          counter (for batches of small grids: no per-block launch cost, no
  *                          tail); 0 (default): one block per tile.  No block waits on another.
- *                          Results are identical. */
+ *                          Results are identical.
+ *   MHD_OPT_FUSED_UPDATE   1: an Adams-Bashforth step (MHD_AB2) runs the assembly and update in
+ *                          one kernel with the next step's inverse z transform of the new state
+ *                          (6 launches a step instead of 7; a step call that does not directly
+ *                          follow another adds one plain inverse z pass first).  0 (default):
+ *                          separate kernels, which measured faster on GB300 at N >= 256 (the
+ *                          fused kernel reads the spectra in column tiles, not coalesced rows).
+ *                          Results are identical; RK4 and PC steps are never fused.
+ *   MHD_OPT_TILE_FUSED     columns per block of that fused kernel: 0 (default) = chosen by the
+ *                          library, otherwise 1..64 rounded down to a power of two and capped by
+ *                          the kernel's block size. */
 enum {
   MHD_OPT_CUDA_GRAPH = 0,
   MHD_OPT_TILE_INV_Z = 1,
@@ -287,7 +297,9 @@ enum {
   MHD_OPT_RADIX_FWD_Y = 8,
   MHD_OPT_RADIX_FWD_Z = 9,
   MHD_OPT_WAIT_POLLS = 10,
-  MHD_OPT_PERSISTENT = 11
+  MHD_OPT_PERSISTENT = 11,
+  MHD_OPT_FUSED_UPDATE = 12,
+  MHD_OPT_TILE_FUSED = 13
 };
 MHD_API mhd_status mhd_set_option(mhd_ctx *ctx, int32_t option, int64_t value);
 

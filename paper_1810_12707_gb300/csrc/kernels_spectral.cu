@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "fft_device.cuh"
+#include "launch_util.cuh"
 #include "tma_util.cuh"
 
 namespace mhd {
@@ -58,6 +59,113 @@ __device__ __forceinline__ void abc_force(RhoAt rho, int kx, int ky, int kz, con
 // FC: element type of the product spectra (FP64, or FP32 in the mixed mode); everything else,
 // the state, the history and the arithmetic, is FP64.
 template <typename FC>
+__device__ __forceinline__ void assemble_mode_fp64(const FC *__restrict__ flux, const cplx64 *y_in, cplx64 *state,
+                                cplx64 *__restrict__ hist, cplx64 *ystage, cplx64 *__restrict__ rhs_out,
+                                const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
+                                const cplx64 *__restrict__ force, int op, int stage, int K, double inv_n3,
+                                int inst, size_t m, cplx64 *ynew, int ystride) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const int kxi = (int)(m % NX);
+  const size_t t = m / NX;
+  const int jy = (int)(t % NK), jz = (int)(t / NK);
+  const double kx = kxi, ky = kept_wave(jy, K), kz = kept_wave(jz, K);
+  const double k2 = kx * kx + ky * ky + kz * kz;
+  const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
+
+  // the product spectra arrive unnormalised: their factor inv_n3 rides on the wavenumbers and
+  // dissipation coefficients they meet (fewer FP64 multiplies than scaling 12 spectra)
+  const double skx = kx * inv_n3, sky = ky * inv_n3, skz = kz * inv_n3, nuk2s = nu * k2 * inv_n3;
+  const cplx64 *S = y_in + (size_t)inst * 7 * spec + m;
+  const FC *F = flux + (size_t)inst * 12 * spec + m;
+  cplx64 y[7], f[12];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) f[q] = c_cvt<cplx64>(F[q * spec]);
+  const cplx64 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+  const cplx64 Ex = f[6], Ey = f[7], Ez = f[8];
+
+  cplx64 r[7];
+  // continuity: -i k . m
+  {
+    const cplx64 s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+    r[0] = cplx64{s.im, -s.re};
+  }
+  // momentum
+  {
+    const double kk[3] = {kx, ky, kz};
+    const cplx64 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cplx64 divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
+                           skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
+      const cplx64 g = {divT.re + kk[a] * cs2 * y[0].re, divT.im + kk[a] * cs2 * y[0].im};
+      const cplx64 u = f[9 + a];
+      r[1 + a] = cplx64{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
+    }
+    if (force != nullptr && phys[inst].famp != 0.0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cplx64 fo = force[((size_t)inst * 3 + a) * spec + m];
+        r[1 + a] = cplx64{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+      }
+    }
+  }
+  // induction: i k x E - eta k^2 B
+  {
+    const cplx64 c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
+                         {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
+                         {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
+    const double etak2 = eta * k2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      r[4 + a] = cplx64{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
+  }
+
+  const size_t o7 = (size_t)inst * 7 * spec + m;
+  if (op == ASM_RHS) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = r[q];
+    return;
+  }
+  const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
+  const double dta1 = dt * a1, dta0 = dt * a0;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const size_t i = o7 + q * spec;
+    const cplx64 rq = r[q];
+    if (op == ASM_AB2 || op == ASM_PC_PRED) {
+      // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
+      cplx64 y0 = state[i];
+      if (a0 != 0.0) {
+        const cplx64 h = hist[i];
+        y0 = cplx64{fma(dta0, h.re, y0.re), fma(dta0, h.im, y0.im)};
+      }
+      const cplx64 yn = {fma(dta1, rq.re, y0.re), fma(dta1, rq.im, y0.im)};
+      if (op == ASM_AB2) {
+        state[i] = yn;
+        if (ynew) ynew[q * ystride] = yn;
+      } else {
+        ystage[i] = yn;
+      }
+      hist[i] = rq;
+    } else if (op == ASM_RK_STAGE) {
+      const cplx64 acc = stage == 1 ? rq : cplx64{hist[i].re + 2.0 * rq.re, hist[i].im + 2.0 * rq.im};
+      hist[i] = acc;
+      const double w = (stage < 3 ? 0.5 : 1.0) * dt;
+      const cplx64 y0 = state[i];
+      ystage[i] = cplx64{y0.re + w * rq.re, y0.im + w * rq.im};
+    } else {  // ASM_RK_FINAL, ASM_PC_CORR
+      const double w = op == ASM_RK_FINAL ? dt / 6.0 : 0.5 * dt;
+      const cplx64 h = hist[i], y0 = state[i];
+      const cplx64 acc = {h.re + rq.re, h.im + rq.im};
+      state[i] = cplx64{y0.re + w * acc.re, y0.im + w * acc.im};
+    }
+  }
+}
+
+template <typename FC>
 __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in, cplx64 *state,
                                 cplx64 *__restrict__ hist, cplx64 *ystage, cplx64 *__restrict__ rhs_out,
                                 const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
@@ -71,99 +179,8 @@ __global__ void assemble_kernel(const FC *__restrict__ flux, const cplx64 *y_in,
     const int inst = (int)(idx / spec);
     const size_t m = idx - (size_t)inst * spec;
     if (op != ASM_RHS && coef[inst].skip) continue;
-    const int kxi = (int)(m % NX);
-    const size_t t = m / NX;
-    const int jy = (int)(t % NK), jz = (int)(t / NK);
-    const double kx = kxi, ky = kept_wave(jy, K), kz = kept_wave(jz, K);
-    const double k2 = kx * kx + ky * ky + kz * kz;
-    const double nu = phys[inst].nu, eta = phys[inst].eta, cs2 = phys[inst].cs * phys[inst].cs;
-
-    // the product spectra arrive unnormalised: their factor inv_n3 rides on the wavenumbers and
-    // dissipation coefficients they meet (fewer FP64 multiplies than scaling 12 spectra)
-    const double skx = kx * inv_n3, sky = ky * inv_n3, skz = kz * inv_n3, nuk2s = nu * k2 * inv_n3;
-    const cplx64 *S = y_in + (size_t)inst * 7 * spec + m;
-    const FC *F = flux + (size_t)inst * 12 * spec + m;
-    cplx64 y[7], f[12];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) f[q] = c_cvt<cplx64>(F[q * spec]);
-    const cplx64 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
-    const cplx64 Ex = f[6], Ey = f[7], Ez = f[8];
-
-    cplx64 r[7];
-    // continuity: -i k . m
-    {
-      const cplx64 s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
-      r[0] = cplx64{s.im, -s.re};
-    }
-    // momentum
-    {
-      const double kk[3] = {kx, ky, kz};
-      const cplx64 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const cplx64 divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
-                             skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
-        const cplx64 g = {divT.re + kk[a] * cs2 * y[0].re, divT.im + kk[a] * cs2 * y[0].im};
-        const cplx64 u = f[9 + a];
-        r[1 + a] = cplx64{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
-      }
-      if (force != nullptr && phys[inst].famp != 0.0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const cplx64 fo = force[((size_t)inst * 3 + a) * spec + m];
-          r[1 + a] = cplx64{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
-        }
-      }
-    }
-    // induction: i k x E - eta k^2 B
-    {
-      const cplx64 c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
-                           {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
-                           {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
-      const double etak2 = eta * k2;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        r[4 + a] = cplx64{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
-    }
-
-    const size_t o7 = (size_t)inst * 7 * spec + m;
-    if (op == ASM_RHS) {
-#pragma unroll
-      for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = r[q];
-      continue;
-    }
-    const double dt = coef[inst].dt, a1 = coef[inst].a1, a0 = coef[inst].a0;
-    const double dta1 = dt * a1, dta0 = dt * a0;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const size_t i = o7 + q * spec;
-      const cplx64 rq = r[q];
-      if (op == ASM_AB2 || op == ASM_PC_PRED) {
-        // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
-        cplx64 y0 = state[i];
-        if (a0 != 0.0) {
-          const cplx64 h = hist[i];
-          y0 = cplx64{fma(dta0, h.re, y0.re), fma(dta0, h.im, y0.im)};
-        }
-        const cplx64 yn = {fma(dta1, rq.re, y0.re), fma(dta1, rq.im, y0.im)};
-        if (op == ASM_AB2) state[i] = yn;
-        else ystage[i] = yn;
-        hist[i] = rq;
-      } else if (op == ASM_RK_STAGE) {
-        const cplx64 acc = stage == 1 ? rq : cplx64{hist[i].re + 2.0 * rq.re, hist[i].im + 2.0 * rq.im};
-        hist[i] = acc;
-        const double w = (stage < 3 ? 0.5 : 1.0) * dt;
-        const cplx64 y0 = state[i];
-        ystage[i] = cplx64{y0.re + w * rq.re, y0.im + w * rq.im};
-      } else {  // ASM_RK_FINAL, ASM_PC_CORR
-        const double w = op == ASM_RK_FINAL ? dt / 6.0 : 0.5 * dt;
-        const cplx64 h = hist[i], y0 = state[i];
-        const cplx64 acc = {h.re + rq.re, h.im + rq.im};
-        state[i] = cplx64{y0.re + w * acc.re, y0.im + w * acc.im};
-      }
-    }
+    assemble_mode_fp64<FC>(flux, y_in, state, hist, ystage, rhs_out, phys, coef, force, op, stage, K, inv_n3, inst, m,
+                           nullptr, 0);
   }
 }
 
@@ -175,6 +192,107 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
   const float e = (hi - (s - bb)) + (d - bb) + lo;  // exact rounding error of hi + d, plus lo
   hi = s + e;
   lo = e - (hi - s);
+}
+
+__device__ __forceinline__ void assemble_mode_mixed(const cplx32 *__restrict__ flux, const cplx32 *y_in, cplx32 *s_hi,
+                                   cplx32 *__restrict__ s_lo, cplx32 *__restrict__ hist, cplx32 *ystage,
+                                   cplx64 *__restrict__ rhs_out, const PhysDev *__restrict__ phys,
+                                   const StepCoef *__restrict__ coef, const cplx32 *__restrict__ force, int op,
+                                   int stage, int K, float inv_n3, int inst, size_t m, cplx32 *ynew, int ystride) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const int kxi = (int)(m % NX);
+  const size_t t = m / NX;
+  const float kx = (float)kxi, ky = (float)kept_wave((int)(t % NK), K), kz = (float)kept_wave((int)(t / NK), K);
+  const float k2 = kx * kx + ky * ky + kz * kz;
+  const PhysDev ph = phys[inst];
+  const float nuk2 = (float)ph.nu * k2, etak2 = (float)ph.eta * k2, cs2 = (float)(ph.cs * ph.cs);
+
+  const size_t base7 = (size_t)inst * 7 * spec + m;
+  const cplx32 *F = flux + (size_t)inst * 12 * spec + m;
+  cplx32 y[7], f[12];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) y[q] = y_in[base7 + q * spec];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
+  const cplx32 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+  const cplx32 Ex = f[6], Ey = f[7], Ez = f[8];
+  cplx32 r[7];
+  {
+    const cplx32 sm = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+    r[0] = cplx32{sm.im, -sm.re};
+  }
+  {
+    const float kk[3] = {kx, ky, kz};
+    const cplx32 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cplx32 g = {kx * T[a][0].re + ky * T[a][1].re + kz * T[a][2].re + kk[a] * cs2 * y[0].re,
+                        kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im + kk[a] * cs2 * y[0].im};
+      const cplx32 u = f[9 + a];
+      r[1 + a] = cplx32{g.im - nuk2 * u.re, -g.re - nuk2 * u.im};
+    }
+    if (force != nullptr && ph.famp != 0.0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cplx32 fo = force[((size_t)inst * 3 + a) * spec + m];
+        r[1 + a] = cplx32{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+      }
+    }
+  }
+  {
+    const cplx32 c[3] = {{ky * Ez.re - kz * Ey.re, ky * Ez.im - kz * Ey.im},
+                         {kz * Ex.re - kx * Ez.re, kz * Ex.im - kx * Ez.im},
+                         {kx * Ey.re - ky * Ex.re, kx * Ey.im - ky * Ex.im}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      r[4 + a] = cplx32{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
+  }
+  if (op == ASM_RHS) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) rhs_out[base7 + q * spec] = c_cvt<cplx64>(r[q]);
+    return;
+  }
+  const StepCoef cf = coef[inst];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const size_t i = base7 + q * spec;
+    const cplx32 rq = r[q];
+    if (op == ASM_AB2 || op == ASM_PC_PRED) {
+      cplx32 inc = {cf.fa1 * rq.re, cf.fa1 * rq.im};
+      if (cf.fa0 != 0.f) {
+        const cplx32 h = hist[i];
+        inc.re += cf.fa0 * h.re;
+        inc.im += cf.fa0 * h.im;
+      }
+      if (op == ASM_AB2) {
+        cplx32 hi = s_hi[i], lo = s_lo[i];
+        df_add(hi.re, lo.re, cf.fdt * inc.re);
+        df_add(hi.im, lo.im, cf.fdt * inc.im);
+        s_hi[i] = hi;
+        s_lo[i] = lo;
+        if (ynew) ynew[q * ystride] = hi;
+      } else {
+        const cplx32 hi = s_hi[i], lo = s_lo[i];
+        ystage[i] = cplx32{hi.re + (lo.re + cf.fdt * inc.re), hi.im + (lo.im + cf.fdt * inc.im)};
+      }
+      hist[i] = rq;
+    } else if (op == ASM_RK_STAGE) {
+      const cplx32 acc = stage == 1 ? rq : cplx32{hist[i].re + 2.f * rq.re, hist[i].im + 2.f * rq.im};
+      hist[i] = acc;
+      const float w = (stage < 3 ? 0.5f : 1.f) * cf.fdt;
+      const cplx32 hi = s_hi[i], lo = s_lo[i];
+      ystage[i] = cplx32{hi.re + (lo.re + w * rq.re), hi.im + (lo.im + w * rq.im)};
+    } else {  // ASM_RK_FINAL, ASM_PC_CORR
+      const float w = op == ASM_RK_FINAL ? cf.fdt / 6.f : 0.5f * cf.fdt;
+      const cplx32 h = hist[i];
+      cplx32 hi = s_hi[i], lo = s_lo[i];
+      df_add(hi.re, lo.re, w * (h.re + rq.re));
+      df_add(hi.im, lo.im, w * (h.im + rq.im));
+      s_hi[i] = hi;
+      s_lo[i] = lo;
+    }
+  }
 }
 
 __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32 *y_in, cplx32 *s_hi,
@@ -190,97 +308,8 @@ __global__ void assemble_df_kernel(const cplx32 *__restrict__ flux, const cplx32
     const int inst = (int)(idx / spec);
     const size_t m = idx - (size_t)inst * spec;
     if (op != ASM_RHS && coef[inst].skip) continue;
-    const int kxi = (int)(m % NX);
-    const size_t t = m / NX;
-    const float kx = (float)kxi, ky = (float)kept_wave((int)(t % NK), K), kz = (float)kept_wave((int)(t / NK), K);
-    const float k2 = kx * kx + ky * ky + kz * kz;
-    const PhysDev ph = phys[inst];
-    const float nuk2 = (float)ph.nu * k2, etak2 = (float)ph.eta * k2, cs2 = (float)(ph.cs * ph.cs);
-
-    const size_t base7 = (size_t)inst * 7 * spec + m;
-    const cplx32 *F = flux + (size_t)inst * 12 * spec + m;
-    cplx32 y[7], f[12];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) y[q] = y_in[base7 + q * spec];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) f[q] = c_scale(F[q * spec], inv_n3);
-    const cplx32 Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
-    const cplx32 Ex = f[6], Ey = f[7], Ez = f[8];
-    cplx32 r[7];
-    {
-      const cplx32 sm = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
-      r[0] = cplx32{sm.im, -sm.re};
-    }
-    {
-      const float kk[3] = {kx, ky, kz};
-      const cplx32 T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const cplx32 g = {kx * T[a][0].re + ky * T[a][1].re + kz * T[a][2].re + kk[a] * cs2 * y[0].re,
-                          kx * T[a][0].im + ky * T[a][1].im + kz * T[a][2].im + kk[a] * cs2 * y[0].im};
-        const cplx32 u = f[9 + a];
-        r[1 + a] = cplx32{g.im - nuk2 * u.re, -g.re - nuk2 * u.im};
-      }
-      if (force != nullptr && ph.famp != 0.0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const cplx32 fo = force[((size_t)inst * 3 + a) * spec + m];
-          r[1 + a] = cplx32{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
-        }
-      }
-    }
-    {
-      const cplx32 c[3] = {{ky * Ez.re - kz * Ey.re, ky * Ez.im - kz * Ey.im},
-                           {kz * Ex.re - kx * Ez.re, kz * Ex.im - kx * Ez.im},
-                           {kx * Ey.re - ky * Ex.re, kx * Ey.im - ky * Ex.im}};
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        r[4 + a] = cplx32{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
-    }
-    if (op == ASM_RHS) {
-#pragma unroll
-      for (int q = 0; q < 7; ++q) rhs_out[base7 + q * spec] = c_cvt<cplx64>(r[q]);
-      continue;
-    }
-    const StepCoef cf = coef[inst];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const size_t i = base7 + q * spec;
-      const cplx32 rq = r[q];
-      if (op == ASM_AB2 || op == ASM_PC_PRED) {
-        cplx32 inc = {cf.fa1 * rq.re, cf.fa1 * rq.im};
-        if (cf.fa0 != 0.f) {
-          const cplx32 h = hist[i];
-          inc.re += cf.fa0 * h.re;
-          inc.im += cf.fa0 * h.im;
-        }
-        if (op == ASM_AB2) {
-          cplx32 hi = s_hi[i], lo = s_lo[i];
-          df_add(hi.re, lo.re, cf.fdt * inc.re);
-          df_add(hi.im, lo.im, cf.fdt * inc.im);
-          s_hi[i] = hi;
-          s_lo[i] = lo;
-        } else {
-          const cplx32 hi = s_hi[i], lo = s_lo[i];
-          ystage[i] = cplx32{hi.re + (lo.re + cf.fdt * inc.re), hi.im + (lo.im + cf.fdt * inc.im)};
-        }
-        hist[i] = rq;
-      } else if (op == ASM_RK_STAGE) {
-        const cplx32 acc = stage == 1 ? rq : cplx32{hist[i].re + 2.f * rq.re, hist[i].im + 2.f * rq.im};
-        hist[i] = acc;
-        const float w = (stage < 3 ? 0.5f : 1.f) * cf.fdt;
-        const cplx32 hi = s_hi[i], lo = s_lo[i];
-        ystage[i] = cplx32{hi.re + (lo.re + w * rq.re), hi.im + (lo.im + w * rq.im)};
-      } else {  // ASM_RK_FINAL, ASM_PC_CORR
-        const float w = op == ASM_RK_FINAL ? cf.fdt / 6.f : 0.5f * cf.fdt;
-        const cplx32 h = hist[i];
-        cplx32 hi = s_hi[i], lo = s_lo[i];
-        df_add(hi.re, lo.re, w * (h.re + rq.re));
-        df_add(hi.im, lo.im, w * (h.im + rq.im));
-        s_hi[i] = hi;
-        s_lo[i] = lo;
-      }
-    }
+    assemble_mode_mixed(flux, y_in, s_hi, s_lo, hist, ystage, rhs_out, phys, coef, force, op, stage, K, inv_n3, inst, m,
+                        nullptr, 0);
   }
 }
 
@@ -373,6 +402,107 @@ __global__ void combine_cdf_kernel(const cdf *__restrict__ in, cplx64 *__restric
 // Double-float mode: the RHS of the FP64 assembly above, term by term in the same order, and the
 // update of the double-float state, in double-float arithmetic (no FP64 operation per mode).  The
 // wavenumbers, k^2 and the product spectra's factor 1/(2 N^3) are exact FP32 numbers.
+__device__ __forceinline__ void assemble_mode_dfloat(const cdf *__restrict__ flux, const cdf *y_in, cdf *state,
+                                       cdf *__restrict__ hist, cdf *ystage, cplx64 *__restrict__ rhs_out,
+                                       const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
+                                       const cdf *__restrict__ force, int op, int stage, int K, float inv_n3,
+                                       int inst, size_t m, cdf *ynew, int ystride) {
+  const int NX = K + 1, NK = 2 * K + 1;
+  const size_t spec = (size_t)NK * NK * NX;
+  const int kxi = (int)(m % NX);
+  const size_t t = m / NX;
+  const int jy = (int)(t % NK), jz = (int)(t / NK);
+  const float kx = (float)kxi, ky = (float)kept_wave(jy, K), kz = (float)kept_wave(jz, K);
+  const float k2 = __fadd_rn(__fadd_rn(__fmul_rn(kx, kx), __fmul_rn(ky, ky)), __fmul_rn(kz, kz));  // exact
+  const dfr nu = phys[inst].nu_df, eta = phys[inst].eta_df, cs2 = phys[inst].cs2_df;
+  const float skx = __fmul_rn(kx, inv_n3), sky = __fmul_rn(ky, inv_n3), skz = __fmul_rn(kz, inv_n3);
+  const dfr nuk2s = dfr_scale2(k2 * nu, inv_n3);
+
+  const cdf *S = y_in + (size_t)inst * 7 * spec + m;
+  const cdf *F = flux + (size_t)inst * 12 * spec + m;
+  cdf y[7], f[12];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) f[q] = F[q * spec];
+  const cdf Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
+  const cdf Ex = f[6], Ey = f[7], Ez = f[8];
+
+  cdf r[7];
+  {  // continuity: -i k . m
+    const cdf s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
+    r[0] = cdf{s.im, -s.re};
+  }
+  {  // momentum
+    const float kk[3] = {kx, ky, kz};
+    const cdf T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cdf divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
+                        skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
+      const dfr kc = kk[a] * cs2;
+      const cdf g = {divT.re + kc * y[0].re, divT.im + kc * y[0].im};
+      const cdf u = f[9 + a];
+      r[1 + a] = cdf{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
+    }
+    if (force != nullptr && phys[inst].famp != 0.0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cdf fo = force[((size_t)inst * 3 + a) * spec + m];
+        r[1 + a] = cdf{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
+      }
+    }
+  }
+  {  // induction: i k x E - eta k^2 B
+    const cdf c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
+                      {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
+                      {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
+    const dfr etak2 = k2 * eta;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r[4 + a] = cdf{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
+  }
+
+  const size_t o7 = (size_t)inst * 7 * spec + m;
+  if (op == ASM_RHS) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = cplx64{dfr_to_double(r[q].re), dfr_to_double(r[q].im)};
+    return;
+  }
+  const StepCoef cf = coef[inst];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const size_t i = o7 + q * spec;
+    const cdf rq = r[q];
+    if (op == ASM_AB2 || op == ASM_PC_PRED) {
+      // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
+      cdf y0 = state[i];
+      if (cf.a0 != 0.0) {
+        const cdf h = hist[i];
+        y0 = cdf{y0.re + cf.dta0_df * h.re, y0.im + cf.dta0_df * h.im};
+      }
+      const cdf yn = cdf_norm(cdf{y0.re + cf.dta1_df * rq.re, y0.im + cf.dta1_df * rq.im});
+      if (op == ASM_AB2) {
+        state[i] = yn;
+        if (ynew) ynew[q * ystride] = yn;
+      } else {
+        ystage[i] = yn;
+      }
+      hist[i] = cdf_norm(rq);
+    } else if (op == ASM_RK_STAGE) {
+      const cdf acc = cdf_norm(stage == 1 ? rq : cdf{hist[i].re + dfr_scale2(rq.re, 2.f), hist[i].im + dfr_scale2(rq.im, 2.f)});
+      hist[i] = acc;
+      const dfr w = stage < 3 ? dfr_scale2(cf.dt_df, 0.5f) : cf.dt_df;
+      const cdf y0 = state[i];
+      ystage[i] = cdf_norm(cdf{y0.re + w * rq.re, y0.im + w * rq.im});
+    } else {  // ASM_RK_FINAL, ASM_PC_CORR
+      const dfr w = op == ASM_RK_FINAL ? cf.dt6_df : dfr_scale2(cf.dt_df, 0.5f);
+      const cdf h = hist[i], y0 = state[i];
+      const cdf acc = {h.re + rq.re, h.im + rq.im};
+      state[i] = cdf_norm(cdf{y0.re + w * acc.re, y0.im + w * acc.im});
+    }
+  }
+}
+
 __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *y_in, cdf *state,
                                        cdf *__restrict__ hist, cdf *ystage, cplx64 *__restrict__ rhs_out,
                                        const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
@@ -386,94 +516,8 @@ __global__ void assemble_dfloat_kernel(const cdf *__restrict__ flux, const cdf *
     const int inst = (int)(idx / spec);
     const size_t m = idx - (size_t)inst * spec;
     if (op != ASM_RHS && coef[inst].skip) continue;
-    const int kxi = (int)(m % NX);
-    const size_t t = m / NX;
-    const int jy = (int)(t % NK), jz = (int)(t / NK);
-    const float kx = (float)kxi, ky = (float)kept_wave(jy, K), kz = (float)kept_wave(jz, K);
-    const float k2 = __fadd_rn(__fadd_rn(__fmul_rn(kx, kx), __fmul_rn(ky, ky)), __fmul_rn(kz, kz));  // exact
-    const dfr nu = phys[inst].nu_df, eta = phys[inst].eta_df, cs2 = phys[inst].cs2_df;
-    const float skx = __fmul_rn(kx, inv_n3), sky = __fmul_rn(ky, inv_n3), skz = __fmul_rn(kz, inv_n3);
-    const dfr nuk2s = dfr_scale2(k2 * nu, inv_n3);
-
-    const cdf *S = y_in + (size_t)inst * 7 * spec + m;
-    const cdf *F = flux + (size_t)inst * 12 * spec + m;
-    cdf y[7], f[12];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) y[q] = S[q * spec];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) f[q] = F[q * spec];
-    const cdf Txx = f[0], Tyy = f[1], Tzz = f[2], Txy = f[3], Txz = f[4], Tyz = f[5];
-    const cdf Ex = f[6], Ey = f[7], Ez = f[8];
-
-    cdf r[7];
-    {  // continuity: -i k . m
-      const cdf s = {kx * y[1].re + ky * y[2].re + kz * y[3].re, kx * y[1].im + ky * y[2].im + kz * y[3].im};
-      r[0] = cdf{s.im, -s.re};
-    }
-    {  // momentum
-      const float kk[3] = {kx, ky, kz};
-      const cdf T[3][3] = {{Txx, Txy, Txz}, {Txy, Tyy, Tyz}, {Txz, Tyz, Tzz}};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const cdf divT = {skx * T[a][0].re + sky * T[a][1].re + skz * T[a][2].re,
-                          skx * T[a][0].im + sky * T[a][1].im + skz * T[a][2].im};
-        const dfr kc = kk[a] * cs2;
-        const cdf g = {divT.re + kc * y[0].re, divT.im + kc * y[0].im};
-        const cdf u = f[9 + a];
-        r[1 + a] = cdf{g.im - nuk2s * u.re, -g.re - nuk2s * u.im};
-      }
-      if (force != nullptr && phys[inst].famp != 0.0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const cdf fo = force[((size_t)inst * 3 + a) * spec + m];
-          r[1 + a] = cdf{r[1 + a].re + fo.re, r[1 + a].im + fo.im};
-        }
-      }
-    }
-    {  // induction: i k x E - eta k^2 B
-      const cdf c[3] = {{sky * Ez.re - skz * Ey.re, sky * Ez.im - skz * Ey.im},
-                        {skz * Ex.re - skx * Ez.re, skz * Ex.im - skx * Ez.im},
-                        {skx * Ey.re - sky * Ex.re, skx * Ey.im - sky * Ex.im}};
-      const dfr etak2 = k2 * eta;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) r[4 + a] = cdf{-c[a].im - etak2 * y[4 + a].re, c[a].re - etak2 * y[4 + a].im};
-    }
-
-    const size_t o7 = (size_t)inst * 7 * spec + m;
-    if (op == ASM_RHS) {
-#pragma unroll
-      for (int q = 0; q < 7; ++q) rhs_out[o7 + q * spec] = cplx64{dfr_to_double(r[q].re), dfr_to_double(r[q].im)};
-      continue;
-    }
-    const StepCoef cf = coef[inst];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const size_t i = o7 + q * spec;
-      const cdf rq = r[q];
-      if (op == ASM_AB2 || op == ASM_PC_PRED) {
-        // y + dt (a1 f^n + a0 f^{n-1}), as dt a1 f^n + (dt a0 f^{n-1} + y)
-        cdf y0 = state[i];
-        if (cf.a0 != 0.0) {
-          const cdf h = hist[i];
-          y0 = cdf{y0.re + cf.dta0_df * h.re, y0.im + cf.dta0_df * h.im};
-        }
-        const cdf yn = cdf_norm(cdf{y0.re + cf.dta1_df * rq.re, y0.im + cf.dta1_df * rq.im});
-        if (op == ASM_AB2) state[i] = yn;
-        else ystage[i] = yn;
-        hist[i] = cdf_norm(rq);
-      } else if (op == ASM_RK_STAGE) {
-        const cdf acc = cdf_norm(stage == 1 ? rq : cdf{hist[i].re + dfr_scale2(rq.re, 2.f), hist[i].im + dfr_scale2(rq.im, 2.f)});
-        hist[i] = acc;
-        const dfr w = stage < 3 ? dfr_scale2(cf.dt_df, 0.5f) : cf.dt_df;
-        const cdf y0 = state[i];
-        ystage[i] = cdf_norm(cdf{y0.re + w * rq.re, y0.im + w * rq.im});
-      } else {  // ASM_RK_FINAL, ASM_PC_CORR
-        const dfr w = op == ASM_RK_FINAL ? cf.dt6_df : dfr_scale2(cf.dt_df, 0.5f);
-        const cdf h = hist[i], y0 = state[i];
-        const cdf acc = {h.re + rq.re, h.im + rq.im};
-        state[i] = cdf_norm(cdf{y0.re + w * acc.re, y0.im + w * acc.im});
-      }
-    }
+    assemble_mode_dfloat(flux, y_in, state, hist, ystage, rhs_out, phys, coef, force, op, stage, K, inv_n3, inst, m,
+                         nullptr, 0);
   }
 }
 
@@ -715,6 +759,175 @@ cudaError_t launch_expand_spectrum(const cplx64 *in, cplx64 *out, const Dims &d,
 cudaError_t launch_status_any(const TimeState *ts, int batch, int32_t *flag, cudaStream_t s) {
   status_any_kernel<<<1, 256, 0, s>>>(ts, batch, flag);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Assembly and Adams-Bashforth update fused with the next step's inverse z pass
+// ------------------------------------------------------------------------------------------
+// The update of a kept mode needs only that mode, and the inverse z transform of the new state
+// needs only the modes of one (ky', kx) column, so one block can do both for a tile of columns:
+// instance blockIdx.y, TC = 2^tsh consecutive columns q of the (ky', kx) plane (cols = NK NX).
+//   1. every kept kz row l of those columns: the RHS, the update of state and history (the
+//      assembly kernel's arithmetic at that mode, term for term), and the 7 new state values
+//      dropped into 7 TC pencils of length N in shared memory at FFT index kept_to_fft(l);
+//   2. the pencils' inverse transform, zero-padded by the 2/3 rule (the column pass's transform);
+//   3. the z-pass output z_out [b][7][N][cols] that the next step's inverse y pass reads.
+// The 12 product spectra and the new state never make the round trip through HBM that the
+// separate forward-z -> assembly -> inverse-z kernels cost.  An instance that takes no step
+// (coef.skip) keeps its state and still gets its transform.
+__device__ __forceinline__ void fused_mode(const cplx64 *flux, cplx64 *state, cplx64 *, cplx64 *hist,
+                                           const PhysDev *phys, const StepCoef *coef, const cplx64 *force, int K,
+                                           double inv_n3, int inst, size_t m, cplx64 *yn, int ys) {
+  assemble_mode_fp64<cplx64>(flux, state, state, hist, nullptr, nullptr, phys, coef, force, ASM_AB2, 0, K, inv_n3,
+                             inst, m, yn, ys);
+}
+__device__ __forceinline__ void fused_mode(const cdf *flux, cdf *state, cdf *, cdf *hist, const PhysDev *phys,
+                                           const StepCoef *coef, const cdf *force, int K, float inv_n3, int inst,
+                                           size_t m, cdf *yn, int ys) {
+  assemble_mode_dfloat(flux, state, state, hist, nullptr, nullptr, phys, coef, force, ASM_AB2, 0, K, inv_n3, inst, m,
+                       yn, ys);
+}
+// mixed: `state` holds the high parts, `lo` the low parts; the transform takes the new high part
+__device__ __forceinline__ void fused_mode(const cplx32 *flux, cplx32 *state, cplx32 *lo, cplx32 *hist,
+                                           const PhysDev *phys, const StepCoef *coef, const cplx32 *force, int K,
+                                           float inv_n3, int inst, size_t m, cplx32 *yn, int ys) {
+  assemble_mode_mixed(flux, state, state, lo, hist, nullptr, nullptr, phys, coef, force, ASM_AB2, 0, K, inv_n3, inst,
+                      m, yn, ys);
+}
+
+// Threads of a block: 7 TC pencils x TPP; the most any (N, VPT) launches.
+template <int N, int VPT>
+__host__ __device__ constexpr int fused_max_threads() {
+  return 7 * (tpp_for<N, VPT>() >= 64 ? tpp_for<N, VPT>() : 64);
+}
+
+template <int N, int VPT, typename C>
+__global__ void __launch_bounds__(fused_max_threads<N, VPT>(), (fused_max_threads<N, VPT>() <= 448 ? 2 : 1))
+    assemble_iz_kernel(const C *__restrict__ flux, C *state, C *lo, C *__restrict__ hist,
+                       const PhysDev *__restrict__ phys, const StepCoef *__restrict__ coef,
+                       const C *__restrict__ force, C *__restrict__ z_out, int tsh,
+                       typename scale_of<C>::type inv_n3, const C *__restrict__ tw) {
+  constexpr int TPP = tpp_for<N, VPT>();
+  constexpr int P = pencil_pitch<C>(N);
+  constexpr int K = (N - 1) / 3;
+  constexpr int NK = 2 * K + 1, NX = K + 1;
+  constexpr int COLS = NK * NX;
+  constexpr size_t SPEC = (size_t)NK * COLS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *sm = reinterpret_cast<C *>(smem_raw);
+  const int tc = 1 << tsh;
+  const int nthr = blockDim.x;
+  const int inst = blockIdx.y;
+  const int q0 = blockIdx.x * tc;
+  const bool skip = coef[inst].skip != 0;
+
+  // 1. update every kept mode of the tile; the new state goes into the pencils
+  for (int it = threadIdx.x; it < tc * NK; it += nthr) {
+    const int c = it & (tc - 1), l = it >> tsh;
+    const int q = q0 + c;
+    C *yn = sm + c * P + sm_idx<C>(kept_to_fft(l, K, N));  // field f at yn[f * tc * P]
+    if (q < COLS) {
+      const size_t m = (size_t)l * COLS + q;
+      if (skip) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) yn[f * tc * P] = state[((size_t)inst * 7 + f) * SPEC + m];
+      } else {
+        fused_mode(flux, state, lo, hist, phys, coef, force, K, inv_n3, inst, m, yn, tc * P);
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) yn[f * tc * P] = C{0, 0};
+    }
+  }
+  // FFT indices K+1 .. N-K-1 are outside the kept set
+  for (int it = threadIdx.x; it < 7 * tc * (N - NK); it += nthr) {
+    const int p = it / (N - NK), r = it - p * (N - NK);
+    sm[p * P + sm_idx<C>(K + 1 + r)] = C{0, 0};
+  }
+  __syncthreads();
+
+  // 2. inverse z transforms of the 7 TC pencils
+  const int pencil = threadIdx.x / TPP;
+  const int t = threadIdx.x - pencil * TPP;
+  const bool active = q0 + (pencil & (tc - 1)) < COLS;
+  pencil_fft<N, +1, C, VPT, true>(sm + (active ? pencil : 0) * P, t, active, tw);
+  __syncthreads();
+
+  // 3. rows z of the next inverse y pass's input, TC consecutive columns per row
+  for (int it = threadIdx.x; it < 7 * tc * N; it += nthr) {
+    const int c = it & (tc - 1), r = it >> tsh;  // r = f N + z
+    const int f = r / N, z = r - f * N;
+    const int q = q0 + c;
+    if (q < COLS) z_out[((size_t)inst * 7 * N + r) * COLS + q] = c_store(sm[(f * tc + c) * P + sm_idx<C>(z)]);
+  }
+}
+
+namespace {
+
+template <int N, int VPT, typename C>
+cudaError_t assemble_iz_n(const C *flux, C *state, C *lo, C *hist, const PhysDev *phys, const StepCoef *coef,
+                          const C *force, C *z_out, const C *tw, int nb, int tile, cudaStream_t s) {
+  constexpr int TPP = tpp_for<N, VPT>();
+  constexpr int K = (N - 1) / 3;
+  constexpr int COLS = (2 * K + 1) * (K + 1);
+  constexpr int MAXT = fused_max_threads<N, VPT>();
+  if (nb <= 0) return cudaSuccess;
+  if (nb > 65535) return cudaErrorInvalidValue;
+  int tc = tile > 0 ? tile : (TPP >= 64 ? 1 : 64 / TPP);
+  while (tc > 1 && 7 * tc * TPP > MAXT) tc /= 2;
+  int tsh = 0;
+  while ((2 << tsh) <= tc) ++tsh;
+  tc = 1 << tsh;
+  const size_t smem = (size_t)7 * tc * pencil_pitch<C>(N) * sizeof(C);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  constexpr auto kfn = assemble_iz_kernel<N, VPT, C>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = ensure_smem<kfn>((int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // the product spectra arrive unnormalised and doubled (the split's 1/2 is taken here)
+  const auto inv_n3 = (typename scale_of<C>::type)(0.5 / ((double)N * N * N));
+  kfn<<<dim3((COLS + tc - 1) / tc, nb), 7 * tc * TPP, smem, s>>>(flux, state, lo, hist, phys, coef, force, z_out, tsh,
+                                                                inv_n3, tw);
+  return cudaGetLastError();
+}
+
+template <int VPT, typename C>
+cudaError_t assemble_iz_v(const C *flux, C *state, C *lo, C *hist, const PhysDev *phys, const StepCoef *coef,
+                          const C *force, C *z_out, const C *tw, const Dims &d, int tile, cudaStream_t s) {
+  switch (d.n) {
+    case 16: return assemble_iz_n<16, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 32: return assemble_iz_n<32, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 64: return assemble_iz_n<64, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 128: return assemble_iz_n<128, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 256: return assemble_iz_n<256, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 512: return assemble_iz_n<512, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    case 1024: return assemble_iz_n<1024, VPT>(flux, state, lo, hist, phys, coef, force, z_out, tw, d.batch, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_iz(const cplx64 *flux, cplx64 *state, cplx64 *hist, const PhysDev *phys,
+                               const StepCoef *coef, const cplx64 *force, cplx64 *z_out, const cplx64 *tw,
+                               const Dims &d, int tile, cudaStream_t s) {
+  return assemble_iz_v<8>(flux, state, (cplx64 *)nullptr, hist, phys, coef, force, z_out, tw, d, tile, s);
+}
+
+cudaError_t launch_assemble_iz(const cdf *flux, cdf *state, cdf *hist, const PhysDev *phys, const StepCoef *coef,
+                               const cdf *force, cdf *z_out, const cdf *tw, const Dims &d, int tile, cudaStream_t s) {
+  return assemble_iz_v<8>(flux, state, (cdf *)nullptr, hist, phys, coef, force, z_out, tw, d, tile, s);
+}
+
+// `vpt` as the inverse z column pass takes it (0: radix 16 at N >= 512, else 8), so that the
+// transform is that pass's to the bit.
+cudaError_t launch_assemble_iz(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, const PhysDev *phys,
+                               const StepCoef *coef, const cplx32 *force, cplx32 *z_out, const cplx32 *tw,
+                               const Dims &d, int tile, int vpt, cudaStream_t s) {
+  if (vpt == 16 || (vpt == 0 && d.n >= 512))
+    return assemble_iz_v<16>(flux, s_hi, s_lo, hist, phys, coef, force, z_out, tw, d, tile, s);
+  return assemble_iz_v<8>(flux, s_hi, s_lo, hist, phys, coef, force, z_out, tw, d, tile, s);
 }
 
 }  // namespace mhd

@@ -62,6 +62,13 @@ struct mhd_ctx {
   bool flux_pipeline = false;
   uint32_t wait_polls = mhd::kWaitPolls;  // poll limit of the pipelined flux pass's copy waits
   bool persistent = false;    // column and flux passes as persistent work-queue kernels
+  bool fuse = false;          // AB2 steps: assembly fused with the next step's inverse z pass
+  int fuse_tile = 0;          // columns per block of the fused pass (0: default)
+  // the fused steps' z buffer holds the inverse z pass of the state of the first z_nb instances
+  // while no entry point has run since the step call numbered z_at
+  uint64_t api_calls = 0;
+  uint64_t z_at = 0;
+  int z_nb = 0;
   unsigned *work_ctr = nullptr;  // two zeroed words per pass of the step (persistent kernels)
   bool forced = false;  // some instance has the ABC body force on
   // tracer particles: per instance a count and device data tr[6][count]; the grid magnetic field
@@ -84,13 +91,13 @@ struct mhd_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> ev_marks;  // (kernel kind, index of the start event)
-  double prof_ms[8] = {0};
-  int64_t prof_count[8] = {0};
+  double prof_ms[9] = {0};
+  int64_t prof_count[9] = {0};
 };
 
 namespace {
-const char *const kKernelNames[8] = {"inverse_z", "inverse_y", "flux_x", "step_dt", "forward_y", "forward_z",
-                                     "assemble_ab2", "tracer_push"};
+const char *const kKernelNames[9] = {"inverse_z", "inverse_y", "flux_x", "step_dt", "forward_y", "forward_z",
+                                     "assemble_ab2", "tracer_push", "assemble_iz"};
 }
 
 namespace {
@@ -123,6 +130,8 @@ struct DeviceGuard {
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
   }
+  // every entry point that may touch a context's buffers counts itself here
+  explicit DeviceGuard(mhd_ctx *c) : DeviceGuard(c->device) { ++c->api_calls; }
   ~DeviceGuard() {
     int cur = -1;
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
@@ -145,6 +154,8 @@ Sizes sizes_for(const mhd::Dims &d, int precision) {
   s.S = b * 7 * d.spec;
   // step (all instances, working precision)
   size_t w1 = std::max(std::max(7 * n * nk * nx, 12 * n * n * nx), 12 * d.spec) * b * elem;
+  // fused AB2 steps keep the inverse z output of the new state behind the 12 product spectra
+  w1 = std::max(w1, (12 * d.spec + 7 * n * nk * nx) * b * elem);
   size_t w2 = std::max(7 * n * n * nx, 12 * n * nk * nx) * b * elem;
   // one instance in FP64
   w1 = std::max(w1, std::max(7 * n * nk * nx, 12 * n * n * nx) * 16);
@@ -290,7 +301,7 @@ const char *mhd_last_error(const mhd_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void mhd_destroy(mhd_ctx *ctx) {
   if (!ctx) return;
   {
-    DeviceGuard g(ctx->device);
+    DeviceGuard g(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     drop_graphs(ctx);
@@ -529,7 +540,7 @@ mhd_status mhd_set_state(mhd_ctx *c, int32_t inst, const double *rho, const doub
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (!rho || !u || !b) return fail(c, MHD_EINVAL, "null input");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::Dims &d = c->d;
   const size_t n3 = (size_t)d.n * d.n * d.n;
   const bool fp64 = c->precision == MHD_FP64;
@@ -593,7 +604,7 @@ mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, doubl
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   if (c->precision == MHD_FP64_DF) {
     // double-float transforms straight from the double-float state
     const cdf *Sd = statedf(c, inst);
@@ -621,7 +632,7 @@ mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (field < 0 || field >= 7 || !out) return fail(c, MHD_EINVAL, "bad field or null output");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::Dims &d = c->d;
   const size_t full = (size_t)d.n * d.n * (d.n / 2 + 1);
   const cplx64 *src = nullptr;
@@ -668,18 +679,22 @@ static cudaError_t prof_end(mhd_ctx *c, bool on) {
 // CF: complex type of the passes (cplx64 or cplx32); `tw` the matching twiddle table.  `advance`
 // runs the step-size kernel after the flux pass.
 // `bgrid` (nullable) receives the grid magnetic field for the tracers.
+// `z_in` (nullable): the inverse z pass of S is already there (a fused step wrote it); step 1 is
+// skipped and the inverse y pass reads it.
 template <typename CF, typename CS>
 static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, const CS *S, const mhd::PhysDev *phys,
                                  mhd::TimeState *ts, mhd::StepCoef *coef, bool advance, const CF *tw,
-                                 typename mhd::grid_of<CF>::type *bgrid) {
+                                 typename mhd::grid_of<CF>::type *bgrid, const CF *z_in = nullptr) {
   const int b = d.batch;
   const bool prof = advance && c->profiling;
   CF *w1 = reinterpret_cast<CF *>(c->W1);
   CF *w2 = reinterpret_cast<CF *>(c->W2);
   unsigned *ctr = c->persistent ? c->work_ctr : nullptr;  // two words per pass: 0, 2, 4, 6, 8
   auto wc = [&](int pass) { return ctr ? ctr + 2 * pass : nullptr; };
-  LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0], wc(0)));
-  LAUNCH(1, mhd::launch_col_inverse(w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1], c->radix[1], wc(1)));
+  if (!z_in)
+    LAUNCH(0, mhd::launch_col_inverse(S, w1, d.n, b * 7, d.nk * d.nx, tw, c->stream, c->tile[0], c->radix[0], wc(0)));
+  LAUNCH(1, mhd::launch_col_inverse(z_in ? z_in : w1, w2, d.n, b * 7 * d.n, d.nx, tw, c->stream, c->tile[1],
+                                    c->radix[1], wc(1)));
   // The CFL maximum of an advancing pass goes to the first slot (zero at the pass's start: the
   // dt kernel resets it after reading).  Evaluations that take no step (later RK stages, the
   // corrector, mhd_rhs) write to a second slot that nothing reads; its maxima are not exact
@@ -697,6 +712,32 @@ static mhd_status flux_spectra_t(mhd_ctx *c, const mhd::Dims &d, int inst0, cons
   return MHD_OK;
 }
 
+// Fused AB2 steps: the assembly kernel also runs the next step's inverse z pass of the new state;
+// its output (z layout [b][7][N][nk nx]) lives in W1 behind the 12 product spectra, which the step
+// overwrites only after the inverse y pass has read it.  A step sequence starts with a plain
+// inverse z pass into the same place (fused_prologue).
+static bool fused_ab2(const mhd_ctx *c) { return c->fuse && c->integrator == MHD_AB2; }
+
+template <typename C>
+static C *zbuf(mhd_ctx *c, const mhd::Dims &d) {
+  return reinterpret_cast<C *>(c->W1) + 12 * d.spec * (size_t)d.batch;
+}
+
+static mhd_status fused_prologue(mhd_ctx *c, const mhd::Dims &d) {
+  const bool prof = c->profiling;
+  const int b = d.batch;
+  if (c->precision == MHD_FP64)
+    LAUNCH(0, mhd::launch_col_inverse(state64(c, 0), zbuf<cplx64>(c, d), d.n, b * 7, d.nk * d.nx, c->tw, c->stream,
+                                      c->tile[0], c->radix[0]));
+  else if (c->precision == MHD_FP64_DF)
+    LAUNCH(0, mhd::launch_col_inverse(statedf(c, 0), zbuf<cdf>(c, d), d.n, b * 7, d.nk * d.nx, c->twdf, c->stream,
+                                      c->tile[0], c->radix[0]));
+  else
+    LAUNCH(0, mhd::launch_col_inverse(state_hi(c, 0), zbuf<cplx32>(c, d), d.n, b * 7, d.nk * d.nx, c->tw32,
+                                      c->stream, c->tile[0], c->radix[0]));
+  return MHD_OK;
+}
+
 // One RHS evaluation (steps 1-6 of the pass order at the state `y_in`, dt on the first
 // evaluation of a step) and the assembly operation `op` for the `d.batch` instances from `inst0`.
 static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, const void *y_in, cplx64 *rhs_out,
@@ -705,37 +746,55 @@ static mhd_status eval_and_assemble(mhd_ctx *c, const mhd::Dims &d, int inst0, c
   const bool prof = op != mhd::ASM_RHS && c->profiling;
   mhd_status st;
   const size_t off = (size_t)inst0 * 7 * d.spec;
+  // a fused AB2 step of the whole step sequence (inst0 = 0): it reads and writes the z buffer
+  const bool fz = op == mhd::ASM_AB2 && inst0 == 0 && fused_ab2(c);
   if (c->precision == MHD_FP64) {
     const cplx64 *yi = static_cast<const cplx64 *>(y_in);
+    cplx64 *Z = fz ? zbuf<cplx64>(c, d) : nullptr;
     if ((st = flux_spectra_t<cplx64>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw,
-                                     static_cast<double *>(bgrid))))
+                                     static_cast<double *>(bgrid), Z)))
       return st;
     cplx64 *Y = c->Y ? static_cast<cplx64 *>(c->Y) + off : nullptr;
     cplx64 *force = c->forced ? c->W2 : nullptr;  // W2 is free after the forward z pass
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
-    LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
-                                   c->stream, force));
+    if (fz)
+      LAUNCH(8, mhd::launch_assemble_iz(c->W1, state64(c, 0), c->H, phys, coef, force, Z, c->tw, d, c->fuse_tile,
+                                        c->stream));
+    else
+      LAUNCH(6, mhd::launch_assemble(c->W1, yi, state64(c, inst0), c->H + off, Y, rhs_out, phys, coef, op, stage, d,
+                                     c->stream, force));
   } else if (c->precision == MHD_FP64_DF) {
     const cdf *yi = static_cast<const cdf *>(y_in);
+    cdf *Z = fz ? zbuf<cdf>(c, d) : nullptr;
     if ((st = flux_spectra_t<cdf>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->twdf,
-                                  static_cast<double *>(bgrid))))
+                                  static_cast<double *>(bgrid), Z)))
       return st;
     cdf *Y = c->Y ? static_cast<cdf *>(c->Y) + off : nullptr;
     cdf *force = c->forced ? reinterpret_cast<cdf *>(c->W2) : nullptr;  // W2 is free after the forward z pass
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
-    LAUNCH(6, mhd::launch_assemble(reinterpret_cast<const cdf *>(c->W1), yi, statedf(c, inst0), histdf(c, inst0), Y,
-                                   rhs_out, phys, coef, op, stage, d, c->stream, force));
+    if (fz)
+      LAUNCH(8, mhd::launch_assemble_iz(reinterpret_cast<const cdf *>(c->W1), statedf(c, 0), histdf(c, 0), phys,
+                                        coef, force, Z, c->twdf, d, c->fuse_tile, c->stream));
+    else
+      LAUNCH(6, mhd::launch_assemble(reinterpret_cast<const cdf *>(c->W1), yi, statedf(c, inst0), histdf(c, inst0),
+                                     Y, rhs_out, phys, coef, op, stage, d, c->stream, force));
   } else {
     const cplx32 *yi = static_cast<const cplx32 *>(y_in);
+    cplx32 *Z = fz ? zbuf<cplx32>(c, d) : nullptr;
     if ((st = flux_spectra_t<cplx32>(c, d, inst0, yi, phys, ts, coef, first && op != mhd::ASM_RHS, c->tw32,
-                                     static_cast<float *>(bgrid))))
+                                     static_cast<float *>(bgrid), Z)))
       return st;
     cplx32 *Y = c->Y ? static_cast<cplx32 *>(c->Y) + off : nullptr;
     cplx32 *force = c->forced ? reinterpret_cast<cplx32 *>(c->W2) : nullptr;  // free after forward z
     if (force) LAUNCH(6, mhd::launch_force(yi, force, phys, d, c->stream));
-    LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), yi, state_hi(c, inst0),
-                                      state_lo(c, inst0), hist32(c, inst0), Y, rhs_out, phys, coef, op, stage, d,
-                                      c->stream, force));
+    if (fz)
+      LAUNCH(8, mhd::launch_assemble_iz(reinterpret_cast<const cplx32 *>(c->W1), state_hi(c, 0), state_lo(c, 0),
+                                        hist32(c, 0), phys, coef, force, Z, c->tw32, d, c->fuse_tile, c->radix[0],
+                                        c->stream));
+    else
+      LAUNCH(6, mhd::launch_assemble_df(reinterpret_cast<const cplx32 *>(c->W1), yi, state_hi(c, inst0),
+                                        state_lo(c, inst0), hist32(c, inst0), Y, rhs_out, phys, coef, op, stage, d,
+                                        c->stream, force));
   }
   return MHD_OK;
 }
@@ -794,7 +853,7 @@ mhd_status mhd_rhs(mhd_ctx *c, int32_t inst, double *drho, double *dm, double *d
   if (st) return st;
   if (!drho || !dm || !db) return fail(c, MHD_EINVAL, "null output");
   if (!c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::Dims d = one(c);
   if ((st = rhs_or_step(c, d, inst, c->W2, c->phys + inst, nullptr, nullptr, 0))) return st;
   // W2 holds the RHS spectra; inverse_zy reads its source before overwriting W2
@@ -819,6 +878,18 @@ static mhd_status step_prefix(mhd_ctx *c, int nb, int32_t nsteps, cudaGraphExec_
   mhd::Dims d = c->d;
   d.batch = nb;
   int s = 0;
+  const bool fused = fused_ab2(c);
+  if (fused) {
+    // the z buffer is current when the previous entry point was a step call over the same
+    // instances; otherwise a plain inverse z pass refills it, and the steps' fused assembly keeps
+    // it current from there
+    const bool current = c->z_nb == nb && c->z_at + 1 == c->api_calls;
+    c->z_nb = 0;
+    if (!current) {
+      mhd_status st = fused_prologue(c, d);
+      if (st) return st;
+    }
+  }
   if (c->use_graph && !c->profiling) {
     if (!*graph) {
       // one direct step first (it also raises the kernels' shared-memory limits, which is not a
@@ -844,11 +915,15 @@ static mhd_status step_prefix(mhd_ctx *c, int nb, int32_t nsteps, cudaGraphExec_
       CK(e);
     }
     for (; s < nsteps; ++s) CK(cudaGraphLaunch(*graph, c->stream));
-    return MHD_OK;
+  } else {
+    for (; s < nsteps; ++s) {
+      mhd_status st = rhs_or_step(c, d, 0, nullptr, c->phys, c->ts, c->coef, 1);
+      if (st) return st;
+    }
   }
-  for (; s < nsteps; ++s) {
-    mhd_status st = rhs_or_step(c, d, 0, nullptr, c->phys, c->ts, c->coef, 1);
-    if (st) return st;
+  if (fused) {
+    c->z_at = c->api_calls;
+    c->z_nb = nb;
   }
   return MHD_OK;
 }
@@ -861,7 +936,7 @@ mhd_status mhd_step(mhd_ctx *c, int32_t nsteps) {
   if (c->live >= 0) return fail(c, MHD_ESTATE, "context belongs to a pool: use mhd_pool_step");
   for (int i = 0; i < c->d.batch; ++i)
     if (!c->is_set[i]) return fail(c, MHD_ESTATE, "instance %d has no state", i);
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   return step_prefix(c, c->d.batch, nsteps, &c->graph_exec);
 }
 
@@ -881,11 +956,11 @@ static mhd_status prof_resolve(mhd_ctx *c) {
 
 mhd_status mhd_profile(mhd_ctx *c, int32_t enable) {
   if (!c) return MHD_EINVAL;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   mhd_status st = prof_resolve(c);
   if (st) return st;
   if (enable) {
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 9; ++i) {
       c->prof_ms[i] = 0.0;
       c->prof_count[i] = 0;
     }
@@ -896,11 +971,11 @@ mhd_status mhd_profile(mhd_ctx *c, int32_t enable) {
 
 mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32_t *count) {
   if (!c || (!out && max > 0) || !count) return MHD_EINVAL;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   mhd_status st = prof_resolve(c);
   if (st) return st;
   int k = 0;
-  for (int i = 0; i < 8 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
+  for (int i = 0; i < 9 && k < max; ++i, ++k) out[k] = mhd_kernel_time{kKernelNames[i], c->prof_ms[i], c->prof_count[i]};
   *count = k;
   return MHD_OK;
 }
@@ -908,7 +983,7 @@ mhd_status mhd_profile_read(mhd_ctx *c, mhd_kernel_time *out, int32_t max, int32
 mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, int32_t *radix, double *ms) {
   if (!c) return MHD_EINVAL;
   if (reps < 1 || reps > 100) return fail(c, MHD_EINVAL, "reps must be 1..100");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::Dims &d = c->d;
   const int b = d.batch;
   cudaEvent_t e0, e1;
@@ -993,7 +1068,7 @@ mhd_status mhd_autotune(mhd_ctx *c, int32_t reps, int32_t *tiles, int32_t *radix
 
 mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   if (!c) return MHD_EINVAL;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   if (option == MHD_OPT_CUDA_GRAPH) {
     if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "graph option must be 0 or 1");
     c->use_graph = value != 0;
@@ -1003,6 +1078,12 @@ mhd_status mhd_set_option(mhd_ctx *c, int32_t option, int64_t value) {
   } else if (option == MHD_OPT_PERSISTENT) {
     if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "persistent option must be 0 or 1");
     c->persistent = value != 0;
+  } else if (option == MHD_OPT_FUSED_UPDATE) {
+    if (value != 0 && value != 1) return fail(c, MHD_EINVAL, "fused update option must be 0 or 1");
+    c->fuse = value != 0;
+  } else if (option == MHD_OPT_TILE_FUSED) {
+    if (value < 0 || value > 64) return fail(c, MHD_EINVAL, "tile must be 0..64");
+    c->fuse_tile = (int)value;
   } else if (option == MHD_OPT_WAIT_POLLS) {
     if (value < 0 || value > (int64_t)mhd::kWaitPolls)
       return fail(c, MHD_EINVAL, "wait poll limit must be 0..%u", (unsigned)mhd::kWaitPolls);
@@ -1026,7 +1107,7 @@ mhd_status mhd_set_forcing(mhd_ctx *c, int32_t inst, double amp, double a, doubl
   if (st) return st;
   if (!isfinite(amp) || !isfinite(a) || !isfinite(b) || !isfinite(cc)) return fail(c, MHD_EINVAL, "non-finite forcing");
   if (kf < 1 || kf > c->d.k) return fail(c, MHD_EINVAL, "forcing wavenumber %d outside 1..%d", kf, c->d.k);
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::PhysDev pd = mhd::make_phys(c->phys_host[inst].nu, c->phys_host[inst].eta, c->phys_host[inst].cs, amp, a,
                                          b, cc, kf);
   CK(cudaMemcpyAsync(c->phys + inst, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
@@ -1040,7 +1121,7 @@ mhd_status mhd_set_forcing(mhd_ctx *c, int32_t inst, double amp, double a, doubl
 
 mhd_status mhd_synchronize(mhd_ctx *c) {
   if (!c) return MHD_EINVAL;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   int32_t any = 0, err = 0;
   CK(mhd::launch_status_any(c->ts, c->d.batch, c->flag, c->stream));
   CK(cudaMemcpyAsync(&any, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -1057,7 +1138,7 @@ mhd_status mhd_tracers_set(mhd_ctx *c, int32_t inst, int64_t count, const double
   if (count < 0 || (count > 0 && !pos)) return fail(c, MHD_EINVAL, "bad tracer count or null positions");
   if (c->live >= 0) return fail(c, MHD_ESTATE, "tracers are not available on pool contexts");
   if (count > 0 && !c->is_set[inst]) return fail(c, MHD_ESTATE, "instance %d has no state", inst);
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   CK(cudaStreamSynchronize(c->stream));
   drop_graphs(c);  // the step gains or loses launches
   dfree(c, c->tr[inst]);
@@ -1105,7 +1186,7 @@ mhd_status mhd_tracers_get(mhd_ctx *c, int32_t inst, double *pos, double *vel) {
   if (st) return st;
   const int64_t count = c->ntr[inst];
   if (count == 0) return MHD_OK;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   std::vector<double> h((size_t)count * 6);
   CK(cudaMemcpyAsync(h.data(), c->tr[inst], h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -1130,7 +1211,7 @@ mhd_status mhd_spectra(mhd_ctx *c, int32_t inst, double *ek, double *em, int32_t
   const mhd::Dims d = one(c);
   const int ns = mhd::num_shells(d.k);
   if ((ek || em) && nshells != ns) return fail(c, MHD_EINVAL, "nshells must equal mhd_num_shells(n)");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const size_t n3 = (size_t)d.n * d.n * d.n;
   const size_t part_len = sizes_for(c->d, c->precision).part;
   const int mblocks = (int)std::min<size_t>(2 * 152, part_len / 2);
@@ -1198,7 +1279,7 @@ mhd_status mhd_diagnostics(mhd_ctx *c, int32_t inst, mhd_diag *out) {
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (!out) return fail(c, MHD_EINVAL, "null output");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const mhd::Dims d = one(c);
   const cplx64 *Si = nullptr;
   if ((st = state_fp64(c, inst, &Si))) return st;
@@ -1240,7 +1321,7 @@ mhd_status mhd_checkpoint(mhd_ctx *c, int32_t inst, double *buf, int32_t on_devi
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (!buf) return fail(c, MHD_EINVAL, "null buffer");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (c->precision != MHD_FP32_MIXED) {  // FP64, or double-float values in the same bytes
@@ -1271,7 +1352,7 @@ mhd_status mhd_restore(mhd_ctx *c, int32_t inst, const double *buf, int32_t on_d
   mhd_status st = check_inst(c, inst);
   if (st) return st;
   if (!buf) return fail(c, MHD_EINVAL, "null buffer");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const size_t sp = 7 * c->d.spec;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (c->precision != MHD_FP32_MIXED) {  // FP64, or double-float values in the same bytes
@@ -1374,7 +1455,7 @@ mhd_status mhd_pool_admit(mhd_pool *p, const mhd_phys *phys, const double *rho, 
       break;
     }
   if (handle < 0) return MHD_EBUSY;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   const int pos = c->live;
   const mhd::PhysDev pd = mhd::make_phys(phys->nu, phys->eta, phys->cs);
   CK(cudaMemcpyAsync(c->phys + pos, &pd, sizeof pd, cudaMemcpyHostToDevice, c->stream));
@@ -1395,14 +1476,14 @@ mhd_status mhd_pool_step(mhd_pool *p, int32_t k) {
   if (!p) return MHD_EINVAL;
   mhd_ctx *c = p->ctx;
   if (k < 0) return fail(c, MHD_EINVAL, "negative step count");
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   return step_prefix(c, c->live, k, &c->pool_graphs[c->live]);
 }
 
 mhd_status mhd_pool_progress(mhd_pool *p, int64_t *steps, int32_t *status, int32_t *finished) {
   if (!p || !steps || !status || !finished) return MHD_EINVAL;
   mhd_ctx *c = p->ctx;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   std::vector<mhd::TimeState> ts(c->live > 0 ? c->live : 1);
   if (c->live > 0) {
     CK(cudaMemcpyAsync(ts.data(), c->ts, c->live * sizeof(mhd::TimeState), cudaMemcpyDeviceToHost, c->stream));
@@ -1435,7 +1516,7 @@ mhd_status mhd_pool_retire(mhd_pool *p, int32_t slot, double *rho, double *m, do
   mhd_status st = pool_position(p, slot, &pos);
   if (st) return st;
   mhd_ctx *c = p->ctx;
-  DeviceGuard g(c->device);
+  DeviceGuard g(c);
   if (rho && m && b) {
     if ((st = mhd_get_state(c, pos, rho, m, b, on_device))) return st;
   }

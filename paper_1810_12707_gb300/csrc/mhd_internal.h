@@ -255,6 +255,21 @@ cudaError_t launch_force(const cdf *y_in, cdf *force, const PhysDev *phys, const
 cudaError_t launch_split_state(const cplx64 *in, cdf *out, size_t count, cudaStream_t s);
 cudaError_t launch_combine_state(const cdf *in, cplx64 *out, size_t count, cudaStream_t s);
 
+// The Adams-Bashforth assembly (ASM_AB2) of `d.batch` instances fused with the inverse z pass of
+// the new state: reads the 12 product spectra `flux` [b][12][spec], state, history and the force
+// spectra (nullable), updates state and history as launch_assemble does, and writes the z-pass
+// output z_out [b][7][N][nk nx] (the layout launch_col_inverse gives the inverse z pass).
+// `tile`: columns per block (0 picks).  Mixed mode: s_hi / s_lo the state's parts, `vpt` the
+// inverse z pass's radix option.
+cudaError_t launch_assemble_iz(const cplx64 *flux, cplx64 *state, cplx64 *hist, const PhysDev *phys,
+                               const StepCoef *coef, const cplx64 *force, cplx64 *z_out, const cplx64 *tw,
+                               const Dims &d, int tile, cudaStream_t s);
+cudaError_t launch_assemble_iz(const cdf *flux, cdf *state, cdf *hist, const PhysDev *phys, const StepCoef *coef,
+                               const cdf *force, cdf *z_out, const cdf *tw, const Dims &d, int tile, cudaStream_t s);
+cudaError_t launch_assemble_iz(const cplx32 *flux, cplx32 *s_hi, cplx32 *s_lo, cplx32 *hist, const PhysDev *phys,
+                               const StepCoef *coef, const cplx32 *force, cplx32 *z_out, const cplx32 *tw,
+                               const Dims &d, int tile, int vpt, cudaStream_t s);
+
 // Final reduction of the diagnostic partials of one instance plus the spectral terms; writes
 // 24 doubles to `out` (see mhd_api.cu for the order).
 // Shell spectra (kernels_spectra.cu).  launch_velocity_x: rho, m (fields 0..3 of [7][z][y][kx],

@@ -27,7 +27,7 @@ MHD_FP64_DF = 2
 MHD_AB2, MHD_RK4, MHD_PC = 0, 1, 2
 (MHD_OPT_CUDA_GRAPH, MHD_OPT_TILE_INV_Z, MHD_OPT_TILE_INV_Y, MHD_OPT_TILE_FWD_Y, MHD_OPT_TILE_FWD_Z,
  MHD_OPT_FLUX_PIPELINE, MHD_OPT_RADIX_INV_Z, MHD_OPT_RADIX_INV_Y, MHD_OPT_RADIX_FWD_Y,
- MHD_OPT_RADIX_FWD_Z, MHD_OPT_WAIT_POLLS, MHD_OPT_PERSISTENT) = range(12)
+ MHD_OPT_RADIX_FWD_Z, MHD_OPT_WAIT_POLLS, MHD_OPT_PERSISTENT, MHD_OPT_FUSED_UPDATE, MHD_OPT_TILE_FUSED) = range(14)
 STATUS_NAMES = {0: "MHD_OK", 1: "MHD_EINVAL", 2: "MHD_ENOMEM", 3: "MHD_ECUDA", 4: "MHD_ESTATE",
                 5: "MHD_ENONFINITE", 6: "MHD_ETIMEOUT", 7: "MHD_EBUSY"}
 
