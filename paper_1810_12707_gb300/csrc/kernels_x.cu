@@ -38,20 +38,26 @@ constexpr int threads_for(int tpp, int pencils, int max_threads = kMaxThreads) {
 // Block size of the flux pass.  At N = 256 and 512 several smaller blocks per SM let one block
 // transform while another waits at a barrier (measured on GB300 over 96..384 threads: 128 best at
 // 256^3 in both precisions, 192 at 512^3); below, the pencil count caps the block at 192 threads.
-constexpr int flux_max_threads(int n) { return n == 256 ? 128 : n == 512 ? 192 : kMaxThreads; }
+// The double-float pass at 512^3 takes 256 (two blocks of 128 registers a thread per SM): 4 %
+// faster than 192.
+constexpr int flux_max_threads(int n, bool df = false) {
+  return n == 256 ? 128 : n == 512 ? (df ? 256 : 192) : kMaxThreads;
+}
 // Values per thread of the flux pass's transforms: FP32 at N <= 256 uses radix 16 (measured
 // faster at 64^3 and 256^3); larger FP32 grids and FP64 use radix 8.
 template <int N, typename C>
 constexpr int flux_vpt() { return sizeof(C) == 8 && N <= 256 ? 16 : 8; }
 template <int N, typename C>
 constexpr int flux_threads() {
-  return threads_for(tpp_for<N, flux_vpt<N, C>()>(), 12 * pairs_for(N), flux_max_threads(N));
+  return threads_for(tpp_for<N, flux_vpt<N, C>()>(), 12 * pairs_for(N),
+                     flux_max_threads(N, std::is_same<C, cdf>::value));
 }
 // Blocks per SM the register allocation is sized for: about 170 registers a thread in FP64, 85 in
 // FP32 with radix 8 and 128 with radix 16 (its 16 values per thread).
 template <int N, typename C>
 constexpr int flux_min_blocks() {
-  const int budget = sizeof(C) == 8 ? (flux_vpt<N, C>() == 16 ? 512 : 768) : 384;
+  const int budget = sizeof(C) == 8 ? (flux_vpt<N, C>() == 16 ? 512 : 768)
+                                    : (N == 512 && std::is_same<C, cdf>::value ? 512 : 384);
   const int b = budget / flux_threads<N, C>();
   return b < 1 ? 1 : b;
 }
