@@ -184,6 +184,39 @@ __device__ __forceinline__ void dft8(cdf *v) {
   }
 }
 
+// The same with inputs 3 and 4 known zeros (the zero-padded first stage): the first layer's
+// pairs (v0, v4) and (v3, v7) need no arithmetic, (v0, v0) and (v7, -v7).  The other inputs
+// take the operations of dft8, so the results are dft8's.
+template <int DIR>
+__device__ __forceinline__ void dft8_zp(cdf *v) {
+  constexpr dfr h = dfr_const(0.70710678118654752440);
+  cdf b[4], c[4];
+  b[0] = v[0];
+  c[0] = v[0];
+  b[3] = v[7];
+  c[3] = cdf{-v[7].re, -v[7].im};
+#pragma unroll
+  for (int j = 1; j < 3; ++j) {
+    b[j] = c_add(v[j], v[j + 4]);
+    c[j] = c_sub(v[j], v[j + 4]);
+  }
+  if constexpr (DIR > 0) {
+    c[1] = cdf{h * (c[1].re - c[1].im), h * (c[1].im + c[1].re)};
+    c[3] = cdf{h * (-c[3].re - c[3].im), h * (c[3].re - c[3].im)};
+  } else {
+    c[1] = cdf{h * (c[1].re + c[1].im), h * (c[1].im - c[1].re)};
+    c[3] = cdf{h * (c[3].im - c[3].re), h * (-c[3].im - c[3].re)};
+  }
+  c[2] = c_mul_i<DIR>(c[2]);
+  dft4<DIR>(b);
+  dft4<DIR>(c);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v[2 * m] = b[m];
+    v[2 * m + 1] = c[m];
+  }
+}
+
 template <int R, int DIR, typename C>
 __device__ __forceinline__ void dft_small(C *v) {
   if constexpr (R == 16) dft16<DIR>(v);
@@ -402,15 +435,12 @@ __device__ __forceinline__ void dft8_first_fma(C *v) {
   v[0] = x0; v[1] = x1; v[2] = x2; v[3] = x3; v[4] = x4; v[5] = x5; v[6] = x6; v[7] = x7;
 }
 
-// The first radix-8 stage in double-float: the plain length-8 DFT (inputs 3 and 4 are zeros
-// when the pencil is zero-padded and were not loaded).
+// The first radix-8 stage in double-float: the plain length-8 DFT, or with the zero-padded
+// pencil's inputs 3 and 4 (not loaded) left out of the arithmetic.
 template <int DIR, bool ZP>
 __device__ __forceinline__ void dft8_first_fma(cdf *v) {
-  if constexpr (ZP) {
-    v[3] = cdf{{0.f, 0.f}, {0.f, 0.f}};
-    v[4] = cdf{{0.f, 0.f}, {0.f, 0.f}};
-  }
-  dft8<DIR>(v);
+  if constexpr (ZP) dft8_zp<DIR>(v);
+  else dft8<DIR>(v);
 }
 
 // ---- values per thread ----

@@ -79,20 +79,32 @@ __device__ __forceinline__ void col_fft_tile(const CI *__restrict__ in, CO *__re
   }
 }
 
-// Double-float forward passes: 4 blocks of 256 threads per SM (64 registers a thread) measured
-// 8 % faster at 512^3 than the 3 that 72 registers allow; the inverse passes measured slower so.
-template <typename CC, int DIR>
-constexpr int col_lb_threads() { return std::is_same<CC, cdf>::value && DIR < 0 ? 256 : 1024; }
-template <typename CC, int DIR>
-constexpr int col_lb_blocks() { return std::is_same<CC, cdf>::value && DIR < 0 ? 4 : 1; }
-
 template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
-__global__ void __launch_bounds__((col_lb_threads<CC, DIR>()), (col_lb_blocks<CC, DIR>()))
-    col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
+__global__ void col_fft_kernel(const CI *__restrict__ in, CO *__restrict__ out, int ntiles, int tsh,
                                int cols, typename scale_of<CC>::type scale, const CC *__restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   col_fft_tile<N, DIR, CI, CO, CC, VPT>(in, out, blockIdx.x, ntiles, tsh, cols, scale, tw,
                                         reinterpret_cast<CC *>(smem_raw));
+}
+
+// Double-float forward passes: the same tile with 4 blocks of 256 threads per SM (64 registers a
+// thread), which measured 8 % faster at 512^3 than the 3 blocks that 72 registers allow (the
+// inverse passes measured slower so and keep col_fft_kernel).
+template <int N, int DIR, typename CI, typename CO, typename CC, int VPT>
+__global__ void __launch_bounds__(256, 4) col_fft_kernel_b4(const CI *__restrict__ in, CO *__restrict__ out,
+                                                           int ntiles, int tsh, int cols,
+                                                           typename scale_of<CC>::type scale,
+                                                           const CC *__restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  col_fft_tile<N, DIR, CI, CO, CC, VPT>(in, out, blockIdx.x, ntiles, tsh, cols, scale, tw,
+                                        reinterpret_cast<CC *>(smem_raw));
+}
+
+// The kernel a pass launches.
+template <int N, int DIR, typename CI, typename CO, int VPT>
+constexpr auto col_kernel() {
+  if constexpr (std::is_same<CO, cdf>::value && DIR < 0) return col_fft_kernel_b4<N, DIR, CI, CO, CO, VPT>;
+  else return col_fft_kernel<N, DIR, CI, CO, CO, VPT>;
 }
 
 // The same pass as a persistent kernel: a grid of (SMs x resident blocks) takes tiles from the
@@ -149,7 +161,7 @@ int col_max_threads() {
   static int cached = 0;
   if (cached == 0) {
     cudaFuncAttributes a;
-    cached = cudaFuncGetAttributes(&a, col_fft_kernel<N, DIR, CI, CO, CO, VPT>) == cudaSuccess ? a.maxThreadsPerBlock
+    cached = cudaFuncGetAttributes(&a, col_kernel<N, DIR, CI, CO, VPT>()) == cudaSuccess ? a.maxThreadsPerBlock
                                                                                                : 256;
   }
   return cached;
@@ -211,10 +223,10 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
     return cudaGetLastError();
   }
   if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem<col_fft_kernel<N, DIR, CI, CO, CO, VPT>>((int)smem);
+    cudaError_t e = ensure_smem<col_kernel<N, DIR, CI, CO, VPT>()>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  col_fft_kernel<N, DIR, CI, CO, CO, VPT><<<(unsigned)blocks, tc * TPP, smem, s>>>(
+  col_kernel<N, DIR, CI, CO, VPT>()<<<(unsigned)blocks, tc * TPP, smem, s>>>(
       in, out, ntiles, tsh, cols, (typename scale_of<CO>::type)scale, tw);
   return cudaGetLastError();
 }
