@@ -459,16 +459,27 @@ def run_ours(args, name, cfg):
                                mhd.MHD_OPT_RADIX_FWD_Z), tuned["radix"]):
                 mhd.mhd_set_option(ectx, opt, r)
 
+    phase = [0.0, 0.0, 0.0]  # host wall time in set_state, step (to completion), get_state
+
     def e2e_step():
+        t0 = time.perf_counter()
         for i in range(batch):
             h = hs[i % len(hs)]
             assert lib.mhd_set_state(ectx.handle, i, h[0].ctypes.data, h[1].ctypes.data, h[2].ctypes.data, 0) == 0
+        t1 = time.perf_counter()
         assert lib.mhd_step(ectx.handle, 1) == 0
+        torch.cuda.synchronize()  # get_state would wait for the step anyway; this splits the phases
+        t2 = time.perf_counter()
         for i in range(batch):
             o = outs[i % len(outs)]
             assert lib.mhd_get_state(ectx.handle, i, o[0].ctypes.data, o[1].ctypes.data, o[2].ctypes.data, 0) == 0
+        t3 = time.perf_counter()
+        phase[0] += t1 - t0
+        phase[1] += t2 - t1
+        phase[2] += t3 - t2
 
     e2e_step()
+    phase[:] = [0.0, 0.0, 0.0]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -477,7 +488,8 @@ def run_ours(args, name, cfg):
         e2e_step()
     te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": world * pts * E / te, "unit": UNIT, "h2d_bytes_per_step": 7 * pts * 8,
-           "d2h_bytes_per_step": 7 * pts * 8, "steps": E}
+           "d2h_bytes_per_step": 7 * pts * 8, "steps": E,
+           "ms_per_step": {"set_state": phase[0] / E * 1e3, "step": phase[1] / E * 1e3, "get_state": phase[2] / E * 1e3}}
     mhd.mhd_destroy(ectx)
 
     # roofline of the dominant kernel (largest share of device time)
