@@ -478,7 +478,10 @@ def run_ours(args, name, cfg):
         phase[1] += t2 - t1
         phase[2] += t3 - t2
 
-    e2e_step()
+    # the first host transfers of fresh pinned buffers are several times slower (measured 140-780
+    # ms for a 512^3 set_state against 41 ms after): three untimed steps
+    for _ in range(3):
+        e2e_step()
     phase[:] = [0.0, 0.0, 0.0]
     if dist:
         dist.barrier()
