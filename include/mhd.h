@@ -160,6 +160,16 @@ MHD_API mhd_status mhd_set_state(mhd_ctx *ctx, int32_t inst, const double *rho, 
 MHD_API mhd_status mhd_get_state(mhd_ctx *ctx, int32_t inst, double *rho, double *m, double *b,
                          int32_t on_device);
 
+/* The same as mhd_get_state into HOST buffers (page-locked ones reach the link's rate), but
+ * returning once the transforms and copies are queued: the copies run on a stream of their own,
+ * so they overlap whatever the context queues next (a following mhd_set_state's host-to-device
+ * copies, for instance).  The buffers must stay valid and unread until mhd_synchronize returns
+ * (mhd_get_state and mhd_destroy also wait for them).  The first call allocates a staging pair
+ * of 14 x dz N^2 doubles (dz = N/8 z-planes, fewer if that exceeds 1/16 of the context's
+ * footprint), kept until mhd_destroy.  Errors: MHD_EINVAL (bad instance, null buffer),
+ * MHD_ENOMEM (staging), MHD_ECUDA. */
+MHD_API mhd_status mhd_get_state_async(mhd_ctx *ctx, int32_t inst, double *rho, double *m, double *b);
+
 /* Real-space right-hand side of instance `inst` at its current state (the inverse transform of
  * the dealiased RHS spectra): d rho/dt (N^3), d m/dt (3 N^3), d B/dt (3 N^3).  The state, the
  * history and the time are unchanged.  Synchronises. */

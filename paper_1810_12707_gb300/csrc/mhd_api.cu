@@ -82,6 +82,12 @@ struct mhd_ctx {
   // host-pointer set/get: a copy stream and the events that hand staging slots between streams
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  // mhd_get_state_async: its own staging pair (allocated on first use), copy stream and events,
+  // so that its device-to-host copies overlap whatever the context queues next
+  cudaStream_t out_stream = nullptr;
+  cudaEvent_t ev_ofull[2] = {nullptr, nullptr}, ev_ofree[2] = {nullptr, nullptr}, ev_out_done = nullptr;
+  double *oslots = nullptr;
+  int odz = 0;
   cudaGraphExec_t graph_exec = nullptr;
   // serving pools: only the first `live` instances are stepped (-1: all), one graph per count
   int live = -1;
@@ -303,11 +309,14 @@ void mhd_destroy(mhd_ctx *ctx) {
   {
     DeviceGuard g(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->out_stream) cudaStreamSynchronize(ctx->out_stream);  // copies into the caller's buffers
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-    for (cudaEvent_t e : {ctx->ev_start, ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1]})
+    if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
+    for (cudaEvent_t e : {ctx->ev_start, ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1],
+                          ctx->ev_ofull[0], ctx->ev_ofull[1], ctx->ev_ofree[0], ctx->ev_ofree[1], ctx->ev_out_done})
       if (e) cudaEventDestroy(e);
     free_all(ctx);
   }
@@ -490,45 +499,106 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
   return MHD_OK;
 }
 
-// Truncated FP64 spectra `src` of one instance -> host rho, m, B.  MHD_EINVAL (nothing queued)
-// when no staging plan fits.
+// Staging of a device-to-host transfer: two slots of 7 x dz N^2 doubles, the stream that copies
+// out of them and the events that hand them between that stream and the context's stream.
+struct Staging {
+  int dz;
+  double *slot[2];
+  cudaStream_t cs;
+  cudaEvent_t *full, *free;
+};
+
+// The staging of mhd_get_state_async: a pair of its own (N/8 z-planes a slot when that fits in a
+// sixteenth of the context's footprint, fewer otherwise), allocated on first use.
+mhd_status async_staging(mhd_ctx *c, Staging *sg) {
+  const size_t n = c->d.n, nn = n * n;
+  if (!c->out_stream) {
+    CK(cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&c->ev_ofull[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_ofree[i], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&c->ev_out_done, cudaEventDisableTiming));
+  }
+  if (!c->oslots) {
+    int dz = (int)(n / 8);
+    const size_t cap = footprint(c->d, c->precision) / 16;
+    while (dz > 1 && (size_t)14 * dz * nn * sizeof(double) > cap) dz /= 2;
+    c->oslots = static_cast<double *>(dalloc(c, (size_t)14 * dz * nn * sizeof(double)));
+    if (!c->oslots) return fail(c, MHD_ENOMEM, "get_state_async: staging of %zu bytes",
+                                (size_t)14 * dz * nn * sizeof(double));
+    c->odz = dz;
+  }
+  sg->dz = c->odz;
+  sg->slot[0] = c->oslots;
+  sg->slot[1] = c->oslots + (size_t)7 * c->odz * nn;
+  sg->cs = c->out_stream;
+  sg->full = c->ev_ofull;
+  sg->free = c->ev_ofree;
+  return MHD_OK;
+}
+
+// Truncated spectra `src` of one instance -> host rho, m, B through the staging `sg`.  `wait`:
+// return once the copies have landed; otherwise the copies are still in flight on sg.cs when it
+// returns (ev_out_done marks their end).
 template <typename C>
-mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, double *m, double *b) {
-  SlabPlan pl;
-  if (!slab_plan(c, &pl)) return MHD_EINVAL;
-  mhd_status st = ensure_copy_stream(c);
-  if (st) return st;
+mhd_status get_state_staged(mhd_ctx *c, const C *src, const C *tw, double *rho, double *m, double *b,
+                            const Staging &sg, bool wait) {
   const mhd::Dims &d = c->d;
   const mhd::Dims d1 = one(c);
   const int n = d.n;
   const size_t nn = (size_t)n * n, n3 = nn * n;
   C *w1 = reinterpret_cast<C *>(c->W1), *w2 = reinterpret_cast<C *>(c->W2);
-  cudaError_t e = mhd::launch_col_inverse(src, w1, n, 7, d.nk * d.nx, tw, c->stream);  // z pass
+  cudaError_t e = cudaSuccess;
+  // the slots' previous copies (an earlier asynchronous get) end before they are written again
+  if (!wait && c->ev_out_done) e = cudaStreamWaitEvent(c->stream, c->ev_out_done, 0);
+  if (e == cudaSuccess) e = mhd::launch_col_inverse(src, w1, n, 7, d.nk * d.nx, tw, c->stream);  // z pass
   int i = 0;
-  for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
-    const int dzc = std::min(pl.dz, n - z0), k = i & 1;
-    double *slot = pl.slot[k];
+  for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += sg.dz, ++i) {
+    const int dzc = std::min(sg.dz, n - z0), k = i & 1;
+    double *slot = sg.slot[k];
     const size_t off = (size_t)z0 * nn, cnt = (size_t)dzc * nn;
-    if (i >= 2) e = cudaStreamWaitEvent(c->stream, c->ev_free[k], 0);  // slot copied out
+    if (i >= 2) e = cudaStreamWaitEvent(c->stream, sg.free[k], 0);  // slot copied out
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
       e = mhd::launch_col_inverse(w1 + slab0 * d.nk * d.nx, w2 + slab0 * n * d.nx, n, dzc, d.nx, tw, c->stream);
     }
     if (e == cudaSuccess)
       e = mhd::launch_get_x_rows(w2, slot, 7, d1, tw, c->stream, (size_t)z0 * n, (size_t)dzc * n, cnt);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_full[k], c->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_full[k], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(sg.full[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sg.cs, sg.full[k], 0);
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       double *dst = f == 0 ? rho + off : f < 4 ? m + (f - 1) * n3 + off : b + (f - 4) * n3 + off;
-      e = cudaMemcpyAsync(dst, slot + f * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream);
+      e = cudaMemcpyAsync(dst, slot + f * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost, sg.cs);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_free[k], c->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sg.free[k], sg.cs);
   }
-  const cudaError_t e2 = cudaStreamSynchronize(c->copy_stream);
+  if (!wait) {
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out_done, sg.cs);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(sg.cs);
+      return fail(c, MHD_ECUDA, "get_state_async: %s", cudaGetErrorString(e));
+    }
+    return MHD_OK;
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(sg.cs);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, MHD_ECUDA, "get_state: %s", cudaGetErrorString(e));
   return MHD_OK;
+}
+
+// Truncated spectra `src` of one instance -> host rho, m, B through the staging slots in W1.
+// MHD_EINVAL (nothing queued) when no staging plan fits.
+template <typename C>
+mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, double *m, double *b) {
+  SlabPlan pl;
+  if (!slab_plan(c, &pl)) return MHD_EINVAL;
+  mhd_status st = ensure_copy_stream(c);
+  if (st) return st;
+  if (c->out_stream) CK(cudaStreamSynchronize(c->out_stream));  // an earlier asynchronous get
+  const Staging sg = {pl.dz, {pl.slot[0], pl.slot[1]}, c->copy_stream, c->ev_full, c->ev_free};
+  return get_state_staged(c, src, tw, rho, m, b, sg, true);
 }
 
 }  // namespace
@@ -626,6 +696,19 @@ mhd_status mhd_get_state(mhd_ctx *c, int32_t inst, double *rho, double *m, doubl
   if ((st = state_fp64(c, inst, &src))) return st;
   if (!on_device && (st = get_state_host(c, src, c->tw, rho, m, b)) != MHD_EINVAL) return st;
   return spectra_to_real(c, src, rho, m, b, on_device);
+}
+
+mhd_status mhd_get_state_async(mhd_ctx *c, int32_t inst, double *rho, double *m, double *b) {
+  mhd_status st = check_inst(c, inst);
+  if (st) return st;
+  if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
+  DeviceGuard g(c);
+  Staging sg;
+  if ((st = async_staging(c, &sg))) return st;
+  if (c->precision == MHD_FP64_DF) return get_state_staged(c, statedf(c, inst), c->twdf, rho, m, b, sg, false);
+  const cplx64 *src = nullptr;
+  if ((st = state_fp64(c, inst, &src))) return st;
+  return get_state_staged(c, src, c->tw, rho, m, b, sg, false);
 }
 
 mhd_status mhd_get_spectrum(mhd_ctx *c, int32_t inst, int32_t field, double *out, int32_t on_device) {
@@ -1127,6 +1210,7 @@ mhd_status mhd_synchronize(mhd_ctx *c) {
   CK(cudaMemcpyAsync(&any, c->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (c->out_stream) CK(cudaStreamSynchronize(c->out_stream));  // mhd_get_state_async copies
   if (err == 1) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up (its copies were drained)");
   if (err) return fail(c, MHD_ETIMEOUT, "a device-side wait gave up and a copy did not complete in the drain");
   return any ? MHD_ENONFINITE : MHD_OK;

@@ -37,7 +37,8 @@ EXPORTS = ("mhd_footprint_bytes", "mhd_init", "mhd_destroy", "mhd_last_error", "
            "mhd_profile_read", "mhd_rhs_noalloc", "mhd_set_option", "mhd_pool_create", "mhd_pool_destroy",
            "mhd_pool_last_error", "mhd_pool_admit", "mhd_pool_step", "mhd_pool_progress",
            "mhd_pool_diagnostics", "mhd_pool_retire", "mhd_pool_info", "mhd_set_forcing", "mhd_num_shells",
-           "mhd_spectra", "mhd_tracers_set", "mhd_tracers_get", "mhd_tracers_count", "mhd_autotune")
+           "mhd_spectra", "mhd_tracers_set", "mhd_tracers_get", "mhd_tracers_count", "mhd_autotune",
+           "mhd_get_state_async")
 
 
 class MhdError(RuntimeError):
@@ -106,6 +107,8 @@ def load_library(path: str = LIBRARY):
         fn = getattr(lib, name)
         fn.restype = I32
         fn.argtypes = [P, I32, P, P, P, I32]
+    lib.mhd_get_state_async.restype = I32
+    lib.mhd_get_state_async.argtypes = [P, I32, P, P, P]
     lib.mhd_get_spectrum.restype = I32
     lib.mhd_get_spectrum.argtypes = [P, I32, I32, P, I32]
     lib.mhd_step.restype = I32
@@ -299,6 +302,19 @@ def _three_fields(ctx, fn, inst, device):
 def mhd_get_state(ctx: Context, inst: int = 0, device: bool = False):
     """(rho, m, B) of one instance in real space."""
     return _three_fields(ctx, load_library().mhd_get_state, inst, device)
+
+
+def mhd_get_state_async(ctx: Context, inst: int, rho: np.ndarray, m: np.ndarray, b: np.ndarray) -> None:
+    """Queue the transfer of (rho, m, B) of one instance into host arrays of shapes (N,N,N),
+    (3,N,N,N), (3,N,N,N), float64, C-contiguous (page-locked ones reach the link's rate); they are
+    filled once mhd_synchronize returns and must stay alive until then."""
+    n = ctx.n
+    for a, shape in ((rho, (n, n, n)), (m, (3, n, n, n)), (b, (3, n, n, n))):
+        if not (isinstance(a, np.ndarray) and a.shape == shape and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.flags.writeable):
+            raise ValueError(f"need a writeable C-contiguous float64 host array of shape {shape}")
+    _check(ctx, load_library().mhd_get_state_async(ctx.handle, int(inst), rho.ctypes.data, m.ctypes.data,
+                                                   b.ctypes.data))
 
 
 def mhd_rhs(ctx: Context, inst: int = 0, device: bool = False):
