@@ -81,13 +81,18 @@ struct mhd_ctx {
   cudaStream_t cap_stream = nullptr;
   // host-pointer set/get: a copy stream and the events that hand staging slots between streams
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // mhd_get_state_async: its own staging pair (allocated on first use), copy stream and events,
   // so that its device-to-host copies overlap whatever the context queues next
   cudaStream_t out_stream = nullptr;
   cudaEvent_t ev_ofull[2] = {nullptr, nullptr}, ev_ofree[2] = {nullptr, nullptr}, ev_out_done = nullptr;
   double *oslots = nullptr;
   int odz = 0;
+  // recorded on the stream at the end of every entry point but mhd_get_state_async (which leaves
+  // W1 behind the y-pass output alone): a host set_state's copies into its W1 slots wait for it
+  // only, not for a transfer out queued after it
+  cudaEvent_t ev_slots = nullptr;
+  bool slots_untouched = false;  // set by mhd_get_state_async for the guard's destructor
   cudaGraphExec_t graph_exec = nullptr;
   // serving pools: only the first `live` instances are stepped (-1: all), one graph per count
   int live = -1;
@@ -136,12 +141,21 @@ struct DeviceGuard {
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
   }
-  // every entry point that may touch a context's buffers counts itself here
-  explicit DeviceGuard(mhd_ctx *c) : DeviceGuard(c->device) { ++c->api_calls; }
+  // every entry point that may touch a context's buffers counts itself here, and marks on its
+  // stream where its use of the staging slots in W1 ends
+  explicit DeviceGuard(mhd_ctx *c) : DeviceGuard(c->device) {
+    ctx = c;
+    ++c->api_calls;
+  }
   ~DeviceGuard() {
+    if (ctx) {
+      if (!ctx->slots_untouched && ctx->ev_slots && ctx->stream) cudaEventRecord(ctx->ev_slots, ctx->stream);
+      ctx->slots_untouched = false;
+    }
     int cur = -1;
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
+  mhd_ctx *ctx = nullptr;
 };
 
 bool valid_n(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
@@ -308,6 +322,7 @@ void mhd_destroy(mhd_ctx *ctx) {
   if (!ctx) return;
   {
     DeviceGuard g(ctx);
+    g.ctx = nullptr;  // no mark: the context goes
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->out_stream) cudaStreamSynchronize(ctx->out_stream);  // copies into the caller's buffers
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -315,8 +330,9 @@ void mhd_destroy(mhd_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
-    for (cudaEvent_t e : {ctx->ev_start, ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1],
-                          ctx->ev_ofull[0], ctx->ev_ofull[1], ctx->ev_ofree[0], ctx->ev_ofree[1], ctx->ev_out_done})
+    for (cudaEvent_t e : {ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1],
+                          ctx->ev_ofull[0], ctx->ev_ofull[1], ctx->ev_ofree[0], ctx->ev_ofree[1], ctx->ev_out_done,
+                          ctx->ev_slots})
       if (e) cudaEventDestroy(e);
     free_all(ctx);
   }
@@ -402,8 +418,11 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->smax_bits, 0, 2 * p->batch * sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->work_ctr, 0, 16 * sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_slots, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_slots, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
+    if (c->ev_slots) cudaEventDestroy(c->ev_slots);
     free_all(c);
     delete c;
     return MHD_ECUDA;
@@ -443,7 +462,6 @@ bool slab_plan(mhd_ctx *c, SlabPlan *pl) {
 mhd_status ensure_copy_stream(mhd_ctx *c) {
   if (c->copy_stream) return MHD_OK;
   CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-  CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
     CK(cudaEventCreateWithFlags(&c->ev_full[i], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
@@ -465,8 +483,9 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
   const mhd::Dims d1 = one(c);
   const int n = d.n;
   const size_t nn = (size_t)n * n, n3 = nn * n;
-  cudaError_t e = cudaEventRecord(c->ev_start, c->stream);  // the staging slots are free from here
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0);
+  // the staging slots are free once the last entry point that used W1 there has finished; a
+  // transfer out queued since (mhd_get_state_async) does not hold the copies in
+  cudaError_t e = cudaStreamWaitEvent(c->copy_stream, c->ev_slots, 0);
   int i = 0;
   for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
     const int dzc = std::min(pl.dz, n - z0), k = i & 1;
@@ -703,6 +722,7 @@ mhd_status mhd_get_state_async(mhd_ctx *c, int32_t inst, double *rho, double *m,
   if (st) return st;
   if (!rho || !m || !b) return fail(c, MHD_EINVAL, "null output");
   DeviceGuard g(c);
+  c->slots_untouched = true;  // this transfer leaves W1 behind the y-pass output alone
   Staging sg;
   if ((st = async_staging(c, &sg))) return st;
   if (c->precision == MHD_FP64_DF) return get_state_staged(c, statedf(c, inst), c->twdf, rho, m, b, sg, false);

@@ -103,3 +103,29 @@ def test_async_get_checks_its_arguments(lib):
     with pytest.raises(ValueError):
         lib.mhd_get_state_async(ctx, 0, np.zeros((16, 16, 15)), good[1], good[2])
     lib.mhd_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_host_set_waits_for_queued_steps(lib, precision):
+    """A host set_state's copies into its staging slots in W1 wait for the steps queued before it
+    (which use all of W1), though not for a transfer out queued after them."""
+    n = 64
+    ics = _ics(n, 2, seed=100)
+    other = _ics(n, 1, seed=110)[0]
+
+    def run(sync_between):
+        ctx = _ctx(lib, n, ics, precision)
+        lib.mhd_step(ctx, 3)
+        out = _bufs(n, pinned=True)
+        lib.mhd_get_state_async(ctx, 0, *out)
+        if sync_between:
+            assert lib.mhd_synchronize(ctx) == lib.MHD_OK
+        lib.mhd_set_state(ctx, 1, other.rho, other.u, other.b)
+        lib.mhd_step(ctx, 2)
+        assert lib.mhd_synchronize(ctx) == lib.MHD_OK
+        res = [a.copy() for a in out] + [a for i in range(2) for a in lib.mhd_get_state(ctx, i)]
+        lib.mhd_destroy(ctx)
+        return res
+
+    for a, b in zip(run(False), run(True)):
+        assert np.array_equal(a, b)
