@@ -149,7 +149,8 @@ struct DeviceGuard {
   }
   ~DeviceGuard() {
     if (ctx) {
-      if (!ctx->slots_untouched && ctx->ev_slots && ctx->stream) cudaEventRecord(ctx->ev_slots, ctx->stream);
+      // (the stream may be 0, the legacy default stream)
+      if (!ctx->slots_untouched && ctx->ev_slots) cudaEventRecord(ctx->ev_slots, ctx->stream);
       ctx->slots_untouched = false;
     }
     int cur = -1;
@@ -323,7 +324,7 @@ void mhd_destroy(mhd_ctx *ctx) {
   {
     DeviceGuard g(ctx);
     g.ctx = nullptr;  // no mark: the context goes
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->stream);  // 0 is the legacy default stream
     if (ctx->out_stream) cudaStreamSynchronize(ctx->out_stream);  // copies into the caller's buffers
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     drop_graphs(ctx);
