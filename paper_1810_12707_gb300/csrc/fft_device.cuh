@@ -234,6 +234,14 @@ __device__ __forceinline__ cdf tw_load(const cdf *p) {
                : "l"(p));
   return v;
 }
+// The same from a generic address (a twiddle table a block has staged in shared memory).
+__device__ __forceinline__ cdf tw_load_generic(const cdf *p) {
+  cdf v;
+  asm volatile("ld.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.re.hi), "=f"(v.re.lo), "=f"(v.im.hi), "=f"(v.im.lo)
+               : "l"(p));
+  return v;
+}
 __device__ __forceinline__ cplx64 tw_load(const cplx64 *p) {
   cplx64 v;
   asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.re), "=d"(v.im) : "l"(p));
@@ -470,7 +478,8 @@ __host__ __device__ constexpr int fft_tpp() { return tpp_for<N, fft_vpt<C>()>();
 // Every thread of the block must call this (it contains group barriers); threads with
 // `active == false` only take part in the barriers.  The caller separates the transform from the
 // preceding writes and the following reads of the pencil with a block barrier.
-template <int N, int DIR, int NS, typename C, int VPT, bool ZP>
+// TWG: `tw` may point to shared memory (generic twiddle loads; double-float only).
+template <int N, int DIR, int NS, typename C, int VPT, bool ZP, bool TWG = false>
 __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, const C *__restrict__ tw) {
   if constexpr (NS < N) {
     static_assert(VPT == 8 || (VPT == 16 && sizeof(C) == 8), "radix 16 is an FP32 option");
@@ -502,7 +511,9 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
           if (kFirst16 && r >= 6 && r <= 9) continue;
           C x = buf[sm_idx<C>(j + r * (N / R))];
           if (!kFma && NS > 1 && r > 0) {
-            const C w = tw_load(tw + r * k * TWSTEP);
+            C w;
+            if constexpr (TWG) w = tw_load_generic(tw + r * k * TWSTEP);
+            else w = tw_load(tw + r * k * TWSTEP);
             x = DIR < 0 ? c_mul(x, w) : c_mulc(x, w);
           }
           v[b * R + r] = x;
@@ -531,7 +542,7 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
       }
     }
     group_sync<TPP>();
-    stockham_stages<N, DIR, NS * R, C, VPT, false>(buf, t, active, tw);
+    stockham_stages<N, DIR, NS * R, C, VPT, false, TWG>(buf, t, active, tw);
   }
 }
 
@@ -539,9 +550,9 @@ __device__ __forceinline__ void stockham_stages(C *buf, int t, bool active, cons
 // zero-padded by the 2/3 rule (elements K+1 .. N-K-1 are zero, K = (N-1)/3), as every inverse
 // transform of a truncated spectrum is; the FP64 first stage then skips the inputs it knows are
 // zero (they need not even be written).
-template <int N, int DIR, typename C, int VPT = fft_vpt<C>(), bool ZP = false>
+template <int N, int DIR, typename C, int VPT = fft_vpt<C>(), bool ZP = false, bool TWG = false>
 __device__ __forceinline__ void pencil_fft(C *buf, int t, bool active, const C *__restrict__ tw) {
-  stockham_stages<N, DIR, 1, C, VPT, ZP>(buf, t, active, tw);
+  stockham_stages<N, DIR, 1, C, VPT, ZP, TWG>(buf, t, active, tw);
 }
 
 // FFT index of kept index j (0..2K) along a truncated axis: j for j <= K, else j - (2K+1) + N.

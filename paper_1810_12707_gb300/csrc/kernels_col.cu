@@ -17,6 +17,14 @@
 
 namespace mhd {
 
+// Double-float passes at N >= 512 stage the twiddle table (N values, 8 KB at 512) in shared
+// memory behind the tile: 4-6 % faster per pass at 512^3 than 16-byte L1 loads per butterfly
+// element; at 256^3 the copy per block cost more than it saved.
+template <typename CC, int N>
+constexpr bool tws_staged() { return std::is_same<CC, cdf>::value && N >= 512; }
+template <typename CC, int N>
+constexpr size_t tws_bytes() { return tws_staged<CC, N>() ? (size_t)N * sizeof(CC) : 0; }
+
 // CI, CO: element types in and out; CC: type of the transform arithmetic (= the output's).
 // A block has TC = 2^tsh columns and TC * N/VPT threads: thread (l0, c) = (tid >> tsh, tid & (TC-1))
 // moves rows l0, l0 + N/VPT, ... of column c, so consecutive threads touch consecutive columns of a
@@ -61,12 +69,20 @@ __device__ __forceinline__ void col_fft_tile(const CI *__restrict__ in, CO *__re
     // FFT indices K+1 .. N-K-1 are outside the kept set
     for (int l = l0; l < N - NK; l += TPP) pen[sm_idx<CC>(K + 1 + l)] = CC{0, 0};
   }
+  // double-float at N >= 512: the twiddle table staged in shared memory behind the pencils
+  constexpr bool kTws = tws_staged<CC, N>();
+  const CC *twp = tw;
+  if constexpr (kTws) {
+    CC *tws = sm + tc * P;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = tw[i];
+    twp = tws;
+  }
   __syncthreads();
 
   const int pencil = threadIdx.x / TPP;
   const int t = threadIdx.x - pencil * TPP;
   const bool active = pencil < tc && tile * tc + pencil < cols;
-  pencil_fft<N, DIR, CC, VPT, (DIR > 0)>(sm + (active ? pencil : 0) * P, t, active, tw);  // inverse: zero-padded
+  pencil_fft<N, DIR, CC, VPT, (DIR > 0), kTws>(sm + (active ? pencil : 0) * P, t, active, twp);  // inverse: zero-padded
   __syncthreads();  // the store loop reads every pencil
 
   if (col_ok) {
@@ -206,7 +222,7 @@ cudaError_t launch_col_v(const CI *in, CO *out, int nslab, int cols, double scal
   const int tsh = floor_log2(tc);  // a requested width that is not a power of two is rounded down
   tc = 1 << tsh;
   const int ntiles = (cols + tc - 1) / tc;
-  const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO);
+  const size_t smem = (size_t)tc * pencil_pitch<CO>(N) * sizeof(CO) + tws_bytes<CO, N>();
   const long long blocks = (long long)nslab * ntiles;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
