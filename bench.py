@@ -197,13 +197,13 @@ TRAFFIC = {
                                  "ncu --set full, profiles/ncu_flux_x_abc256_fp64.md"),
     ("flux_x", 256, 1, "fp32"): (315_693_312 + 489_866_752, "8098a458af43095a",
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
-    ("flux_x", 256, 1, "fp64df"): (631_945_984 + 1_028_301_312, "6a21fb829a8a5931",
-                                   "ncu dram__bytes metrics, profiles/ncu_df_kernels_abc256.md"),
+    ("flux_x", 256, 1, "fp64df"): (631_424_000 + 1_028_800_512, "76c413daf911ef3f",
+                                   "ncu --set full, profiles/ncu_df_kernels_abc256.md"),
     # the 512^3 launch (about 20 GB on the device) is larger than a full capture should be: the
     # 256^3 capture scaled by the units the launch processes (row pairs x kept kx, 7.953 times),
     # the flux pass's traffic being proportional to them (19 fields x rows x (K + 1) values)
-    ("flux_x", 512, 1, "fp64df"): (round((631_945_984 + 1_028_301_312) * (512 * 512 * 171) / (256 * 256 * 86)),
-                                   "6a21fb829a8a5931",
+    ("flux_x", 512, 1, "fp64df"): (round((631_424_000 + 1_028_800_512) * (512 * 512 * 171) / (256 * 256 * 86)),
+                                   "76c413daf911ef3f",
                                    "256^3 ncu capture scaled by row pairs x (K + 1), profiles/ncu_df_kernels_abc256.md"),
 }
 
