@@ -297,13 +297,13 @@ class Server:
             still = collections.deque()
             while waiting:
                 req = waiting.popleft()
-                verdict = self._place(req, stats)
-                if verdict == "admitted":
+                outcome = self._place(req, stats)
+                if outcome == "admitted":
                     stats.admitted_at[req.rid] = time.perf_counter() - t0
                     stats.queue_s.append(stats.admitted_at[req.rid] - req.arrival)
                     continue
                 still.append(req)
-                if verdict == "memory":
+                if outcome == "memory":
                     still.extend(waiting)
                     waiting.clear()
             waiting = still
