@@ -262,19 +262,14 @@ __device__ __forceinline__ int launder(int x) {
 }
 
 // ---- shared-memory pencil layout ----
-// The first Stockham stage writes with a stride of 8 elements; stored plainly, every lane of a
-// wavefront would hit the same banks.  8-byte elements: element e lives at e + e / 16, one pad
-// element per 128 bytes.  16-byte elements (a wavefront is 8 lanes of 128 bytes): e lives at
-// e ^ ((e / 8) mod 8), its 8-element group permuted by the group's index, so stride-8 lanes land
-// in 8 different bank quads while contiguous lanes stay in one group -- no pad, which leaves room
-// for a twiddle table beside the pencils.  Pencils are `pencil_pitch` apart, an odd number of
+// A pencil element e lives at sm_idx<C>(e) = e + e / (128 / sizeof(C)): one pad element per 128
+// bytes.  The first Stockham stage writes with a stride of 8 elements; without the pad every lane
+// of a wavefront would hit the same banks.  Pencils are `pencil_pitch` apart, an odd number of
 // elements, so that lanes walking across pencils (the column loads) also spread over the banks.
 template <typename C>
-__host__ __device__ constexpr int sm_idx(int e) {
-  return sizeof(C) == 16 ? (e ^ ((e >> 3) & 7)) : e + e / (int)(128 / sizeof(C));
-}
+__host__ __device__ constexpr int sm_idx(int e) { return e + e / (int)(128 / sizeof(C)); }
 template <typename C>
-__host__ __device__ constexpr int pencil_pitch(int n) { return sizeof(C) == 16 ? (n | 1) : (sm_idx<C>(n) | 1); }
+__host__ __device__ constexpr int pencil_pitch(int n) { return sm_idx<C>(n) | 1; }
 
 // ---- barrier of one pencil's thread group ----
 // A pencil is transformed by the TPP = N/VPT consecutive threads of its group and nobody else

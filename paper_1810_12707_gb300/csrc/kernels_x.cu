@@ -43,12 +43,6 @@ constexpr int threads_for(int tpp, int pencils, int max_threads = kMaxThreads) {
 constexpr int flux_max_threads(int n, bool df = false) {
   return n == 256 ? 128 : n == 512 ? (df ? 256 : 192) : kMaxThreads;
 }
-// The double-float flux pass at N >= 512 stages the twiddle table (N values) in shared memory
-// behind its pencils, as the column passes do.
-template <int N, typename C>
-constexpr bool flux_tws() { return std::is_same<C, cdf>::value && N >= 512; }
-template <int N, typename C>
-constexpr size_t flux_tws_bytes() { return flux_tws<N, C>() ? (size_t)N * sizeof(C) : 0; }
 // Values per thread of the flux pass's transforms: FP32 at N <= 256 uses radix 16 (measured
 // faster at 64^3 and 256^3); larger FP32 grids and FP64 use radix 8.
 template <int N, typename C>
@@ -73,8 +67,7 @@ constexpr int flux_min_blocks() {
 // so the stages synchronise per group; one block barrier closes the whole transform.
 // Every inverse (DIR = +1) transform here starts from a truncated half spectrum, so its pencil is
 // zero-padded by the 2/3 rule (see pencil_fft).
-// TWG: `tw` may point to shared memory (see pencil_fft).
-template <int N, int DIR, int VPT, bool TWG = false, typename Ptr, typename C>
+template <int N, int DIR, int VPT, typename Ptr, typename C>
 __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict__ tw) {
   constexpr int TPP = tpp_for<N, VPT>();
   const int G = blockDim.x / TPP;
@@ -82,7 +75,7 @@ __device__ __forceinline__ void fft_pencils(int np, Ptr ptr, const C *__restrict
   for (int base = 0; base < np; base += G) {
     const int id = base + g;
     const bool active = g < G && id < np;
-    pencil_fft<N, DIR, C, VPT, (DIR > 0), TWG>(ptr(active ? id : 0), t, active, tw);
+    pencil_fft<N, DIR, C, VPT, (DIR > 0)>(ptr(active ? id : 0), t, active, tw);
   }
   __syncthreads();  // the callers' next phase reads every pencil
 }
@@ -143,18 +136,10 @@ __device__ __forceinline__ void flux_x_item(const C *__restrict__ in, C *__restr
     const int f = r % 7, p = r / 7;
     sm[(p * 12 + f) * P + sm_idx<C>(KT + 1 + z)] = C{0, 0};
   }
-  constexpr bool kTws = flux_tws<N, C>();
-  const C *twp = tw;
-  if constexpr (kTws) {
-    C *tws = sm + 12 * PAIRS * P;
-    for (int i = threadIdx.x; i < N; i += nthr) tws[i] = tw[i];
-    twp = tws;
-  }
   __syncthreads();
 
   // 2. inverse transforms of the 7 fields
-  fft_pencils<N, +1, (flux_vpt<N, C>()), kTws>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; },
-                                               twp);
+  fft_pencils<N, +1, (flux_vpt<N, C>())>(7 * PAIRS, [&](int id) { return sm + ((id / 7) * 12 + id % 7) * P; }, tw);
 
   // 3. products on the grid (real part: row 0, imaginary part: row 1)
   constexpr bool kDF = std::is_same<C, cdf>::value;
@@ -291,7 +276,7 @@ __device__ __forceinline__ void flux_x_item(const C *__restrict__ in, C *__restr
   __syncthreads();
 
   // 4. forward transforms of the 12 products
-  fft_pencils<N, -1, (flux_vpt<N, C>()), kTws>(12 * PAIRS, [&](int id) { return sm + id * P; }, twp);
+  fft_pencils<N, -1, (flux_vpt<N, C>())>(12 * PAIRS, [&](int id) { return sm + id * P; }, tw);
 
   // 5. unpack and store the kept half spectra
   for (int q = threadIdx.x; q < 12 * PAIRS * NX; q += nthr) {
@@ -733,7 +718,7 @@ cudaError_t flux_n(const C *in, C *out, const PhysDev *phys, unsigned long long 
   }
   const int bpi = N * N / (2 * PAIRS);
   const int threads = flux_threads<N, C>();
-  const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C) + flux_tws_bytes<N, C>();
+  const size_t smem = (size_t)12 * PAIRS * pencil_pitch<C>(N) * sizeof(C);
   if (smem > 48 * 1024) {
     cudaError_t e = ensure_smem<flux_x_kernel<N, C>>((int)smem);
     if (e != cudaSuccess) return e;
