@@ -164,9 +164,10 @@ MHD_API mhd_status mhd_get_state(mhd_ctx *ctx, int32_t inst, double *rho, double
  * returning once the transforms and copies are queued: the copies run on a stream of their own,
  * so they overlap whatever the context queues next (a following mhd_set_state's host-to-device
  * copies, for instance).  The buffers must stay valid and unread until mhd_synchronize returns
- * (mhd_get_state and mhd_destroy also wait for them).  The first call allocates a staging pair
- * of 14 x dz N^2 doubles (dz = N/8 z-planes, fewer if that exceeds 1/16 of the context's
- * footprint), kept until mhd_destroy.  Errors: MHD_EINVAL (bad instance, null buffer),
+ * (mhd_get_state and mhd_destroy also wait for them).  The first call allocates its staging,
+ * kept until mhd_destroy: the whole state, 7 N^3 doubles (about 36 % of mhd_footprint_bytes of
+ * one instance), when that is at most half of mhd_footprint_bytes, else fewer slabs of N/8
+ * z-planes (at least two, then thinner ones).  Errors: MHD_EINVAL (bad instance, null buffer),
  * MHD_ENOMEM (staging), MHD_ECUDA. */
 MHD_API mhd_status mhd_get_state_async(mhd_ctx *ctx, int32_t inst, double *rho, double *m, double *b);
 

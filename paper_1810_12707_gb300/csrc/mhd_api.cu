@@ -85,9 +85,9 @@ struct mhd_ctx {
   // mhd_get_state_async: its own staging pair (allocated on first use), copy stream and events,
   // so that its device-to-host copies overlap whatever the context queues next
   cudaStream_t out_stream = nullptr;
-  cudaEvent_t ev_ofull[2] = {nullptr, nullptr}, ev_ofree[2] = {nullptr, nullptr}, ev_out_done = nullptr;
+  cudaEvent_t ev_ofull[8] = {}, ev_ofree[8] = {}, ev_out_done = nullptr;
   double *oslots = nullptr;
-  int odz = 0;
+  int odz = 0, ons = 0;
   // recorded on the stream at the end of every entry point but mhd_get_state_async (which leaves
   // W1 behind the y-pass output alone): a host set_state's copies into its W1 slots wait for it
   // only, not for a transfer out queued after it
@@ -331,10 +331,13 @@ void mhd_destroy(mhd_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
-    for (cudaEvent_t e : {ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1],
-                          ctx->ev_ofull[0], ctx->ev_ofull[1], ctx->ev_ofree[0], ctx->ev_ofree[1], ctx->ev_out_done,
+    for (cudaEvent_t e : {ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1], ctx->ev_out_done,
                           ctx->ev_slots})
       if (e) cudaEventDestroy(e);
+    for (int i = 0; i < 8; ++i) {
+      if (ctx->ev_ofull[i]) cudaEventDestroy(ctx->ev_ofull[i]);
+      if (ctx->ev_ofree[i]) cudaEventDestroy(ctx->ev_ofree[i]);
+    }
     free_all(ctx);
   }
   delete ctx;
@@ -523,35 +526,40 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
 // out of them and the events that hand them between that stream and the context's stream.
 struct Staging {
   int dz;
-  double *slot[2];
+  int ns;  // slots, 2..8, used in turn
+  double *slot[8];
   cudaStream_t cs;
   cudaEvent_t *full, *free;
 };
 
-// The staging of mhd_get_state_async: a pair of its own (N/8 z-planes a slot when that fits in a
-// sixteenth of the context's footprint, fewer otherwise), allocated on first use.
+// The staging of mhd_get_state_async, allocated on first use: slots of N/8 z-planes, as many as
+// there are slabs (8: the whole state, so that the transforms never wait for the copies out) when
+// that takes at most half the context's footprint (it takes about 36 % at every N), else fewer (at
+// least 2, then thinner slabs).
 mhd_status async_staging(mhd_ctx *c, Staging *sg) {
   const size_t n = c->d.n, nn = n * n;
   if (!c->out_stream) {
     CK(cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 8; ++i) {
       CK(cudaEventCreateWithFlags(&c->ev_ofull[i], cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&c->ev_ofree[i], cudaEventDisableTiming));
     }
     CK(cudaEventCreateWithFlags(&c->ev_out_done, cudaEventDisableTiming));
   }
   if (!c->oslots) {
-    int dz = (int)(n / 8);
-    const size_t cap = footprint(c->d, c->precision) / 16;
-    while (dz > 1 && (size_t)14 * dz * nn * sizeof(double) > cap) dz /= 2;
-    c->oslots = static_cast<double *>(dalloc(c, (size_t)14 * dz * nn * sizeof(double)));
-    if (!c->oslots) return fail(c, MHD_ENOMEM, "get_state_async: staging of %zu bytes",
-                                (size_t)14 * dz * nn * sizeof(double));
+    const size_t cap = footprint(c->d, c->precision) / 2;
+    int dz = (int)(n / 8), ns = 8;
+    while (ns > 2 && (size_t)7 * ns * dz * nn * sizeof(double) > cap) --ns;
+    while (dz > 1 && (size_t)7 * ns * dz * nn * sizeof(double) > cap) dz /= 2;
+    const size_t bytes = (size_t)7 * ns * dz * nn * sizeof(double);
+    c->oslots = static_cast<double *>(dalloc(c, bytes));
+    if (!c->oslots) return fail(c, MHD_ENOMEM, "get_state_async: staging of %zu bytes", bytes);
     c->odz = dz;
+    c->ons = ns;
   }
   sg->dz = c->odz;
-  sg->slot[0] = c->oslots;
-  sg->slot[1] = c->oslots + (size_t)7 * c->odz * nn;
+  sg->ns = c->ons;
+  for (int k = 0; k < c->ons; ++k) sg->slot[k] = c->oslots + (size_t)7 * k * c->odz * nn;
   sg->cs = c->out_stream;
   sg->full = c->ev_ofull;
   sg->free = c->ev_ofree;
@@ -575,10 +583,10 @@ mhd_status get_state_staged(mhd_ctx *c, const C *src, const C *tw, double *rho, 
   if (e == cudaSuccess) e = mhd::launch_col_inverse(src, w1, n, 7, d.nk * d.nx, tw, c->stream);  // z pass
   int i = 0;
   for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += sg.dz, ++i) {
-    const int dzc = std::min(sg.dz, n - z0), k = i & 1;
+    const int dzc = std::min(sg.dz, n - z0), k = i % sg.ns;
     double *slot = sg.slot[k];
     const size_t off = (size_t)z0 * nn, cnt = (size_t)dzc * nn;
-    if (i >= 2) e = cudaStreamWaitEvent(c->stream, sg.free[k], 0);  // slot copied out
+    if (i >= sg.ns) e = cudaStreamWaitEvent(c->stream, sg.free[k], 0);  // slot copied out
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       const size_t slab0 = (size_t)f * n + z0;  // y pass of these z-planes
       e = mhd::launch_col_inverse(w1 + slab0 * d.nk * d.nx, w2 + slab0 * n * d.nx, n, dzc, d.nx, tw, c->stream);
@@ -617,7 +625,7 @@ mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, do
   mhd_status st = ensure_copy_stream(c);
   if (st) return st;
   if (c->out_stream) CK(cudaStreamSynchronize(c->out_stream));  // an earlier asynchronous get
-  const Staging sg = {pl.dz, {pl.slot[0], pl.slot[1]}, c->copy_stream, c->ev_full, c->ev_free};
+  const Staging sg = {pl.dz, 2, {pl.slot[0], pl.slot[1]}, c->copy_stream, c->ev_full, c->ev_free};
   return get_state_staged(c, src, tw, rho, m, b, sg, true);
 }
 
