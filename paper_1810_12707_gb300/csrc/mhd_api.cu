@@ -82,8 +82,9 @@ struct mhd_ctx {
   // host-pointer set/get: a copy stream and the events that hand staging slots between streams
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  // mhd_get_state_async: its own staging pair (allocated on first use), copy stream and events,
-  // so that its device-to-host copies overlap whatever the context queues next
+  // mhd_get_state_async: its own staging (allocated on first use, `ons` slots of `odz`
+  // z-planes), copy stream and events, so that its device-to-host copies overlap whatever the
+  // context queues next
   cudaStream_t out_stream = nullptr;
   cudaEvent_t ev_ofull[8] = {}, ev_ofree[8] = {}, ev_out_done = nullptr;
   double *oslots = nullptr;
