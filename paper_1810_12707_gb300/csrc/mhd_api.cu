@@ -81,7 +81,7 @@ struct mhd_ctx {
   cudaStream_t cap_stream = nullptr;
   // host-pointer set/get: a copy stream and the events that hand staging slots between streams
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_full[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_full[8] = {}, ev_free[8] = {};
   // mhd_get_state_async: its own staging (allocated on first use, `ons` slots of `odz`
   // z-planes), copy stream and events, so that its device-to-host copies overlap whatever the
   // context queues next
@@ -332,10 +332,11 @@ void mhd_destroy(mhd_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->out_stream) cudaStreamDestroy(ctx->out_stream);
-    for (cudaEvent_t e : {ctx->ev_full[0], ctx->ev_full[1], ctx->ev_free[0], ctx->ev_free[1], ctx->ev_out_done,
-                          ctx->ev_slots})
+    for (cudaEvent_t e : {ctx->ev_out_done, ctx->ev_slots})
       if (e) cudaEventDestroy(e);
     for (int i = 0; i < 8; ++i) {
+      if (ctx->ev_full[i]) cudaEventDestroy(ctx->ev_full[i]);
+      if (ctx->ev_free[i]) cudaEventDestroy(ctx->ev_free[i]);
       if (ctx->ev_ofull[i]) cudaEventDestroy(ctx->ev_ofull[i]);
       if (ctx->ev_ofree[i]) cudaEventDestroy(ctx->ev_ofree[i]);
     }
@@ -440,15 +441,18 @@ mhd_status mhd_init(const mhd_params *p, const mhd_phys *phys, mhd_ctx **out) {
 
 // ---- host-pointer transfers, pipelined over slabs of z-planes ----
 // The 7 real fields of one instance cross the host link slab by slab on a second stream while the
-// context's stream transforms the slab before (x and y passes); two staging slots live in W1
-// behind the y-pass output, so nothing is allocated.
+// context's stream transforms the slab before (x and y passes); the staging slots (2 to 8) live
+// in W1 behind the y-pass output, so nothing is allocated.
 namespace {
 
 struct SlabPlan {
   int dz;           // z-planes per slab
-  double *slot[2];  // 7 fields x dz N^2 doubles each
+  int ns;           // slots, 2..8, used in turn
+  double *slot[8];  // 7 fields x dz N^2 doubles each
 };
 
+// As many slots of N/8 z-planes as W1 holds behind the y-pass output, up to one per slab (so
+// that a transfer in can run ahead of the transforms); thinner slabs when not even two fit.
 bool slab_plan(mhd_ctx *c, SlabPlan *pl) {
   const mhd::Dims &d = c->d;
   const size_t n = d.n, nn = n * n;
@@ -458,16 +462,20 @@ bool slab_plan(mhd_ctx *c, SlabPlan *pl) {
   int dz = (int)(n / 8);
   while (dz > 1 && (size_t)14 * dz * nn > avail) dz /= 2;
   if ((size_t)14 * dz * nn > avail) return false;
+  int ns = (int)std::min<size_t>(avail / ((size_t)7 * dz * nn), (size_t)8);
+  ns = std::min(ns, (int)((n + dz - 1) / dz));
+  if (ns < 2) ns = 2;
   pl->dz = dz;
-  pl->slot[0] = reinterpret_cast<double *>(c->W1 + head);
-  pl->slot[1] = pl->slot[0] + (size_t)7 * dz * nn;
+  pl->ns = ns;
+  for (int k = 0; k < ns; ++k)
+    pl->slot[k] = reinterpret_cast<double *>(c->W1 + head) + (size_t)7 * k * dz * nn;
   return true;
 }
 
 mhd_status ensure_copy_stream(mhd_ctx *c) {
   if (c->copy_stream) return MHD_OK;
   CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 8; ++i) {
     CK(cudaEventCreateWithFlags(&c->ev_full[i], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming));
   }
@@ -493,10 +501,10 @@ mhd_status set_state_host(mhd_ctx *c, const double *rho, const double *u, const 
   cudaError_t e = cudaStreamWaitEvent(c->copy_stream, c->ev_slots, 0);
   int i = 0;
   for (int z0 = 0; z0 < n && e == cudaSuccess; z0 += pl.dz, ++i) {
-    const int dzc = std::min(pl.dz, n - z0), k = i & 1;
+    const int dzc = std::min(pl.dz, n - z0), k = i % pl.ns;
     double *slot = pl.slot[k];
     const size_t off = (size_t)z0 * nn, cnt = (size_t)dzc * nn;
-    if (i >= 2) e = cudaStreamWaitEvent(c->copy_stream, c->ev_free[k], 0);
+    if (i >= pl.ns) e = cudaStreamWaitEvent(c->copy_stream, c->ev_free[k], 0);
     for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
       const double *src = f == 0 ? rho + off : f < 4 ? u + (f - 1) * n3 + off : b + (f - 4) * n3 + off;
       e = cudaMemcpyAsync(slot + f * cnt, src, cnt * sizeof(double), cudaMemcpyHostToDevice, c->copy_stream);
@@ -626,7 +634,8 @@ mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, do
   mhd_status st = ensure_copy_stream(c);
   if (st) return st;
   if (c->out_stream) CK(cudaStreamSynchronize(c->out_stream));  // an earlier asynchronous get
-  const Staging sg = {pl.dz, 2, {pl.slot[0], pl.slot[1]}, c->copy_stream, c->ev_full, c->ev_free};
+  Staging sg = {pl.dz, pl.ns, {}, c->copy_stream, c->ev_full, c->ev_free};
+  for (int k = 0; k < pl.ns; ++k) sg.slot[k] = pl.slot[k];
   return get_state_staged(c, src, tw, rho, m, b, sg, true);
 }
 
