@@ -634,8 +634,8 @@ mhd_status get_state_host(mhd_ctx *c, const C *src, const C *tw, double *rho, do
   mhd_status st = ensure_copy_stream(c);
   if (st) return st;
   if (c->out_stream) CK(cudaStreamSynchronize(c->out_stream));  // an earlier asynchronous get
-  Staging sg = {pl.dz, pl.ns, {}, c->copy_stream, c->ev_full, c->ev_free};
-  for (int k = 0; k < pl.ns; ++k) sg.slot[k] = pl.slot[k];
+  // two slots: more measured slower for the synchronous transfer out
+  const Staging sg = {pl.dz, 2, {pl.slot[0], pl.slot[1]}, c->copy_stream, c->ev_full, c->ev_free};
   return get_state_staged(c, src, tw, rho, m, b, sg, true);
 }
 
