@@ -199,12 +199,10 @@ TRAFFIC = {
                                  "ncu --set full, profiles/ncu_abc256_fp32.md"),
     ("flux_x", 256, 1, "fp64df"): (631_424_000 + 1_028_800_512, "76c413daf911ef3f",
                                    "ncu --set full, profiles/ncu_df_kernels_abc256.md"),
-    # the 512^3 launch (about 20 GB on the device) is larger than a full capture should be: the
-    # 256^3 capture scaled by the units the launch processes (row pairs x kept kx, 7.953 times),
-    # the flux pass's traffic being proportional to them (19 fields x rows x (K + 1) values)
-    ("flux_x", 512, 1, "fp64df"): (round((631_424_000 + 1_028_800_512) * (512 * 512 * 171) / (256 * 256 * 86)),
-                                   "76c413daf911ef3f",
-                                   "256^3 ncu capture scaled by row pairs x (K + 1), profiles/ncu_df_kernels_abc256.md"),
+    # the 512^3 launch, captured directly with these three metrics (one ncu pass, so nothing is
+    # saved or restored around it), profiles/ncu_df_kernels_abc256.md
+    ("flux_x", 512, 1, "fp64df"): (5_023_917_824 + 8_550_996_480, "76c413daf911ef3f",
+                                   "ncu dram__bytes metrics on one 512^3 launch, profiles/ncu_df_kernels_abc256.md"),
 }
 
 
